@@ -1,0 +1,327 @@
+"""Benchmark: DOF/s of the AMG-Krylov solve to a 1e-8 relative residual.
+
+Workload: linear elasticity (E = 1, nu = 0.3) on the unit cube, 32^3 cubes x 6
+Kuhn tetrahedra, hierarchical P2, 823,875 DOF, clamped at z = 0, seeded
+U[-1,1]^3 traction on z = 1.  One step = one amg_solve from x = 0 to
+||b - A x|| / ||b|| <= 1e-8 (the whole solve phase: Krylov iterations with
+V-cycles, smoothing, transfers, coarsest solves).  The timed arm is the chosen
+configuration: FP32 V-cycle (symmetric multicolour block Gauss-Seidel 1+1)
+inside FP64 flexible CG.  The plain FP64 AMG-PCG on the same inputs is reported
+beside it.  The setup phase is timed separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--n 32]
+
+Multi-GPU: the solve does not shard here; N ranks run N independent replicas
+(weak scaling) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-8
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def metric_name(n):
+    return (f"DOF/s solved to 1e-8 rel. residual, AMG-Krylov (elasticity {n}^3 P2, "
+            f"FP32 V-cycle in FP64 flexible CG)")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def oracle_sample(n_sample: int, steps: int, warmup: int):
+    """Time the CPU oracle's solve phase on the same workload at n_sample^3."""
+    from fem_inputs import elasticity_problem
+    from oracle import amg
+    prob = elasticity_problem(n_sample, seed=1)
+    h = amg.build_hierarchy(prob)
+    times = []
+    its = None
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        res, _ = amg.solve(prob, tol=TOL, h=h)
+        dt = time.perf_counter() - t0
+        its = res.iterations
+        if k >= warmup:
+            times.append(dt)
+    return prob.n_dof, times, its
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n_sample = args.ref_n
+    ndof, times, its = oracle_sample(n_sample, max(1, args.steps), max(0, min(args.warmup, 1)))
+    t = float(np.mean(times))
+    value = ndof / t
+    line = {
+        "metric": metric_name(args.n), "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"elasticity {args.n}^3 P2 (oracle sample {n_sample}^3)",
+                   "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cpu_threads(),
+                         "kind": "oracle",
+                         "sample": f"FP64 AMG-PCG solve phase of elasticity {n_sample}^3 "
+                                   f"({ndof} DOF, {its} iterations), setup excluded"},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from fem_inputs import elasticity_problem
+    import __graft_entry__ as ge
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1503_01287_gb300 import binding as B
+    B.load_library()
+
+    prob = elasticity_problem(args.n, seed=1)
+    ndof = prob.n_dof
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+
+    t0 = time.perf_counter()
+    chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32), stream=sptr)
+    setup_chosen_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    plain = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64), stream=sptr)
+    setup_plain_ms = 1e3 * (time.perf_counter() - t0)
+
+    b = torch.from_numpy(prob.rhs()).cuda()
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+
+    def timed(handle, steps, warmup, host=False):
+        hb = hx = None
+        if host:
+            hb = torch.from_numpy(prob.rhs()).pin_memory()
+            hx = torch.zeros(ndof, dtype=torch.float64).pin_memory()
+        stats = []
+        for _ in range(warmup):
+            if host:
+                handle.solve(hb, hx, TOL, device_ptrs=False)
+            else:
+                handle.solve(b, x, TOL, device_ptrs=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            if host:
+                st = handle.solve(hb, hx, TOL, device_ptrs=False)
+            else:
+                st = handle.solve(b, x, TOL, device_ptrs=True)
+            stats.append(st.as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, stats = timed(chosen, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms_e2e, stats_e2e = timed(chosen, args.steps, max(1, args.warmup // 2), host=True)
+    ms_plain, stats_plain = timed(plain, max(1, args.steps // 2), 1)
+
+    # correctness of what was timed: recomputed residual of the last solution
+    A = prob.a_scipy().tocsr()
+    xv = x.cpu().numpy()
+    bv = prob.rhs()
+    true_rel = float(np.linalg.norm(bv - A @ xv) / np.linalg.norm(bv))
+
+    # dominant kernel: the FP32 multicolour GS sweep on level 0 (all colours)
+    info0 = chosen.level_info(0)
+    sweep_ms, sweep_launches = chosen.time_level_op("smooth", 0, B.AMG_FP32, reps=20, warmup=3)
+    gs_bytes = 40 * info0.nnzb + 80 * info0.n_nodes
+    spmv_ms, _ = chosen.time_level_op("apply", 0, B.AMG_FP64, reps=20, warmup=3)
+    spmv_bytes = 76 * info0.nnzb + 52 * info0.n_nodes
+    peak, peak_kind = peaks()
+    achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "gs_sweep_fp32_elasticity_n32.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_sweep")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ndof_s, times, its = oracle_sample(args.ref_n, 1, 0)
+        cpu = {"value": ndof_s / times[0], "unit": "DOF/s", "cores": cpu_threads(),
+               "kind": "oracle",
+               "sample": f"FP64 AMG-PCG solve phase of elasticity {args.ref_n}^3 "
+                         f"({ndof_s} DOF, {its} iterations), setup excluded"}
+
+    value = world * ndof / (ms * 1e-3)
+    launches = int(sum(s["kernel_launches"] for s in stats))
+    line = {
+        "metric": metric_name(args.n), "value": value, "unit": "DOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycle + f64 outer", "data": "synthetic",
+        "config": {"workload": f"elasticity_n{args.n}: 32^3 cubes x 6 tets P2, E=1 nu=0.3, "
+                               f"clamped z=0, U[-1,1]^3 traction z=1"
+                               if args.n == 32 else f"elasticity_n{args.n}",
+                   "dofs": ndof, "tol": TOL, "smoother": "GS-1-1 multicolour",
+                   "krylov": "flexible CG", "l2": "inputs larger than L2 (A = "
+                   f"{(76 * info0.nnzb) / 1e6:.0f} MB FP64 + {(40 * info0.nnzb) / 1e6:.0f} MB FP32)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations": stats[-1]["iterations"],
+        "true_rel_residual": true_rel,
+        "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
+        "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
+                   "colours": stats[-1]["level_colours"]},
+        "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                       "iterations": stats_plain[-1]["iterations"]},
+        "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": "DOF/s",
+                "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_block_rows<float,32,GS> (one level-0 sweep = "
+                               f"{sweep_launches} colour launches)",
+                     "unit_bytes": gs_bytes, "ms_per_unit": sweep_ms,
+                     "peak_kind": f"{peak_kind} hbm_gbs"},
+        "kernels": {"spmv_fp64_level0": {"ms": spmv_ms, "bytes": spmv_bytes,
+                                         "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9}},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    chosen.free()
+    plain.free()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--ref-n", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

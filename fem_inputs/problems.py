@@ -51,6 +51,7 @@ class Problem:
     g: np.ndarray | None = None          # float64 (NP,)
     exact_u: np.ndarray | None = None    # (N, 3) exact hierarchical coefficients, if known
     exact_p: np.ndarray | None = None
+    p_weights: np.ndarray | None = None  # int phi_i of the P1 pressure basis (Stokes)
     params: dict = field(default_factory=dict)
 
     @property
@@ -328,6 +329,13 @@ def _saddle_parts(mesh: BoxMesh, kind: str, mu: float, lam: float | None):
     return (rowptr, col, val), (brp, bc, bv), (crp, cc, cv)
 
 
+def pressure_weights(mesh: BoxMesh) -> np.ndarray:
+    """w_i = int phi_i dx of the P1 hats: row sums of the P1 mass matrix."""
+    rp, _, cv = assemble_pressure_mass(mesh, 1.0)
+    return np.bincount(np.repeat(np.arange(mesh.n_vertices), np.diff(rp)), weights=cv,
+                       minlength=mesh.n_vertices)
+
+
 def stokes_lid_problem(n: int, mu: float = 1.0) -> Problem:
     """Lid-driven cavity: u = (1,0,0) on every node with z = 1, u = 0 on the rest of
     the boundary, c = 0; the pressure is fixed up to a constant (mean zero)."""
@@ -344,7 +352,8 @@ def stokes_lid_problem(n: int, mu: float = 1.0) -> Problem:
     liftv = hierarchical_interpolant(mesh, lid)
     prob = Problem(f"stokes_lid_n{n}", "stokes", mesh, rp, c, v, tags,
                    np.zeros((mesh.n_nodes, 3)), liftv, brp, bc, bv, crp, cc, cv,
-                   np.zeros(mesh.n_vertices), params={"n": n, "mu": mu})
+                   np.zeros(mesh.n_vertices), p_weights=pressure_weights(mesh),
+                   params={"n": n, "mu": mu})
     return eliminate_dirichlet(prob)
 
 
@@ -407,7 +416,7 @@ def stokes_quadratic_problem(n: int, seed: int = 0, mu: float = 1.0) -> Problem:
     prob = Problem(f"stokes_quadratic_n{n}_s{seed}", "stokes", mesh, rp, c, v, tags,
                    np.zeros((mesh.n_nodes, 3)), exact.copy(), brp, bc, bv, crp, cc, cv,
                    np.zeros(mesh.n_vertices), exact_u=exact, exact_p=pfun(mesh.coords),
-                   params={"n": n, "seed": seed, "mu": mu})
+                   p_weights=pressure_weights(mesh), params={"n": n, "seed": seed, "mu": mu})
     return eliminate_dirichlet(prob)
 
 

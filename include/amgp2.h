@@ -1,0 +1,307 @@
+/*
+ * amgp2 -- graph-based algebraic multigrid for hierarchical-P2 finite element
+ * systems (H. Yang, arXiv:1503.01287), single-GPU CUDA implementation.
+ *
+ * The library solves the linear systems of Sec. 2.4 of the paper,
+ *   SPD (Eq. ellipticeqn):    A u = f,   A = [K_ll K_ql^T; K_ql K_qq]
+ *   saddle (Eq. mixedeqn):    [A B^T; B -C] [u; p] = [f; g]
+ * with the AMG of Sec. 3 (Algorithm 1; coarsening on the separate graphs of
+ * K_ll and K_qq, Sec. 3.2; prolongation P = diag(I, J[, H]), Eqs.
+ * disprolongmat / mixprolongmat; Galerkin coarse operators P^T K P; block
+ * Jacobi / block Gauss-Seidel / segregated Gauss-Seidel smoothers, Sec. 3.3)
+ * as the preconditioner of CG (SPD) or flexible GMRES (saddle), stopping on
+ * ||b - K x_k||_2 / ||b||_2 <= tol from x_0 = 0 (Sec. 4.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Unknowns are grouped in nodes of 3 components (u_x, u_y, u_z), stored
+ *    interleaved: unknown 3*i + c is component c of node i.  Nodes are ordered
+ *    vertices ("linear" DOF) before edges ("quadratic" DOF), Eq. ellipticeqn.
+ *  - A is 3x3-block CSR: a_rowptr[n_nodes+1], a_col[nnzb] (ascending within a
+ *    row, diagonal block present), a_val[9*nnzb] with each block row-major.
+ *    Its pattern is the structural one (node pairs sharing an element), kept
+ *    even where values are zero: coarsening and colouring read only the pattern.
+ *  - B (saddle kinds) is 1x3-block CSR with one row per pressure unknown:
+ *    b_rowptr[n_pres+1], b_col[b_nnz] (velocity node ids), b_val[3*b_nnz].
+ *  - C (saddle kinds) is scalar CSR n_pres x n_pres; its pattern is the P1
+ *    (vertex) graph and is required also for Stokes, where its values are 0.
+ *  - Dirichlet nodes are identity rows of A with zero off-diagonal blocks in
+ *    their row and column and zero right-hand side (tag AMG_NODE_DIRICHLET).
+ *  - Return codes: AMG_OK (0) on success, AMG_NOT_CONVERGED (1) when the
+ *    iteration limit is reached (x then holds the last iterate, stats are
+ *    filled), negative values on errors; amg_last_error() gives the message.
+ *  - Nothing is thrown across the ABI.  All calls are host calls; device
+ *    work is ordered on the CUDA stream given to amg_setup.
+ */
+#ifndef AMGP2_H
+#define AMGP2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- enums */
+
+/* Problem kinds of Sec. 2.1: Eqs. veclap, elasdis, elasmix, stokesmix. */
+enum amg_kind {
+  AMG_VECTOR_LAPLACE = 0,
+  AMG_ELASTICITY = 1,
+  AMG_MIXED_ELASTICITY = 2,
+  AMG_STOKES = 3
+};
+
+/* Node tags (Sec. 2.3: vertex DOF of V_L, edge DOF of V_Q); bit-or Dirichlet. */
+enum amg_node_tag {
+  AMG_NODE_VERTEX = 0,
+  AMG_NODE_EDGE = 1,
+  AMG_NODE_DIRICHLET = 0x10
+};
+
+/* Smoothers of Sec. 3.3. */
+enum amg_smoother {
+  AMG_SMOOTHER_GS = 0,      /* symmetric multicolour 3x3-block Gauss-Seidel     */
+  AMG_SMOOTHER_JACOBI = 1,  /* damped 3x3-block Jacobi (omega, default 0.5)     */
+  AMG_SMOOTHER_SGS = 2      /* segregated Gauss-Seidel for saddle systems       */
+};
+
+enum amg_precision {
+  AMG_FP64 = 0,             /* cycle in FP64                                    */
+  AMG_FP32 = 1              /* cycle in FP32, outer Krylov and coarsest in FP64 */
+};
+
+enum amg_krylov {
+  AMG_KRYLOV_AUTO = 0,      /* PCG (FP64 cycle) / flexible CG (FP32 cycle) for
+                               SPD kinds, flexible GMRES for saddle kinds      */
+  AMG_KRYLOV_PCG = 1,
+  AMG_KRYLOV_FCG = 2,
+  AMG_KRYLOV_FGMRES = 3,
+  AMG_KRYLOV_NONE = 4       /* stand-alone AMG: repeated Algorithm 1            */
+};
+
+enum amg_status {
+  AMG_OK = 0,
+  AMG_NOT_CONVERGED = 1,
+  AMG_ERR_INVALID = -1,     /* bad argument or malformed matrix                 */
+  AMG_ERR_CUDA = -2,        /* a CUDA call failed                               */
+  AMG_ERR_BREAKDOWN = -3,   /* zero/NaN pivot or non-finite residual            */
+  AMG_ERR_TIMEOUT = -4,     /* a bounded device loop hit its limit              */
+  AMG_ERR_NOMEM = -5,       /* device allocation failed                         */
+  AMG_ERR_UNSUPPORTED = -6  /* option combination not provided                  */
+};
+
+/* --------------------------------------------------------------- structs */
+
+typedef struct amg_matrix {
+  int32_t n_nodes;          /* velocity nodes; 3 unknowns each                  */
+  int32_t n_pres;           /* pressure unknowns; 0 for the SPD kinds           */
+  int64_t nnzb;             /* 3x3 blocks of A                                  */
+  const int32_t* a_rowptr;
+  const int32_t* a_col;
+  const double* a_val;      /* 9 * nnzb, row-major blocks                       */
+  int64_t b_nnz;
+  const int32_t* b_rowptr;
+  const int32_t* b_col;
+  const double* b_val;      /* 3 * b_nnz                                        */
+  int64_t c_nnz;
+  const int32_t* c_rowptr;
+  const int32_t* c_col;
+  const double* c_val;
+  int32_t device_ptrs;      /* 1: all arrays (and node_tags) are device memory  */
+} amg_matrix;
+
+typedef struct amg_options {
+  int32_t smoother;         /* amg_smoother; default GS (SPD) / SGS (saddle)    */
+  int32_t m_pre;            /* pre-smoothing steps, Algorithm 1 (default 1)     */
+  int32_t m_post;           /* post-smoothing steps (default 1)                 */
+  int32_t nu;               /* recursive calls per level: 1 V-cycle, 2 W-cycle  */
+  int32_t cycles;           /* cycles per preconditioner application (1 or 2)   */
+  int32_t precision;        /* amg_precision (default FP64)                     */
+  int32_t krylov;           /* amg_krylov (default AUTO)                        */
+  int32_t max_levels;       /* levels 0..max_levels-1 (default 5)               */
+  int32_t coarse_dofs;      /* stop coarsening at <= this many unknowns (300)   */
+  int32_t gmres_restart;    /* FGMRES(m) restart length (default 50)            */
+  int32_t separate;         /* 1: separate K_ll / K_qq graphs (Sec. 3.2.1);
+                               0: graph of the whole matrix (Table 2, row 3)    */
+  int32_t max_iterations;   /* Krylov iteration limit (default 1000)            */
+  int32_t use_graphs;       /* 1: replay each Krylov iteration as a CUDA graph  */
+  int32_t verbose;
+  double omega;             /* block Jacobi damping (default 0.5)               */
+  double omega_p;           /* sGS pressure step omega (default 0.125)          */
+} amg_options;
+
+#define AMG_MAX_LEVELS 8
+
+typedef struct amg_stats {
+  int32_t iterations;       /* Krylov iterations (operator applications)       */
+  int32_t converged;
+  int32_t n_levels;
+  int32_t pad0;
+  double rel_residual;      /* recursive residual estimate at exit              */
+  double true_rel_residual; /* ||b - K x|| / ||b|| recomputed at exit           */
+  double setup_ms;
+  double solve_ms;
+  int64_t kernel_launches;  /* kernels launched by the last amg_solve           */
+  int32_t level_nodes[AMG_MAX_LEVELS];
+  int32_t level_pres[AMG_MAX_LEVELS];
+  int64_t level_nnzb[AMG_MAX_LEVELS];
+  int32_t level_colours[AMG_MAX_LEVELS];
+} amg_stats;
+
+typedef struct amg_level_info {
+  int32_t n_nodes;
+  int32_t n_pres;
+  int64_t nnzb;
+  int64_t p_nnz;            /* entries of the node prolongation to level+1      */
+  int64_t h_nnz;            /* entries of the pressure prolongation             */
+  int64_t b_nnz;
+  int64_t c_nnz;
+  int32_t n_colours;
+  int32_t is_coarsest;
+} amg_level_info;
+
+/* What amg_level_copy returns (always to host memory). */
+enum amg_level_item {
+  AMG_Q_A_ROWPTR = 0,   /* int32  [n_nodes+1]                                   */
+  AMG_Q_A_COL = 1,      /* int32  [nnzb]                                        */
+  AMG_Q_A_VAL = 2,      /* double [9*nnzb], row-major blocks                    */
+  AMG_Q_TAGS = 3,       /* int32  [n_nodes]                                     */
+  AMG_Q_CF_STATE = 4,   /* int32  [n_nodes]  1 = C, 2 = F (not on coarsest)     */
+  AMG_Q_P_ROWPTR = 5,   /* int32  [n_nodes+1]                                   */
+  AMG_Q_P_COL = 6,      /* int32  [p_nnz]   coarse node ids                     */
+  AMG_Q_P_VAL = 7,      /* double [p_nnz]   node weights (x I_3)                */
+  AMG_Q_COLOUR = 8,     /* int32  [n_nodes] greedy colour of each node          */
+  AMG_Q_DINV = 9,       /* double [9*n_nodes] inverses of diagonal blocks       */
+  AMG_Q_B_ROWPTR = 10,  /* int32  [n_pres+1]                                    */
+  AMG_Q_B_COL = 11,
+  AMG_Q_B_VAL = 12,     /* double [3*b_nnz]                                     */
+  AMG_Q_C_ROWPTR = 13,
+  AMG_Q_C_COL = 14,
+  AMG_Q_C_VAL = 15,
+  AMG_Q_PCF_STATE = 16, /* int32 [n_pres] pressure C/F state                    */
+  AMG_Q_H_ROWPTR = 17,
+  AMG_Q_H_COL = 18,
+  AMG_Q_H_VAL = 19,
+  AMG_Q_COARSE_INV = 20 /* double [m*m] generalised inverse of the coarsest K,
+                           m = 3*n_nodes + n_pres (coarsest level only)         */
+};
+
+typedef struct amg_handle amg_handle;
+
+/* ------------------------------------------------------------ entry points */
+
+/* Fills *opt with the defaults listed in amg_options. */
+void amg_default_options(amg_options* opt);
+
+/*
+ * amg_setup -- the AMG setup phase of Sec. 3.2 on the GPU.
+ *
+ * Copies A (and B, C) to the device, then per level: coarsening graph (K_ll and
+ * K_qq patterns, or the whole pattern when opt->separate = 0; the P1 pattern of
+ * C for the pressure), greedy maximal independent set in increasing node index
+ * (C/F split), prolongation rows (C: 1, F: 1/k on its k C-neighbours, Eqs.
+ * disprolongmat / mixprolongmat), Galerkin product P^T K P, first-fit greedy
+ * colouring in increasing node index, inverses of the 3x3 diagonal blocks.
+ * Coarsening stops when a level has <= opt->coarse_dofs unknowns or
+ * opt->max_levels levels exist; the coarsest matrix is factorised by LU with
+ * complete pivoting stopped at its numerical rank (Algorithm 1, step 6).
+ *
+ *   mat        the system; all arrays host or all device (mat->device_ptrs).
+ *   node_tags  int32 [n_nodes], amg_node_tag values; same memory kind as mat.
+ *   kind       amg_kind.
+ *   opt        options, or NULL for the defaults.
+ *   stream     cudaStream_t; NULL makes the handle create and own a stream.
+ *   out        receives the new handle; NULL on failure.
+ * Ownership: inputs are copied; the caller keeps its arrays.  The handle owns
+ * every device allocation and is released with amg_free.
+ * Errors: AMG_ERR_INVALID for malformed input (missing diagonal block, column
+ * out of range, non-finite values), AMG_ERR_NOMEM, AMG_ERR_CUDA,
+ * AMG_ERR_TIMEOUT (a bounded setup loop hit its limit).
+ */
+int amg_setup(const amg_matrix* mat, const int32_t* node_tags, int32_t kind,
+              const amg_options* opt, void* stream, amg_handle** out);
+
+/*
+ * amg_solve -- solve K x = b to ||b - K x||_2 / ||b||_2 <= rel_tol from x = 0
+ * (stopping rule of Sec. 4.2) with AMG-preconditioned CG / flexible CG (SPD
+ * kinds) or flexible GMRES (saddle kinds).  For Stokes the pressure is
+ * returned with zero mean in the P1 mass weighting.
+ *   b, x        3*n_nodes + n_pres doubles; device pointers when
+ *               device_ptrs = 1, else host pointers (copied in and out inside
+ *               the call).  b and x must not alias.
+ *   stats       optional, filled on return.
+ * The call synchronises its stream before returning.
+ */
+int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t device_ptrs,
+              amg_stats* stats);
+
+/*
+ * amg_set_pressure_weights -- Stokes only: weights w_i (normally int phi_i dx of
+ * the P1 pressure basis) defining the pressure normalisation sum_i w_i p_i = 0
+ * applied to every preconditioned vector and to the result.  Without this call
+ * the weights are all 1.  w: n_pres doubles, host or device (device_ptrs).
+ */
+int amg_set_pressure_weights(amg_handle* h, const double* w, int32_t device_ptrs);
+
+/* Releases the handle and all its device memory.  NULL is accepted. */
+void amg_free(amg_handle* h);
+
+/* Message of the last error of this handle, or of the calling thread's last
+ * failed call when h is NULL.  The string stays valid until the next call. */
+const char* amg_last_error(const amg_handle* h);
+
+/* ---------------------------------------------- inspection (parity tests) */
+
+/* Sizes of level `level` of the hierarchy (0 = finest). */
+int amg_level_info_get(const amg_handle* h, int32_t level, amg_level_info* info);
+
+/* Copies one array of level `level` (see amg_level_item) into host memory of
+ * `capacity` bytes.  AMG_ERR_INVALID if the item does not exist on that level
+ * or capacity is too small. */
+int amg_level_copy(const amg_handle* h, int32_t level, int32_t item, void* host_dst,
+                   int64_t capacity);
+
+/* One application of the preconditioner, z = M^{-1} r (opt->cycles cycles of
+ * Algorithm 1 from zero), in the precision chosen at setup.  r and z are device
+ * pointers of 3*n_nodes + n_pres doubles.  Synchronises the stream. */
+int amg_apply_preconditioner(amg_handle* h, const double* r, double* z);
+
+/* y = K_l x on level `level` with the library's FP64 (precision = AMG_FP64) or
+ * FP32 (AMG_FP32, values rounded to float, accumulated in float) kernels; x
+ * and y are device pointers of 3*n_nodes + n_pres doubles. */
+int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const double* x,
+                    double* y);
+
+/* One smoothing sweep of level `level` on device vectors x (in/out) and b:
+ * direction 0 = pre-smoothing order, 1 = post-smoothing order. */
+int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
+                     const double* b);
+
+/* ------------------------------------------------------------ measurement */
+
+enum amg_level_op {
+  AMG_OP_APPLY = 0,      /* y = K_l x                                            */
+  AMG_OP_RESIDUAL = 1,   /* r = b - K_l x                                        */
+  AMG_OP_SMOOTH = 2,     /* one pre-smoothing sweep (all colours for GS)         */
+  AMG_OP_RESTRICT = 3,   /* b_{l+1} = P^T r                                      */
+  AMG_OP_PROLONG = 4,    /* x_l += P x_{l+1}                                     */
+  AMG_OP_PRECOND = 5     /* one preconditioner application (level ignored)       */
+};
+
+/*
+ * amg_time_level_op -- device time of one level operation of the cycle, for
+ * roofline measurements.  Runs `warmup` untimed then `reps` timed repetitions
+ * of `op` on level `level` in `precision` (AMG_FP64 / AMG_FP32) on the handle's
+ * work vectors, between two CUDA events recorded on the handle's stream;
+ * *ms_per_rep receives the mean.  *launches_per_rep receives the kernel
+ * launches of one repetition (e.g. the colour count of a GS sweep).
+ * The work vectors' contents are overwritten.
+ */
+int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precision, int32_t reps,
+                      int32_t warmup, double* ms_per_rep, int32_t* launches_per_rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGP2_H */

@@ -38,13 +38,8 @@ def attach_pressure(lv, prob):
     lv.C = c
     lv.c_pattern = amg.block_pattern(prob.c_rowptr, prob.c_col, npres)
     lv.extra["stokes"] = prob.kind == "stokes"
-    lv.extra["pmass"] = None
-    if prob.kind == "stokes":
-        # weights w_i = int phi_i = sum of the P1 consistent mass row (exact for hats)
-        from fem_inputs.assemble import assemble_pressure_mass  # input data, not method
-        rp, cc, cv = assemble_pressure_mass(prob.mesh, 1.0)
-        lv.extra["pmass"] = np.bincount(np.repeat(np.arange(npres), np.diff(rp)), weights=cv,
-                                        minlength=npres)
+    # Stokes: pressure normalisation weights w_i = int phi_i (problem data)
+    lv.extra["pmass"] = prob.p_weights if prob.kind == "stokes" else None
 
 
 def coarsen_pressure(cur, nxt):

@@ -1,0 +1,183 @@
+// Internal declarations of the amgp2 CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "amgp2.h"
+
+namespace amgp2 {
+
+// ------------------------------------------------------------------------ errors
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+
+#define AMG_CUDA(x) ::amgp2::check_cuda((x), #x, __FILE__, __LINE__)
+#define AMG_LAUNCH_CHECK() ::amgp2::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// ------------------------------------------------------------------------ device buffers
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count) AMG_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  operator T*() const { return p; }
+};
+
+// ------------------------------------------------------------------------ hierarchy
+
+// One level of the hierarchy.  A is kept as 9 value planes (plane e holds entry
+// (e/3, e%3) of every block), so that consecutive threads reading consecutive
+// blocks read consecutive addresses; the column indices are shared by both
+// precisions.
+struct Level {
+  int n = 0;            // 3-component nodes
+  int np = 0;           // pressure unknowns
+  int64_t nnzb = 0;
+  DBuf<int> rowptr, col, tags;
+  DBuf<double> val;     // 9 * nnzb, plane-major
+  DBuf<float> val32;
+  DBuf<double> dinv;    // 9 * n, node-major row-major inverses of diagonal blocks
+  DBuf<float> dinv32;
+  int ncolours = 0;
+  std::vector<int> colour_ptr;  // host: offsets into colour_rows, ncolours+1
+  DBuf<int> colour, colour_rows;
+  int max_row_blocks = 0;
+  double avg_row_blocks = 0.0;
+
+  // transfer to level+1 (absent on the coarsest level)
+  DBuf<int> state, cid;
+  int64_t p_nnz = 0;
+  DBuf<int> p_rowptr, p_col;   // rows: fine nodes, cols: coarse nodes
+  DBuf<double> p_val;
+  DBuf<float> p_val32;
+  DBuf<int> r_rowptr, r_col;   // R = P^T: rows coarse nodes, cols fine nodes (ascending)
+  DBuf<double> r_val;
+  DBuf<float> r_val32;
+
+  // saddle parts
+  int64_t b_nnz = 0, c_nnz = 0;
+  DBuf<int> b_rowptr, b_col;   // rows: pressure; cols: velocity nodes
+  DBuf<double> b_val;          // 3 planes of b_nnz
+  DBuf<float> b_val32;
+  DBuf<int> bt_rowptr, bt_col; // B^T: rows velocity nodes; cols pressure
+  DBuf<double> bt_val;         // 3 planes
+  DBuf<float> bt_val32;
+  DBuf<int> c_rowptr, c_col;
+  DBuf<double> c_val;
+  DBuf<float> c_val32;
+  DBuf<double> schur;          // sGS scaling S_D (np)
+  DBuf<float> schur32;
+  DBuf<int> pstate, pcid;
+  int64_t h_nnz = 0;
+  DBuf<int> h_rowptr, h_col, ht_rowptr, ht_col;
+  DBuf<double> h_val, ht_val;
+  DBuf<float> h_val32, ht_val32;
+
+  // cycle work vectors (3n + np)
+  DBuf<double> x64, b64, r64, t64;
+  DBuf<float> x32, b32, r32, t32;
+
+  int dofs() const { return 3 * n + np; }
+};
+
+}  // namespace amgp2
+
+struct amg_handle {
+  amg_options opt{};
+  int kind = 0;
+  bool saddle = false;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::vector<std::unique_ptr<amgp2::Level>> L;
+  int coarse_m = 0;
+  int coarse_rank = 0;
+  amgp2::DBuf<double> coarse_inv;  // m x m row-major generalised inverse
+  // Krylov state
+  amgp2::DBuf<double> kb, kx, kr, kz, kp, kq, kw, kro;
+  amgp2::DBuf<double> gm_V, gm_Z;  // FGMRES bases
+  amgp2::DBuf<double> red;         // reduction partials
+  amgp2::DBuf<double> scal;        // device scalars
+  amgp2::DBuf<double> pmass;       // Stokes pressure weights
+  double pmass_sum = 0.0;
+  double* host_scal = nullptr;     // pinned
+  amgp2::DBuf<int> flag;           // device error word
+  std::string last_error;
+  int64_t launches = 0;
+  double setup_ms = 0.0;
+  cudaGraphExec_t cycle_graph = nullptr;  // one preconditioner application
+  bool cycle_graph_valid = false;
+  ~amg_handle();
+};
+
+namespace amgp2 {
+
+// ------------------------------------------------------------------------ helpers
+
+constexpr int kReduceBlocks = 608;   // 4 x 152 SMs
+constexpr int kReduceThreads = 256;
+
+inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// exclusive scan of int counts; out[n] receives the total; returns the total
+int64_t exclusive_scan(const int* in, int* out, int n, cudaStream_t s, amg_handle* h);
+
+// setup (setup.cu)
+void build_hierarchy(amg_handle* h, const amg_matrix* m, const int32_t* tags);
+
+// cycle (cycle.cu)
+template <typename T>
+void level_apply(amg_handle* h, int l, const T* x, T* y);   // y = K_l x
+template <typename T>
+void level_residual(amg_handle* h, int l, const T* x, const T* b, T* r);
+template <typename T>
+void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_zero);
+template <typename T>
+void vcycle(amg_handle* h, int l, bool x_is_zero);
+template <typename T>
+void precondition_device(amg_handle* h, const double* r, double* z);
+// restriction (restrict = true) or prolongation between level and level+1 on
+// the level work vectors, in FP32 or FP64
+void level_transfer(amg_handle* h, int l, bool restrict_, bool f32);
+
+// krylov (krylov.cu)
+int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st);
+
+// small kernels shared across files
+void launch_copy(const double* a, double* b, int64_t n, cudaStream_t s, amg_handle* h);
+void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s, amg_handle* h);
+void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s, amg_handle* h);
+void launch_fill(double* a, double v, int64_t n, cudaStream_t s, amg_handle* h);
+
+}  // namespace amgp2

@@ -1,0 +1,471 @@
+// C ABI of the amgp2 library (declarations and contracts in include/amgp2.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "amg_internal.cuh"
+
+namespace amgp2 {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s failed at %s:%d: %s", what, file, line, cudaGetErrorString(e));
+  cudaGetLastError();  // clear a sticky-free error so the handle stays usable
+  throw Error{e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA, buf};
+}
+
+template <class F>
+int guarded(amg_handle* h, F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    if (h) h->last_error = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    if (h) h->last_error = e.what();
+    return AMG_ERR_INVALID;
+  }
+}
+
+}  // namespace amgp2
+
+using namespace amgp2;
+
+amg_handle::~amg_handle() {
+  if (host_scal) cudaFreeHost(host_scal);
+  if (cycle_graph) cudaGraphExecDestroy(cycle_graph);
+  L.clear();
+  coarse_inv.release();
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+extern "C" {
+
+void amg_default_options(amg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->smoother = -1;          // resolved per kind in amg_setup
+  o->m_pre = 1;
+  o->m_post = 1;
+  o->nu = 1;
+  o->cycles = 1;
+  o->precision = AMG_FP64;
+  o->krylov = AMG_KRYLOV_AUTO;
+  o->max_levels = 5;
+  o->coarse_dofs = 300;
+  o->gmres_restart = 50;
+  o->separate = 1;
+  o->max_iterations = 1000;
+  o->use_graphs = 1;
+  o->verbose = 0;
+  o->omega = 0.5;
+  o->omega_p = 0.125;
+}
+
+int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,
+              void* stream, amg_handle** out) {
+  if (out) *out = nullptr;
+  amg_handle* h = nullptr;
+  int rc = guarded(nullptr, [&]() -> int {
+    if (!m || !node_tags || !out) fail(AMG_ERR_INVALID, "null argument");
+    if (kind < AMG_VECTOR_LAPLACE || kind > AMG_STOKES) fail(AMG_ERR_INVALID, "unknown kind");
+    if (m->n_nodes <= 0 || m->nnzb < m->n_nodes || !m->a_rowptr || !m->a_col || !m->a_val)
+      fail(AMG_ERR_INVALID, "A must have n_nodes > 0 and a diagonal block per row");
+    const bool saddle = kind == AMG_MIXED_ELASTICITY || kind == AMG_STOKES;
+    if (saddle && (m->n_pres <= 0 || !m->b_rowptr || !m->b_col || !m->b_val || !m->c_rowptr ||
+                   !m->c_col || !m->c_val || m->c_nnz < m->n_pres))
+      fail(AMG_ERR_INVALID, "saddle kinds need B and C (C's pattern also for Stokes)");
+    if (!saddle && m->n_pres != 0) fail(AMG_ERR_INVALID, "n_pres must be 0 for SPD kinds");
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    h = new amg_handle();
+    if (opt) h->opt = *opt;
+    else amg_default_options(&h->opt);
+    if (h->opt.smoother < 0) h->opt.smoother = saddle ? AMG_SMOOTHER_SGS : AMG_SMOOTHER_GS;
+    if (saddle && h->opt.smoother != AMG_SMOOTHER_SGS)
+      fail(AMG_ERR_UNSUPPORTED, "saddle kinds use the segregated Gauss-Seidel smoother");
+    if (!saddle && h->opt.smoother == AMG_SMOOTHER_SGS)
+      fail(AMG_ERR_INVALID, "the segregated smoother needs a saddle kind");
+    if (h->opt.precision != AMG_FP64 && h->opt.precision != AMG_FP32)
+      fail(AMG_ERR_INVALID, "unknown precision");
+    if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
+        h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1)
+      fail(AMG_ERR_INVALID, "option out of range");
+    h->kind = kind;
+    h->saddle = saddle;
+    if (stream) {
+      h->stream = (cudaStream_t)stream;
+    } else {
+      // graph capture needs a non-legacy stream: the handle then owns one
+      AMG_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+      h->stream = h->own_stream;
+    }
+    h->flag.alloc(1);
+    AMG_CUDA(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
+    auto t0 = std::chrono::steady_clock::now();
+    build_hierarchy(h, m, node_tags);
+    if (kind == AMG_STOKES) {
+      const int np = m->n_pres;
+      h->pmass.alloc(np);
+      std::vector<double> w(np, 1.0);   // until amg_set_pressure_weights is called
+      AMG_CUDA(cudaMemcpyAsync(h->pmass.p, w.data(), np * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream));
+      h->pmass_sum = (double)np;
+    }
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    h->setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return AMG_OK;
+  });
+  if (rc != AMG_OK) {
+    delete h;
+    if (out) *out = nullptr;
+  }
+  return rc;
+}
+
+int amg_set_pressure_weights(amg_handle* h, const double* w, int32_t device_ptrs) {
+  return guarded(h, [&]() -> int {
+    if (!h || !w) fail(AMG_ERR_INVALID, "null argument");
+    if (h->kind != AMG_STOKES) fail(AMG_ERR_INVALID, "pressure weights apply to Stokes only");
+    const int np = h->L[0]->np;
+    std::vector<double> hw(np);
+    AMG_CUDA(cudaMemcpyAsync(hw.data(), w, np * sizeof(double),
+                             device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                             h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    double s = 0.0;
+    for (double v : hw) {
+      if (!(v >= 0.0) || !std::isfinite(v)) fail(AMG_ERR_INVALID, "weights must be finite, >= 0");
+      s += v;
+    }
+    if (!(s > 0.0)) fail(AMG_ERR_INVALID, "weights sum to zero");
+    AMG_CUDA(cudaMemcpyAsync(h->pmass.p, hw.data(), np * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    h->pmass_sum = s;
+    return AMG_OK;
+  });
+}
+
+static void fill_stats(amg_handle* h, amg_stats* st) {
+  st->n_levels = (int)h->L.size();
+  st->setup_ms = h->setup_ms;
+  for (int l = 0; l < AMG_MAX_LEVELS; ++l) {
+    if (l < (int)h->L.size()) {
+      st->level_nodes[l] = h->L[l]->n;
+      st->level_pres[l] = h->L[l]->np;
+      st->level_nnzb[l] = h->L[l]->nnzb;
+      st->level_colours[l] = h->L[l]->ncolours;
+    } else {
+      st->level_nodes[l] = st->level_pres[l] = st->level_colours[l] = 0;
+      st->level_nnzb[l] = 0;
+    }
+  }
+}
+
+int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t device_ptrs,
+              amg_stats* stats) {
+  return guarded(h, [&]() -> int {
+    if (!h || !b || !x) fail(AMG_ERR_INVALID, "null argument");
+    if (b == x) fail(AMG_ERR_INVALID, "b and x must not alias");
+    if (!(rel_tol > 0.0)) fail(AMG_ERR_INVALID, "rel_tol must be > 0");
+    amg_stats local{};
+    amg_stats* st = stats ? stats : &local;
+    std::memset(st, 0, sizeof(*st));
+    fill_stats(h, st);
+    const int64_t n = h->L[0]->dofs();
+    const int64_t l0 = h->launches;
+    cudaEvent_t e0, e1;
+    AMG_CUDA(cudaEventCreate(&e0));
+    AMG_CUDA(cudaEventCreate(&e1));
+    AMG_CUDA(cudaEventRecord(e0, h->stream));
+    int rc;
+    if (device_ptrs) {
+      rc = solve_device(h, b, x, rel_tol, st);
+    } else {
+      // staging vectors are kept in the handle so repeated solves allocate nothing
+      if ((int64_t)h->kb.n < n) h->kb.alloc(n);
+      if ((int64_t)h->kx.n < n) h->kx.alloc(n);
+      AMG_CUDA(cudaMemcpyAsync(h->kb.p, b, n * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream));
+      rc = solve_device(h, h->kb, h->kx, rel_tol, st);
+      AMG_CUDA(cudaMemcpyAsync(x, h->kx.p, n * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    }
+    AMG_CUDA(cudaEventRecord(e1, h->stream));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st->solve_ms = ms;
+    st->converged = rc == AMG_OK;
+    st->kernel_launches = h->launches - l0;
+    return rc;
+  });
+}
+
+void amg_free(amg_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+const char* amg_last_error(const amg_handle* h) {
+  if (h) return h->last_error.c_str();
+  return g_last_error.c_str();
+}
+
+int amg_level_info_get(const amg_handle* h, int32_t level, amg_level_info* info) {
+  return guarded(const_cast<amg_handle*>(h), [&]() -> int {
+    if (!h || !info) fail(AMG_ERR_INVALID, "null argument");
+    if (level < 0 || level >= (int)h->L.size()) fail(AMG_ERR_INVALID, "no such level");
+    const Level& lv = *h->L[level];
+    info->n_nodes = lv.n;
+    info->n_pres = lv.np;
+    info->nnzb = lv.nnzb;
+    info->p_nnz = lv.p_nnz;
+    info->h_nnz = lv.h_nnz;
+    info->b_nnz = lv.b_nnz;
+    info->c_nnz = lv.c_nnz;
+    info->n_colours = lv.ncolours;
+    info->is_coarsest = level == (int)h->L.size() - 1;
+    return AMG_OK;
+  });
+}
+
+}  // extern "C"
+
+namespace amgp2 {
+namespace {
+
+__global__ void k_planes_to_aos(const double* __restrict__ planes, int nv, int64_t nnz,
+                                double* __restrict__ aos) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    for (int e = 0; e < nv; ++e) aos[nv * k + e] = planes[e * nnz + k];
+}
+
+void copy_out(amg_handle* h, const void* src, size_t bytes, void* dst, int64_t cap) {
+  if ((int64_t)bytes > cap) fail(AMG_ERR_INVALID, "destination too small");
+  if (bytes == 0) return;
+  if (!src) fail(AMG_ERR_INVALID, "item not present on this level");
+  AMG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+  AMG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void copy_planes(amg_handle* h, const double* planes, int nv, int64_t nnz, void* dst, int64_t cap) {
+  if ((int64_t)(nnz * nv * sizeof(double)) > cap) fail(AMG_ERR_INVALID, "destination too small");
+  if (nnz == 0) return;
+  DBuf<double> tmp;
+  tmp.alloc(nnz * nv);
+  k_planes_to_aos<<<std::max(1, std::min(div_up(nnz, 256), 4096)), 256, 0, h->stream>>>(
+      planes, nv, nnz, tmp);
+  AMG_LAUNCH_CHECK();
+  copy_out(h, tmp.p, nnz * nv * sizeof(double), dst, cap);
+}
+
+}  // namespace
+}  // namespace amgp2
+
+extern "C" {
+
+int amg_level_copy(const amg_handle* hc, int32_t level, int32_t item, void* dst, int64_t cap) {
+  amg_handle* h = const_cast<amg_handle*>(hc);
+  return guarded(h, [&]() -> int {
+    if (!h || !dst) fail(AMG_ERR_INVALID, "null argument");
+    if (level < 0 || level >= (int)h->L.size()) fail(AMG_ERR_INVALID, "no such level");
+    const Level& lv = *h->L[level];
+    const bool last = level == (int)h->L.size() - 1;
+    const size_t I = sizeof(int), D = sizeof(double);
+    switch (item) {
+      case AMG_Q_A_ROWPTR: copy_out(h, lv.rowptr, (lv.n + 1) * I, dst, cap); break;
+      case AMG_Q_A_COL: copy_out(h, lv.col, lv.nnzb * I, dst, cap); break;
+      case AMG_Q_A_VAL: copy_planes(h, lv.val, 9, lv.nnzb, dst, cap); break;
+      case AMG_Q_TAGS: copy_out(h, lv.tags, lv.n * I, dst, cap); break;
+      case AMG_Q_CF_STATE:
+        if (last) fail(AMG_ERR_INVALID, "the coarsest level has no C/F split");
+        copy_out(h, lv.state, lv.n * I, dst, cap); break;
+      case AMG_Q_P_ROWPTR:
+        if (last) fail(AMG_ERR_INVALID, "the coarsest level has no prolongation");
+        copy_out(h, lv.p_rowptr, (lv.n + 1) * I, dst, cap); break;
+      case AMG_Q_P_COL:
+        if (last) fail(AMG_ERR_INVALID, "the coarsest level has no prolongation");
+        copy_out(h, lv.p_col, lv.p_nnz * I, dst, cap); break;
+      case AMG_Q_P_VAL:
+        if (last) fail(AMG_ERR_INVALID, "the coarsest level has no prolongation");
+        copy_out(h, lv.p_val, lv.p_nnz * D, dst, cap); break;
+      case AMG_Q_COLOUR:
+        if (last || h->saddle) fail(AMG_ERR_INVALID, "level has no colouring");
+        copy_out(h, lv.colour, lv.n * I, dst, cap); break;
+      case AMG_Q_DINV: copy_out(h, lv.dinv, 9 * lv.n * D, dst, cap); break;
+      case AMG_Q_B_ROWPTR:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no B");
+        copy_out(h, lv.b_rowptr, (lv.np + 1) * I, dst, cap); break;
+      case AMG_Q_B_COL:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no B");
+        copy_out(h, lv.b_col, lv.b_nnz * I, dst, cap); break;
+      case AMG_Q_B_VAL:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no B");
+        copy_planes(h, lv.b_val, 3, lv.b_nnz, dst, cap); break;
+      case AMG_Q_C_ROWPTR:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no C");
+        copy_out(h, lv.c_rowptr, (lv.np + 1) * I, dst, cap); break;
+      case AMG_Q_C_COL:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no C");
+        copy_out(h, lv.c_col, lv.c_nnz * I, dst, cap); break;
+      case AMG_Q_C_VAL:
+        if (!h->saddle) fail(AMG_ERR_INVALID, "no C");
+        copy_out(h, lv.c_val, lv.c_nnz * D, dst, cap); break;
+      case AMG_Q_PCF_STATE:
+        if (!h->saddle || last) fail(AMG_ERR_INVALID, "no pressure C/F split");
+        copy_out(h, lv.pstate, lv.np * I, dst, cap); break;
+      case AMG_Q_H_ROWPTR:
+        if (!h->saddle || last) fail(AMG_ERR_INVALID, "no H");
+        copy_out(h, lv.h_rowptr, (lv.np + 1) * I, dst, cap); break;
+      case AMG_Q_H_COL:
+        if (!h->saddle || last) fail(AMG_ERR_INVALID, "no H");
+        copy_out(h, lv.h_col, lv.h_nnz * I, dst, cap); break;
+      case AMG_Q_H_VAL:
+        if (!h->saddle || last) fail(AMG_ERR_INVALID, "no H");
+        copy_out(h, lv.h_val, lv.h_nnz * D, dst, cap); break;
+      case AMG_Q_COARSE_INV:
+        if (!last) fail(AMG_ERR_INVALID, "only the coarsest level has a factorisation");
+        copy_out(h, h->coarse_inv, (size_t)h->coarse_m * h->coarse_m * D, dst, cap); break;
+      default:
+        fail(AMG_ERR_INVALID, "unknown item");
+    }
+    return AMG_OK;
+  });
+}
+
+int amg_apply_preconditioner(amg_handle* h, const double* r, double* z) {
+  return guarded(h, [&]() -> int {
+    if (!h || !r || !z) fail(AMG_ERR_INVALID, "null argument");
+    if (h->opt.precision == AMG_FP32) precondition_device<float>(h, r, z);
+    else precondition_device<double>(h, r, z);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    return AMG_OK;
+  });
+}
+
+int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const double* x, double* y) {
+  return guarded(h, [&]() -> int {
+    if (!h || !x || !y) fail(AMG_ERR_INVALID, "null argument");
+    if (level < 0 || level >= (int)h->L.size()) fail(AMG_ERR_INVALID, "no such level");
+    Level& lv = *h->L[level];
+    if (precision == AMG_FP64) {
+      level_apply<double>(h, level, x, y);
+    } else if (precision == AMG_FP32) {
+      if (!lv.val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with precision FP32");
+      const int64_t n = lv.dofs();
+      launch_to_float(x, lv.t32, n, h->stream, h);
+      level_apply<float>(h, level, lv.t32.p, lv.r32.p);
+      launch_to_double(lv.r32, y, n, h->stream, h);
+    } else {
+      fail(AMG_ERR_INVALID, "unknown precision");
+    }
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    return AMG_OK;
+  });
+}
+
+int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x, const double* b) {
+  return guarded(h, [&]() -> int {
+    if (!h || !x || !b) fail(AMG_ERR_INVALID, "null argument");
+    if (level < 0 || level >= (int)h->L.size() - 1)
+      fail(AMG_ERR_INVALID, "no smoother on this level");
+    level_smooth<double>(h, level, x, b, direction != 0, false);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    return AMG_OK;
+  });
+}
+
+int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precision, int32_t reps,
+                      int32_t warmup, double* ms_per_rep, int32_t* launches_per_rep) {
+  return guarded(h, [&]() -> int {
+    if (!h || !ms_per_rep || reps < 1 || warmup < 0) fail(AMG_ERR_INVALID, "bad argument");
+    const int L = (int)h->L.size();
+    if (op != AMG_OP_PRECOND && (level < 0 || level >= L)) fail(AMG_ERR_INVALID, "no such level");
+    if ((op == AMG_OP_SMOOTH || op == AMG_OP_RESTRICT || op == AMG_OP_PROLONG) && level == L - 1)
+      fail(AMG_ERR_INVALID, "the coarsest level has no smoother or transfer");
+    const bool f32 = precision == AMG_FP32;
+    if (f32 && !h->L[0]->val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with FP32");
+    Level& lv = *h->L[op == AMG_OP_PRECOND ? 0 : level];
+    if (op == AMG_OP_PRECOND && (int64_t)h->kr.n < lv.dofs()) {
+      h->kr.alloc(lv.dofs());
+      h->kz.alloc(lv.dofs());
+      AMG_CUDA(cudaMemsetAsync(h->kr.p, 0, h->kr.bytes(), h->stream));
+    }
+    auto once = [&]() {
+      switch (op) {
+        case AMG_OP_APPLY:
+          if (f32) level_apply<float>(h, level, lv.x32.p, lv.r32.p);
+          else level_apply<double>(h, level, lv.x64.p, lv.r64.p);
+          break;
+        case AMG_OP_RESIDUAL:
+          if (f32) level_residual<float>(h, level, lv.x32.p, lv.b32.p, lv.r32.p);
+          else level_residual<double>(h, level, lv.x64.p, lv.b64.p, lv.r64.p);
+          break;
+        case AMG_OP_SMOOTH:
+          if (f32) level_smooth<float>(h, level, lv.x32.p, lv.b32.p, false, false);
+          else level_smooth<double>(h, level, lv.x64.p, lv.b64.p, false, false);
+          break;
+        case AMG_OP_RESTRICT:
+        case AMG_OP_PROLONG:
+          level_transfer(h, level, op == AMG_OP_RESTRICT, f32);
+          break;
+        case AMG_OP_PRECOND:
+          if (h->opt.precision == AMG_FP32) precondition_device<float>(h, h->kr, h->kz);
+          else precondition_device<double>(h, h->kr, h->kz);
+          break;
+        default:
+          fail(AMG_ERR_INVALID, "unknown op");
+      }
+    };
+    // vectors: zero x, b = 1 so that the data are finite
+    launch_fill(lv.x64, 0.0, lv.dofs(), h->stream, h);
+    launch_fill(lv.b64, 1.0, lv.dofs(), h->stream, h);
+    if (f32) {
+      launch_to_float(lv.x64, lv.x32, lv.dofs(), h->stream, h);
+      launch_to_float(lv.b64, lv.b32, lv.dofs(), h->stream, h);
+    }
+    for (int i = 0; i < warmup; ++i) once();
+    const int64_t l0 = h->launches;
+    cudaEvent_t e0, e1;
+    AMG_CUDA(cudaEventCreate(&e0));
+    AMG_CUDA(cudaEventCreate(&e1));
+    AMG_CUDA(cudaEventRecord(e0, h->stream));
+    for (int i = 0; i < reps; ++i) once();
+    AMG_CUDA(cudaEventRecord(e1, h->stream));
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_rep = ms / reps;
+    if (launches_per_rep) *launches_per_rep = (int32_t)((h->launches - l0) / reps);
+    return AMG_OK;
+  });
+}
+
+}  // extern "C"

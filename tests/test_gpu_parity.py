@@ -1,0 +1,383 @@
+"""GPU path vs CPU oracle, through the C ABI.
+
+Bit-exact: C/F splits, prolongation patterns and weights, coarse patterns,
+colourings.  Floating point: Galerkin values and FP64 operator applications
+within 1e-12 relative (per entry, relative to |A||x|); smoothing sweeps and
+preconditioner applications within 1e-10; final FP64 solutions within 1e-9
+relative.  FP32 tolerances follow from float rounding: each of the <= ~200
+products of a row is rounded once (2^-24) plus the accumulation, bounded here
+by 2e-5 relative to |A||x|.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from fem_inputs import problems as fp
+from oracle import amg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STATE = {amg.STATE_C: 1, amg.STATE_F: 2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def B():
+    from paper_1503_01287_gb300 import binding
+    return binding
+
+
+def gpu(prob, **opts):
+    o = B().default_options(**opts)
+    return B().setup_problem(prob, o)
+
+
+def oracle_opts(prob, **kw):
+    sm = kw.pop("smoother", None)
+    if sm is None:
+        sm = "sgs" if prob.saddle else "gs"
+    return amg.Options(smoother=sm, **kw)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def check_hierarchy(h, oh, vals_tol=1e-12, check_colour=True):
+    assert h.n_levels == len(oh.levels), (h.n_levels, [lv.n for lv in oh.levels])
+    for l, lv in enumerate(oh.levels):
+        info = h.level_info(l)
+        last = l == len(oh.levels) - 1
+        assert info.n_nodes == lv.n
+        assert np.array_equal(h.level_array(l, "a_rowptr"), lv.rowptr)
+        assert np.array_equal(h.level_array(l, "a_col"), lv.col)
+        assert np.array_equal(h.level_array(l, "tags"), lv.tags)
+        v = h.level_array(l, "a_val").reshape(-1, 3, 3)
+        assert np.abs(v - lv.val).max() <= vals_tol * np.abs(lv.val).max()
+        d = h.level_array(l, "dinv").reshape(-1, 3, 3)
+        assert np.abs(d - lv.dinv).max() <= 1e-10 * np.abs(lv.dinv).max()
+        if not last:
+            st = h.level_array(l, "cf_state")
+            assert np.array_equal(st, np.vectorize(STATE.get)(lv.state))
+            prow = h.level_array(l, "p_rowptr")
+            pcol = h.level_array(l, "p_col")
+            ps = lv.P_structure.tocsr()
+            ps.sort_indices()
+            assert np.array_equal(prow, ps.indptr) and np.array_equal(pcol, ps.indices)
+            rows = np.repeat(np.arange(lv.n), np.diff(prow))
+            want = np.asarray(lv.P[rows, pcol]).ravel()
+            assert np.array_equal(h.level_array(l, "p_val"), want)
+            if check_colour and not oh.saddle:
+                assert np.array_equal(h.level_array(l, "colour"), lv.colour)
+        if oh.saddle:
+            assert info.n_pres == lv.npres
+            nb = 3 * lv.n
+            bc = h.level_array(l, "b_col")
+            brow = h.level_array(l, "b_rowptr")
+            bv = h.level_array(l, "b_val").reshape(-1, 3)
+            Bg = sp.csr_matrix((bv.ravel(), (np.repeat(np.repeat(np.arange(lv.npres),
+                                                                  np.diff(brow)), 3),
+                                              (3 * bc[:, None] + np.arange(3)).ravel())),
+                               shape=(lv.npres, nb))
+            assert abs(Bg - lv.B).max() <= vals_tol * max(abs(lv.B).max(), 1e-300)
+            crow = h.level_array(l, "c_rowptr")
+            Cg = sp.csr_matrix((h.level_array(l, "c_val"), h.level_array(l, "c_col"), crow),
+                               shape=(lv.npres, lv.npres))
+            assert abs(Cg - lv.C).max() <= vals_tol * max(abs(lv.C).max(), 1e-300) + 1e-300
+            if not last:
+                assert np.array_equal(h.level_array(l, "pcf_state"),
+                                      np.vectorize(STATE.get)(lv.p_state))
+                hs = lv.H_structure.tocsr()
+                hs.sort_indices()
+                assert np.array_equal(h.level_array(l, "h_rowptr"), hs.indptr)
+                assert np.array_equal(h.level_array(l, "h_col"), hs.indices)
+
+
+def coarse_check(h, oh):
+    L = len(oh.levels) - 1
+    m = 3 * oh.levels[L].n + oh.levels[L].npres
+    X = h.level_array(L, "coarse_inv").reshape(m, m)
+    rng = np.random.default_rng(5)
+    bvec = rng.standard_normal(m)
+    if oh.saddle:
+        from oracle import saddle as sd
+        K = sd.coarse_matrix(oh.levels[L])
+    else:
+        K = oh.levels[L].A.toarray()
+    bvec = K @ bvec          # consistent right-hand side
+    want = amg.complete_pivot_solve(oh.coarse_factor[1], bvec)
+    got = X @ bvec
+    assert np.abs(K @ got - bvec).max() <= 1e-9 * np.abs(bvec).max()
+    if not oh.saddle:
+        assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+
+
+# --------------------------------------------------------------------------- setup parity
+
+@pytest.mark.parametrize("maker", [
+    lambda: fp.vector_laplace_problem(4, seed=0),
+    lambda: fp.elasticity_problem(6, seed=1),
+    lambda: fp.elasticity_problem((5, 7, 4), seed=2, lengths=(1.0, 2.5, 3.0), nu=0.4),
+    lambda: fp.elasticity_quadratic_problem(5, seed=2, jitter=0.2),
+])
+def test_hierarchy_matches_oracle(maker):
+    prob = maker()
+    h = gpu(prob)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob))
+    check_hierarchy(h, oh)
+    coarse_check(h, oh)
+
+
+def test_nonseparating_hierarchy_matches_oracle():
+    prob = fp.elasticity_problem(6, seed=1)
+    h = gpu(prob, separate=0)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob, separate=False))
+    check_hierarchy(h, oh)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: fp.mixed_elasticity_problem(4, nu=0.49, seed=5),
+    lambda: fp.stokes_lid_problem(4),
+])
+def test_saddle_hierarchy_matches_oracle(maker):
+    prob = maker()
+    h = gpu(prob)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob))
+    check_hierarchy(h, oh)
+    coarse_check(h, oh)
+
+
+# --------------------------------------------------------------------------- kernels
+
+def _abs_bound(A, x):
+    return abs(A) @ np.abs(x)
+
+
+@pytest.mark.parametrize("n", [6, 10])
+def test_operator_apply_fp64_and_fp32(n):
+    prob = fp.elasticity_problem(n, seed=3)
+    h = gpu(prob, precision=B().AMG_FP32)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob))
+    rng = np.random.default_rng(n)
+    for l, lv in enumerate(oh.levels):
+        x = rng.standard_normal(3 * lv.n)
+        y = torch.zeros(3 * lv.n, dtype=torch.float64, device="cuda")
+        h.level_apply(l, cuda(x), y, B().AMG_FP64)
+        want = lv.A @ x
+        bound = _abs_bound(lv.A, x)
+        assert np.all(np.abs(y.cpu().numpy() - want) <= 1e-12 * bound + 1e-300)
+        h.level_apply(l, cuda(x), y, B().AMG_FP32)
+        assert np.all(np.abs(y.cpu().numpy() - want) <= 2e-5 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+def test_smoothing_sweep_matches_oracle(smoother):
+    prob = fp.elasticity_problem(7, seed=4)
+    code = {"gs": B().AMG_SMOOTHER_GS, "jacobi": B().AMG_SMOOTHER_JACOBI}[smoother]
+    h = gpu(prob, smoother=code)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob, smoother=smoother))
+    rng = np.random.default_rng(1)
+    for l in range(len(oh.levels) - 1):
+        lv = oh.levels[l]
+        for post in (False, True):
+            x0 = rng.standard_normal(3 * lv.n)
+            b = rng.standard_normal(3 * lv.n)
+            xg = cuda(x0)
+            h.level_smooth(l, xg, cuda(b), post=post)
+            if smoother == "gs":
+                want = amg.gs_sweep(lv, x0, b, reverse=post)
+            else:
+                want = amg.jacobi_sweep(lv, x0, b, 0.5)
+            got = xg.cpu().numpy()
+            assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("kind", ["elasticity", "laplace", "mixed", "stokes"])
+def test_preconditioner_matches_oracle(kind):
+    prob = {"elasticity": lambda: fp.elasticity_problem(6, seed=7),
+            "laplace": lambda: fp.vector_laplace_problem(5, seed=1),
+            "mixed": lambda: fp.mixed_elasticity_problem(4, nu=0.49, seed=5),
+            "stokes": lambda: fp.stokes_lid_problem(4)}[kind]()
+    h = gpu(prob)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob))
+    r = np.random.default_rng(3).standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(cuda(r), z)
+    want = amg.precondition(oh, r)
+    got = z.cpu().numpy()
+    if kind == "stokes":
+        # coarse generalised inverses may differ by null-space components: compare the
+        # images under K, which are unique
+        from oracle import saddle as sd
+        kg, kw = sd.apply_K(oh.levels[0], got), sd.apply_K(oh.levels[0], want)
+        assert np.linalg.norm(kg - kw) <= 1e-8 * np.linalg.norm(kw)
+    else:
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+# --------------------------------------------------------------------------- full solves
+
+def _solve(h, prob, tol):
+    b = cuda(prob.rhs())
+    x = torch.zeros_like(b)
+    st = h.solve(b, x, tol, device_ptrs=True)
+    return st, x.cpu().numpy()
+
+
+def test_solve_vector_laplace_workload():
+    """The 4^3 vector-Laplacian workload: AMG-PCG to 1e-10, exact quadratic solution."""
+    prob = fp.vector_laplace_problem(4, seed=0)
+    h = gpu(prob)
+    st, x = _solve(h, prob, 1e-10)
+    ref, _ = amg.solve(prob, tol=1e-10)
+    assert st.converged and st.true_rel_residual <= 1e-10 * 1.5
+    assert abs(st.iterations - ref.iterations) <= 1
+    assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    u = x.reshape(-1, 3) + prob.lift
+    assert np.abs(u - prob.exact_u).max() <= 1e-8 * np.abs(prob.exact_u).max()
+
+
+@pytest.mark.parametrize("opts,okw", [
+    ({}, {}),
+    ({"smoother": 1}, {"smoother": "jacobi"}),
+    ({"nu": 2}, {"nu": 2}),
+    ({"m_pre": 2, "m_post": 2}, {"m_pre": 2, "m_post": 2}),
+    ({"cycles": 2}, {"cycles": 2}),
+    ({"separate": 0}, {"separate": False}),
+])
+def test_pcg_fp64_matches_oracle(opts, okw):
+    prob = fp.elasticity_problem(8, seed=1)
+    h = gpu(prob, **opts)
+    st, x = _solve(h, prob, 1e-10)
+    ref, _ = amg.solve(prob, oracle_opts(prob, **okw), tol=1e-10)
+    assert st.converged
+    assert abs(st.iterations - ref.iterations) <= 1, (st.iterations, ref.iterations)
+    assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    d = (prob.tags & fp.TAG_DIRICHLET) != 0
+    assert np.all(x.reshape(-1, 3)[d] == 0.0)
+
+
+def test_standalone_amg_matches_oracle():
+    prob = fp.vector_laplace_problem(6, seed=2)
+    h = gpu(prob, krylov=B().AMG_KRYLOV_NONE)
+    st, x = _solve(h, prob, 1e-8)
+    oh = amg.build_hierarchy(prob, oracle_opts(prob))
+    b = prob.rhs()
+    xo = np.zeros_like(b)
+    its = 0
+    while np.linalg.norm(b - oh.levels[0].A @ xo) > 1e-8 * np.linalg.norm(b) and its < 500:
+        xo = xo + amg.precondition(oh, b - oh.levels[0].A @ xo)
+        its += 1
+    assert st.converged and abs(st.iterations - its) <= 1, (st.iterations, its)
+    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_fp32_cycle_flexible_cg():
+    prob = fp.elasticity_problem(10, seed=1)
+    h = gpu(prob, precision=B().AMG_FP32)
+    st, x = _solve(h, prob, 1e-8)
+    ref, _ = amg.solve(prob, tol=1e-12)
+    assert st.converged and st.true_rel_residual <= 1.5e-8
+    # error against the FP64 oracle solution, bounded by the stopping rule
+    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-5, err
+    ref8, _ = amg.solve(prob, tol=1e-8)
+    assert st.iterations <= ref8.iterations + 3
+
+
+@pytest.mark.parametrize("kind", ["mixed", "stokes"])
+def test_saddle_fgmres_matches_oracle(kind):
+    prob = (fp.mixed_elasticity_problem(4, nu=0.49, seed=5) if kind == "mixed"
+            else fp.stokes_lid_problem(4))
+    h = gpu(prob)
+    st, x = _solve(h, prob, 1e-10)
+    ref, oh = amg.solve(prob, tol=1e-10)
+    assert st.converged and st.true_rel_residual <= 1e-9
+    assert abs(st.iterations - ref.iterations) <= 2, (st.iterations, ref.iterations)
+    from oracle import saddle as sd
+    K0 = oh.levels[0]
+    nb = np.linalg.norm(prob.rhs())
+    assert np.linalg.norm(sd.apply_K(K0, x) - prob.rhs()) <= 1.5e-10 * nb
+    if kind == "mixed":
+        assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    else:
+        n3 = 3 * prob.n_nodes
+        assert np.linalg.norm(x[:n3] - ref.x[:n3]) <= 1e-7 * np.linalg.norm(ref.x[:n3])
+        assert abs(prob.p_weights @ x[n3:]) <= 1e-12 * np.abs(x[n3:]).max() * prob.n_pres
+
+
+def test_fp32_saddle():
+    prob = fp.mixed_elasticity_problem(5, nu=0.499, seed=5)
+    h = gpu(prob, precision=B().AMG_FP32)
+    st, x = _solve(h, prob, 1e-8)
+    assert st.converged and st.true_rel_residual <= 1.5e-8
+
+
+# --------------------------------------------------------------------------- full size
+
+@pytest.mark.slow
+def test_full_size_elasticity_32():
+    """The 32^3 elasticity workload (823,875 DOF) in the launch configuration the
+    bench times: coarsening, prolongation and colouring bit-exact on levels 0-1,
+    sampled Galerkin blocks, and the solve checked by its recomputed residual."""
+    prob = fp.elasticity_problem(32, seed=1)
+    h = gpu(prob, precision=B().AMG_FP32)
+    oo = oracle_opts(prob)
+    lv0 = amg.Level(prob.n_nodes, prob.a_rowptr, prob.a_col, np.array(prob.a_val), prob.tags)
+    lv0.A = amg.scalar_view(lv0.rowptr, lv0.col, lv0.val, lv0.n)
+    lv1 = amg.coarsen_level(lv0, oo)
+    assert np.array_equal(h.level_array(0, "cf_state"), np.vectorize(STATE.get)(lv0.state))
+    assert np.array_equal(h.level_array(0, "p_col"), lv0.P_structure.tocsr().indices)
+    assert np.array_equal(h.level_array(1, "a_rowptr"), lv1.rowptr)
+    assert np.array_equal(h.level_array(1, "a_col"), lv1.col)
+    v1 = h.level_array(1, "a_val").reshape(-1, 3, 3)
+    idx = np.random.default_rng(0).choice(len(lv1.col), 20000, replace=False)
+    assert np.abs(v1[idx] - lv1.val[idx]).max() <= 1e-12 * np.abs(lv1.val).max()
+    col0 = amg.greedy_colouring(amg.block_pattern(lv0.rowptr, lv0.col, lv0.n))
+    assert np.array_equal(h.level_array(0, "colour"), col0)
+    st, x = _solve(h, prob, 1e-8)
+    assert st.converged
+    A = prob.a_scipy().tocsr()
+    b = prob.rhs()
+    assert np.linalg.norm(b - A @ x) <= 1.5e-8 * np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------------- errors
+
+def test_invalid_inputs_are_rejected():
+    prob = fp.elasticity_problem(2, seed=1)
+    bad = fp.elasticity_problem(2, seed=1)
+    bad.a_col = bad.a_col.copy()
+    bad.a_col[[0, 1]] = bad.a_col[[1, 0]]          # unsorted row
+    with pytest.raises(B().AmgError) as e:
+        gpu(bad)
+    assert e.value.code == -1
+    bad = fp.elasticity_problem(2, seed=1)
+    bad.a_val = bad.a_val.copy()
+    bad.a_val[5, 1, 1] = np.nan
+    with pytest.raises(B().AmgError):
+        gpu(bad)
+    h = gpu(prob, max_iterations=2)
+    st, x = _solve(h, prob, 1e-14)
+    assert not st.converged and st.iterations == 2 and np.all(np.isfinite(x))
+    b = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    st = h.solve(b, x, 1e-8, device_ptrs=True)
+    assert st.iterations == 0 and torch.all(x == 0)
+
+
+def test_host_pointer_solve_matches_device():
+    prob = fp.elasticity_problem(6, seed=1)
+    h = gpu(prob)
+    st_d, xd = _solve(h, prob, 1e-9)
+    xh = np.zeros(prob.n_dof)
+    st_h = h.solve(np.ascontiguousarray(prob.rhs()), xh, 1e-9, device_ptrs=False)
+    assert st_h.iterations == st_d.iterations
+    assert np.array_equal(xh, xd)
