@@ -207,19 +207,29 @@ def test_preconditioner_matches_oracle(kind):
             "stokes": lambda: fp.stokes_lid_problem(4)}[kind]()
     h = gpu(prob)
     oh = amg.build_hierarchy(prob, oracle_opts(prob))
-    r = np.random.default_rng(3).standard_normal(prob.n_dof)
-    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
-    h.apply_preconditioner(cuda(r), z)
-    want = amg.precondition(oh, r)
-    got = z.cpu().numpy()
     if kind == "stokes":
-        # coarse generalised inverses may differ by null-space components: compare the
-        # images under K, which are unique
-        from oracle import saddle as sd
-        kg, kw = sd.apply_K(oh.levels[0], got), sd.apply_K(oh.levels[0], want)
-        assert np.linalg.norm(kg - kw) <= 1e-8 * np.linalg.norm(kw)
-    else:
-        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+        # The Galerkin Stokes coarsest matrix is singular; any solution of a consistent
+        # coarse system is valid (Algorithm 1, step 6) and two generalised inverses differ
+        # by null-space parts that do not cancel after prolongation.  The coarse inverse is
+        # checked on its own (coarse_check); here the oracle uses the GPU's, so that the
+        # rest of the cycle is compared exactly.
+        L = len(oh.levels) - 1
+        m = 3 * oh.levels[L].n + oh.levels[L].npres
+        X = h.level_array(L, "coarse_inv").reshape(m, m)
+        coarse_check(h, oh)
+        oh.coarse_factor = ("given", None)
+        orig = amg.coarse_solve
+        amg.coarse_solve = lambda hh, b: X @ b
+    try:
+        r = np.random.default_rng(3).standard_normal(prob.n_dof)
+        z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+        h.apply_preconditioner(cuda(r), z)
+        want = amg.precondition(oh, r)
+    finally:
+        if kind == "stokes":
+            amg.coarse_solve = orig
+    got = z.cpu().numpy()
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
 
 
 # --------------------------------------------------------------------------- full solves
