@@ -274,7 +274,8 @@ def run_gpu(args, rank, world):
         "true_rel_residual": true_rel,
         "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
-                   "colours": stats[-1]["level_colours"]},
+                   "colours": stats[-1]["level_colours"],
+                   "lanes_per_row": stats[-1]["level_group"]},
         "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                        "iterations": stats_plain[-1]["iterations"]},
         "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": "DOF/s",
@@ -298,6 +299,25 @@ def run_gpu(args, rank, world):
     plain.free()
 
 
+def run_profile(args):
+    """One chosen and one plain solve, nothing else timed (a case for ncu)."""
+    import torch
+
+    from fem_inputs import elasticity_problem
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1503_01287_gb300 import binding as B
+    prob = elasticity_problem(args.n, seed=1)
+    stream = torch.cuda.Stream()
+    b = torch.from_numpy(prob.rhs()).cuda()
+    x = torch.zeros_like(b)
+    for prec in (B.AMG_FP32, B.AMG_FP64):
+        h = B.setup_problem(prob, B.default_options(precision=prec), stream=stream.cuda_stream)
+        st = h.solve(b, x, TOL, device_ptrs=True)
+        print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)
+        h.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,11 +327,15 @@ def main():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--ref-n", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="setup, then exactly one FP32-cycle solve and one FP64 solve (for ncu)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile:
+        return run_profile(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -146,6 +146,7 @@ typedef struct amg_stats {
   int32_t level_pres[AMG_MAX_LEVELS];
   int64_t level_nnzb[AMG_MAX_LEVELS];
   int32_t level_colours[AMG_MAX_LEVELS];
+  int32_t level_group[AMG_MAX_LEVELS];  /* lanes per block row chosen at setup       */
 } amg_stats;
 
 typedef struct amg_level_info {

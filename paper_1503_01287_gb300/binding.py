@@ -69,7 +69,8 @@ class AmgStats(C.Structure):
                 ("level_nodes", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_pres", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_nnzb", C.c_int64 * AMG_MAX_LEVELS),
-                ("level_colours", C.c_int32 * AMG_MAX_LEVELS)]
+                ("level_colours", C.c_int32 * AMG_MAX_LEVELS),
+                ("level_group", C.c_int32 * AMG_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -80,7 +81,8 @@ class AmgStats(C.Structure):
                 "level_nodes": list(self.level_nodes[:nl]),
                 "level_pres": list(self.level_pres[:nl]),
                 "level_nnzb": list(self.level_nnzb[:nl]),
-                "level_colours": list(self.level_colours[:nl])}
+                "level_colours": list(self.level_colours[:nl]),
+                "level_group": list(self.level_group[:nl])}
 
 
 class AmgLevelInfo(C.Structure):

@@ -68,13 +68,14 @@ struct Level {
   DBuf<int> rowptr, col, tags;
   DBuf<double> val;     // 9 * nnzb, plane-major
   DBuf<float> val32;
-  DBuf<double> dinv;    // 9 * n, node-major row-major inverses of diagonal blocks
+  DBuf<double> dinv;    // 12 * n: per node 3 padded rows (4 values) of the inverse
   DBuf<float> dinv32;
   int ncolours = 0;
   std::vector<int> colour_ptr;  // host: offsets into colour_rows, ncolours+1
   DBuf<int> colour, colour_rows;
   int max_row_blocks = 0;
   double avg_row_blocks = 0.0;
+  int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
 
   // transfer to level+1 (absent on the coarsest level)
   DBuf<int> state, cid;
@@ -105,11 +106,12 @@ struct Level {
   DBuf<double> h_val, ht_val;
   DBuf<float> h_val32, ht_val32;
 
-  // cycle work vectors (3n + np)
+  // cycle work vectors, padded layout (4n + np)
   DBuf<double> x64, b64, r64, t64;
   DBuf<float> x32, b32, r32, t32;
 
-  int dofs() const { return 3 * n + np; }
+  int dofs() const { return 3 * n + np; }    // unknowns (user layout)
+  int dofs4() const { return 4 * n + np; }   // padded cycle layout
 };
 
 }  // namespace amgp2
@@ -125,7 +127,8 @@ struct amg_handle {
   int coarse_rank = 0;
   amgp2::DBuf<double> coarse_inv;  // m x m row-major generalised inverse
   // Krylov state
-  amgp2::DBuf<double> kb, kx, kr, kz, kp, kq, kw, kro;
+  amgp2::DBuf<double> kb, kx, kr, kz, kp, kq, kw, kro;   // padded layout
+  amgp2::DBuf<double> ub, ux;                             // user layout staging
   amgp2::DBuf<double> gm_V, gm_Z;  // FGMRES bases
   amgp2::DBuf<double> red;         // reduction partials
   amgp2::DBuf<double> scal;        // device scalars
@@ -171,6 +174,9 @@ void precondition_device(amg_handle* h, const double* r, double* z);
 // the level work vectors, in FP32 or FP64
 void level_transfer(amg_handle* h, int l, bool restrict_, bool f32);
 
+// picks the lanes-per-row of each level by timing the operator kernel
+void autotune_levels(amg_handle* h);
+
 // krylov (krylov.cu)
 int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st);
 
@@ -179,5 +185,8 @@ void launch_copy(const double* a, double* b, int64_t n, cudaStream_t s, amg_hand
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s, amg_handle* h);
 void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s, amg_handle* h);
 void launch_fill(double* a, double v, int64_t n, cudaStream_t s, amg_handle* h);
+// user layout (3 per node, then pressure) <-> padded layout (4 per node, then pressure)
+void launch_to_padded(const double* u, double* p, int n, int np, cudaStream_t s, amg_handle* h);
+void launch_from_padded(const double* p, double* u, int n, int np, cudaStream_t s, amg_handle* h);
 
 }  // namespace amgp2

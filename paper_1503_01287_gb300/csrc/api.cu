@@ -7,6 +7,8 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "amg_internal.cuh"
 
 namespace amgp2 {
@@ -116,6 +118,8 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
     h->flag.alloc(1);
     AMG_CUDA(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
     auto t0 = std::chrono::steady_clock::now();
+    nvtxRangePushA("amg_setup");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     build_hierarchy(h, m, node_tags);
     if (kind == AMG_STOKES) {
       const int np = m->n_pres;
@@ -171,8 +175,10 @@ static void fill_stats(amg_handle* h, amg_stats* st) {
       st->level_pres[l] = h->L[l]->np;
       st->level_nnzb[l] = h->L[l]->nnzb;
       st->level_colours[l] = h->L[l]->ncolours;
+      st->level_group[l] = h->L[l]->group;
     } else {
       st->level_nodes[l] = st->level_pres[l] = st->level_colours[l] = 0;
+      st->level_group[l] = 0;
       st->level_nnzb[l] = 0;
     }
   }
@@ -194,17 +200,19 @@ int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t
     AMG_CUDA(cudaEventCreate(&e0));
     AMG_CUDA(cudaEventCreate(&e1));
     AMG_CUDA(cudaEventRecord(e0, h->stream));
+    nvtxRangePushA(h->opt.precision == AMG_FP32 ? "amg_solve_fp32" : "amg_solve_fp64");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     int rc;
     if (device_ptrs) {
       rc = solve_device(h, b, x, rel_tol, st);
     } else {
       // staging vectors are kept in the handle so repeated solves allocate nothing
-      if ((int64_t)h->kb.n < n) h->kb.alloc(n);
-      if ((int64_t)h->kx.n < n) h->kx.alloc(n);
-      AMG_CUDA(cudaMemcpyAsync(h->kb.p, b, n * sizeof(double), cudaMemcpyHostToDevice,
+      if ((int64_t)h->ub.n < n) h->ub.alloc(n);
+      if ((int64_t)h->ux.n < n) h->ux.alloc(n);
+      AMG_CUDA(cudaMemcpyAsync(h->ub.p, b, n * sizeof(double), cudaMemcpyHostToDevice,
                                h->stream));
-      rc = solve_device(h, h->kb, h->kx, rel_tol, st);
-      AMG_CUDA(cudaMemcpyAsync(x, h->kx.p, n * sizeof(double), cudaMemcpyDeviceToHost,
+      rc = solve_device(h, h->ub, h->ux, rel_tol, st);
+      AMG_CUDA(cudaMemcpyAsync(x, h->ux.p, n * sizeof(double), cudaMemcpyDeviceToHost,
                                h->stream));
     }
     AMG_CUDA(cudaEventRecord(e1, h->stream));
@@ -313,7 +321,16 @@ int amg_level_copy(const amg_handle* hc, int32_t level, int32_t item, void* dst,
       case AMG_Q_COLOUR:
         if (last || h->saddle) fail(AMG_ERR_INVALID, "level has no colouring");
         copy_out(h, lv.colour, lv.n * I, dst, cap); break;
-      case AMG_Q_DINV: copy_out(h, lv.dinv, 9 * lv.n * D, dst, cap); break;
+      case AMG_Q_DINV: {
+        if ((int64_t)(9 * lv.n * D) > cap) fail(AMG_ERR_INVALID, "destination too small");
+        std::vector<double> pad(12 * (size_t)lv.n);
+        copy_out(h, lv.dinv, pad.size() * D, pad.data(), (int64_t)(pad.size() * D));
+        double* o = static_cast<double*>(dst);
+        for (int i = 0; i < lv.n; ++i)
+          for (int r = 0; r < 3; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) o[9 * i + 3 * r + c2] = pad[12 * i + 4 * r + c2];
+        break;
+      }
       case AMG_Q_B_ROWPTR:
         if (!h->saddle) fail(AMG_ERR_INVALID, "no B");
         copy_out(h, lv.b_rowptr, (lv.np + 1) * I, dst, cap); break;
@@ -357,8 +374,13 @@ int amg_level_copy(const amg_handle* hc, int32_t level, int32_t item, void* dst,
 int amg_apply_preconditioner(amg_handle* h, const double* r, double* z) {
   return guarded(h, [&]() -> int {
     if (!h || !r || !z) fail(AMG_ERR_INVALID, "null argument");
-    if (h->opt.precision == AMG_FP32) precondition_device<float>(h, r, z);
-    else precondition_device<double>(h, r, z);
+    Level& lv = *h->L[0];
+    const int64_t n4 = lv.dofs4();
+    if ((int64_t)h->kr.n < n4) { h->kr.alloc(n4); h->kz.alloc(n4); }
+    launch_to_padded(r, h->kr, lv.n, lv.np, h->stream, h);
+    if (h->opt.precision == AMG_FP32) precondition_device<float>(h, h->kr, h->kz);
+    else precondition_device<double>(h, h->kr, h->kz);
+    launch_from_padded(h->kz, z, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
     return AMG_OK;
@@ -370,17 +392,19 @@ int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const doubl
     if (!h || !x || !y) fail(AMG_ERR_INVALID, "null argument");
     if (level < 0 || level >= (int)h->L.size()) fail(AMG_ERR_INVALID, "no such level");
     Level& lv = *h->L[level];
+    launch_to_padded(x, lv.t64, lv.n, lv.np, h->stream, h);
     if (precision == AMG_FP64) {
-      level_apply<double>(h, level, x, y);
+      level_apply<double>(h, level, lv.t64.p, lv.r64.p);
     } else if (precision == AMG_FP32) {
       if (!lv.val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with precision FP32");
-      const int64_t n = lv.dofs();
-      launch_to_float(x, lv.t32, n, h->stream, h);
+      const int64_t n4 = lv.dofs4();
+      launch_to_float(lv.t64, lv.t32, n4, h->stream, h);
       level_apply<float>(h, level, lv.t32.p, lv.r32.p);
-      launch_to_double(lv.r32, y, n, h->stream, h);
+      launch_to_double(lv.r32, lv.r64, n4, h->stream, h);
     } else {
       fail(AMG_ERR_INVALID, "unknown precision");
     }
+    launch_from_padded(lv.r64, y, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
     return AMG_OK;
@@ -392,7 +416,11 @@ int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
     if (!h || !x || !b) fail(AMG_ERR_INVALID, "null argument");
     if (level < 0 || level >= (int)h->L.size() - 1)
       fail(AMG_ERR_INVALID, "no smoother on this level");
-    level_smooth<double>(h, level, x, b, direction != 0, false);
+    Level& lv = *h->L[level];
+    launch_to_padded(x, lv.x64, lv.n, lv.np, h->stream, h);
+    launch_to_padded(b, lv.b64, lv.n, lv.np, h->stream, h);
+    level_smooth<double>(h, level, lv.x64.p, lv.b64.p, direction != 0, false);
+    launch_from_padded(lv.x64, x, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
     return AMG_OK;
@@ -410,9 +438,9 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
     const bool f32 = precision == AMG_FP32;
     if (f32 && !h->L[0]->val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with FP32");
     Level& lv = *h->L[op == AMG_OP_PRECOND ? 0 : level];
-    if (op == AMG_OP_PRECOND && (int64_t)h->kr.n < lv.dofs()) {
-      h->kr.alloc(lv.dofs());
-      h->kz.alloc(lv.dofs());
+    if (op == AMG_OP_PRECOND && (int64_t)h->kr.n < lv.dofs4()) {
+      h->kr.alloc(lv.dofs4());
+      h->kz.alloc(lv.dofs4());
       AMG_CUDA(cudaMemsetAsync(h->kr.p, 0, h->kr.bytes(), h->stream));
     }
     auto once = [&]() {
@@ -442,11 +470,11 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
       }
     };
     // vectors: zero x, b = 1 so that the data are finite
-    launch_fill(lv.x64, 0.0, lv.dofs(), h->stream, h);
-    launch_fill(lv.b64, 1.0, lv.dofs(), h->stream, h);
+    launch_fill(lv.x64, 0.0, lv.dofs4(), h->stream, h);
+    launch_fill(lv.b64, 1.0, lv.dofs4(), h->stream, h);
     if (f32) {
-      launch_to_float(lv.x64, lv.x32, lv.dofs(), h->stream, h);
-      launch_to_float(lv.b64, lv.b32, lv.dofs(), h->stream, h);
+      launch_to_float(lv.x64, lv.x32, lv.dofs4(), h->stream, h);
+      launch_to_float(lv.b64, lv.b32, lv.dofs4(), h->stream, h);
     }
     for (int i = 0; i < warmup; ++i) once();
     const int64_t l0 = h->launches;

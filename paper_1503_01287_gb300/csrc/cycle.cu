@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "amg_internal.cuh"
+#include "vec.cuh"
 
 namespace amgp2 {
 
@@ -17,12 +18,13 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
 // One group of G lanes per block row.  Each lane walks the row's blocks with
 // stride G; block values come from the 9 planes (consecutive lanes read
-// consecutive addresses of each plane); the three partial sums are reduced with
-// shuffles inside the group.
+// consecutive addresses of each plane), x_j is one vector load of the padded
+// node; the three partial sums are reduced with shuffles inside the group.
 //   kApply : y_i = (A x)_i
 //   kResid : y_i = b_i - (A x)_i
 //   kGS    : x_i += D_i^{-1} (b_i - (A x)_i)   for the rows listed in `rows`
 //   kJacobi: y_i = x_i + omega D_i^{-1} (b_i - (A x)_i)
+// D^{-1} is stored as 3 padded rows per node (12 values).
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(256) k_block_rows(
     int nrows, const int* __restrict__ rows, const int* __restrict__ rowptr,
@@ -38,7 +40,8 @@ __global__ void __launch_bounds__(256) k_block_rows(
     const int a = ldg(rowptr + i), e = ldg(rowptr + i + 1);
     for (int k = a + lane; k < e; k += G) {
       const int j = ldg(col + k);
-      const T x0 = ldg(x + 3 * j), x1 = ldg(x + 3 * j + 1), x2 = ldg(x + 3 * j + 2);
+      T x0, x1, x2;
+      ld3(x, j, x0, x1, x2);
       const T* v = val + k;
       s0 = fma(ldg(v), x0, s0);
       s0 = fma(ldg(v + nnzb), x1, s0);
@@ -59,24 +62,30 @@ __global__ void __launch_bounds__(256) k_block_rows(
   }
   if (!active || lane != 0) return;
   if (MODE == kApply) {
-    y[3 * i] = s0; y[3 * i + 1] = s1; y[3 * i + 2] = s2;
+    st3(y, i, s0, s1, s2);
     return;
   }
-  const T r0 = b[3 * i] - s0, r1 = b[3 * i + 1] - s1, r2 = b[3 * i + 2] - s2;
+  T b0, b1, b2;
+  ld3(b, i, b0, b1, b2);
+  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
   if (MODE == kResid) {
-    y[3 * i] = r0; y[3 * i + 1] = r1; y[3 * i + 2] = r2;
+    st3(y, i, r0, r1, r2);
     return;
   }
-  const T* d = dinv + 9 * (int64_t)i;
-  const T c0 = d[0] * r0 + d[1] * r1 + d[2] * r2;
-  const T c1 = d[3] * r0 + d[4] * r1 + d[5] * r2;
-  const T c2 = d[6] * r0 + d[7] * r1 + d[8] * r2;
+  const T* d = dinv + 12 * (int64_t)i;
+  T d0, d1, d2;
+  ld3(d, 0, d0, d1, d2);
+  const T c0 = d0 * r0 + d1 * r1 + d2 * r2;
+  ld3(d, 1, d0, d1, d2);
+  const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
+  ld3(d, 2, d0, d1, d2);
+  const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
+  T x0, x1, x2;
+  ld3(x, i, x0, x1, x2);
   if (MODE == kGS) {
-    y[3 * i] = x[3 * i] + c0; y[3 * i + 1] = x[3 * i + 1] + c1; y[3 * i + 2] = x[3 * i + 2] + c2;
+    st3(y, i, x0 + c0, x1 + c1, x2 + c2);
   } else {
-    y[3 * i] = x[3 * i] + omega * c0;
-    y[3 * i + 1] = x[3 * i + 1] + omega * c1;
-    y[3 * i + 2] = x[3 * i + 2] + omega * c2;
+    st3(y, i, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
   }
 }
 
@@ -89,11 +98,13 @@ __global__ void k_restrict(int nc, const int* __restrict__ rrow, const int* __re
     for (int t = rrow[I]; t < rrow[I + 1]; ++t) {
       const int i = rcol[t];
       const T w = rval[t];
-      s0 = fma(w, r[3 * i], s0);
-      s1 = fma(w, r[3 * i + 1], s1);
-      s2 = fma(w, r[3 * i + 2], s2);
+      T r0, r1, r2;
+      ld3(r, i, r0, r1, r2);
+      s0 = fma(w, r0, s0);
+      s1 = fma(w, r1, s1);
+      s2 = fma(w, r2, s2);
     }
-    bc[3 * I] = s0; bc[3 * I + 1] = s1; bc[3 * I + 2] = s2;
+    st3(bc, I, s0, s1, s2);
   }
 }
 
@@ -106,11 +117,15 @@ __global__ void k_prolong(int n, const int* __restrict__ prow, const int* __rest
     for (int q = prow[i]; q < prow[i + 1]; ++q) {
       const int J = pcol[q];
       const T w = pval[q];
-      s0 = fma(w, xc[3 * J], s0);
-      s1 = fma(w, xc[3 * J + 1], s1);
-      s2 = fma(w, xc[3 * J + 2], s2);
+      T c0, c1, c2;
+      ld3(xc, J, c0, c1, c2);
+      s0 = fma(w, c0, s0);
+      s1 = fma(w, c1, s1);
+      s2 = fma(w, c2, s2);
     }
-    x[3 * i] += s0; x[3 * i + 1] += s1; x[3 * i + 2] += s2;
+    T x0, x1, x2;
+    ld3(x, i, x0, x1, x2);
+    st3(x, i, x0 + s0, x1 + s1, x2 + s2);
   }
 }
 
@@ -135,19 +150,25 @@ __global__ void k_prolong1(int n, const int* __restrict__ prow, const int* __res
   }
 }
 
-// x = X b with the FP64 generalised inverse of the coarsest matrix (warp per row)
+// x = X b with the FP64 generalised inverse of the coarsest matrix (warp per row).
+// X is indexed in the unpadded order (3 per node, then pressure); n3 = 3 n.
+__device__ __forceinline__ int pad_index(int j, int n3) {
+  return j < n3 ? 4 * (j / 3) + j % 3 : j + n3 / 3;
+}
+
 template <typename T>
-__global__ void k_coarse_solve(int m, const double* __restrict__ X, const T* __restrict__ b,
-                               T* __restrict__ x) {
+__global__ void k_coarse_solve(int m, int n3, const double* __restrict__ X,
+                               const T* __restrict__ b, T* __restrict__ x) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int i = w; i < m; i += nw) {
     double s = 0.0;
-    for (int j = lane; j < m; j += 32) s = fma(X[(int64_t)i * m + j], (double)b[j], s);
+    for (int j = lane; j < m; j += 32)
+      s = fma(X[(int64_t)i * m + j], (double)b[pad_index(j, n3)], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[i] = (T)s;
+    if (lane == 0) x[pad_index(i, n3)] = (T)s;
   }
 }
 
@@ -180,7 +201,9 @@ __global__ void k_bt_add(int n, const int* __restrict__ row, const int* __restri
       s1 = fma(val[nnz + q], pk, s1);
       s2 = fma(val[2 * nnz + q], pk, s2);
     }
-    y[3 * i] += sign * s0; y[3 * i + 1] += sign * s1; y[3 * i + 2] += sign * s2;
+    T y0, y1, y2;
+    ld3(y, i, y0, y1, y2);
+    st3(y, i, y0 + sign * s0, y1 + sign * s1, y2 + sign * s2);
   }
 }
 
@@ -197,9 +220,11 @@ __global__ void k_pressure_rows(int np, const int* __restrict__ brow, const int*
     T s = T(0);
     for (int q = brow[k]; q < brow[k + 1]; ++q) {
       const int j = bcol[q];
-      s = fma(bval[q], u[3 * j], s);
-      s = fma(bval[bnnz + q], u[3 * j + 1], s);
-      s = fma(bval[2 * bnnz + q], u[3 * j + 2], s);
+      T u0, u1, u2;
+      ld3(u, j, u0, u1, u2);
+      s = fma(bval[q], u0, s);
+      s = fma(bval[bnnz + q], u1, s);
+      s = fma(bval[2 * bnnz + q], u2, s);
     }
     T cp = T(0);
     for (int q = crow[k]; q < crow[k + 1]; ++q) cp = fma(cval[q], p[ccol[q]], cp);
@@ -253,8 +278,9 @@ inline int gridn(int64_t n, int t = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 152 * 16));
 }
 
-// lanes per block row, from the level's average row length
+// lanes per block row: the autotuned value, else from the average row length
 inline int group_for(const Level& lv) {
+  if (lv.group) return lv.group;
   if (lv.avg_row_blocks > 20.0) return 32;
   if (lv.avg_row_blocks > 10.0) return 16;
   if (lv.avg_row_blocks > 5.0) return 8;
@@ -293,12 +319,12 @@ void level_apply(amg_handle* h, int l, const T* x, T* y) {
                            nullptr, T(0));
   h->launches++;
   if (h->saddle && lv.np > 0) {
-    const T* p = x + 3 * lv.n;
+    const T* p = x + 4 * lv.n;
     k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
                                             lv.b_nnz, p, T(1), y);
     k_pressure_rows<T, 0><<<gridn(lv.np), 256, 0, s>>>(
         lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, p, nullptr, y + 3 * lv.n, nullptr, T(0));
+        LvVec<T>::cval(lv), x, p, nullptr, y + 4 * lv.n, nullptr, T(0));
     h->launches += 2;
   }
 }
@@ -311,12 +337,12 @@ void level_residual(amg_handle* h, int l, const T* x, const T* b, T* r) {
                            nullptr, T(0));
   h->launches++;
   if (h->saddle && lv.np > 0) {
-    const T* p = x + 3 * lv.n;
+    const T* p = x + 4 * lv.n;
     k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
                                             lv.b_nnz, p, T(-1), r);
     k_pressure_rows<T, 1><<<gridn(lv.np), 256, 0, s>>>(
         lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, p, b + 3 * lv.n, r + 3 * lv.n, nullptr, T(0));
+        LvVec<T>::cval(lv), x, p, b + 4 * lv.n, r + 4 * lv.n, nullptr, T(0));
     h->launches += 2;
   }
 }
@@ -328,7 +354,7 @@ template <typename T>
 void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_zero) {
   Level& lv = *h->L[l];
   cudaStream_t s = h->stream;
-  const int dofs = lv.dofs();
+  const int dofs = lv.dofs4();
   if (x_is_zero) {
     k_zero<T><<<gridn(dofs), 256, 0, s>>>(x, dofs);
     h->launches++;
@@ -340,19 +366,19 @@ void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_z
     // u <- u + omega D^{-1} (f - A u - B^T p)   (M_A = damped block Jacobi)
     T* t = LvVec<T>::t(lv);
     T* r = LvVec<T>::r(lv);
-    const T* p = x + 3 * lv.n;
+    const T* p = x + 4 * lv.n;
     // r_u = f - B^T p, then t_u = u + omega D^{-1} (r_u - A u)
-    k_copyT<T><<<gridn(3 * lv.n), 256, 0, s>>>(b, r, 3 * (int64_t)lv.n);
+    k_copyT<T><<<gridn(4 * lv.n), 256, 0, s>>>(b, r, 4 * (int64_t)lv.n);
     k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
                                             lv.b_nnz, p, T(-1), r);
     launch_rows_g<T, kJacobi>(G, s, lv.n, nullptr, lv, val, x, r, t, dinv, (T)h->opt.omega);
-    k_copyT<T><<<gridn(3 * lv.n), 256, 0, s>>>(t, x, 3 * (int64_t)lv.n);
+    k_copyT<T><<<gridn(4 * lv.n), 256, 0, s>>>(t, x, 4 * (int64_t)lv.n);
     // p <- p + omega_p S_D^{-1} (B u_new - C p - g)
     k_pressure_rows<T, 2><<<gridn(lv.np), 256, 0, s>>>(
         lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, x + 3 * lv.n, b + 3 * lv.n, t + 3 * lv.n, LvVec<T>::schur(lv),
+        LvVec<T>::cval(lv), x, x + 4 * lv.n, b + 4 * lv.n, t + 4 * lv.n, LvVec<T>::schur(lv),
         (T)h->opt.omega_p);
-    k_copyT<T><<<gridn(lv.np), 256, 0, s>>>(t + 3 * lv.n, x + 3 * lv.n, lv.np);
+    k_copyT<T><<<gridn(lv.np), 256, 0, s>>>(t + 4 * lv.n, x + 4 * lv.n, lv.np);
     h->launches += 6;
     return;
   }
@@ -374,7 +400,8 @@ void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_z
 template <typename T>
 static void coarse_solve(amg_handle* h, const T* b, T* x) {
   const int m = h->coarse_m;
-  k_coarse_solve<T><<<gridn((int64_t)m * 32), 256, 0, h->stream>>>(m, h->coarse_inv, b, x);
+  const int n3 = 3 * h->L.back()->n;
+  k_coarse_solve<T><<<gridn((int64_t)m * 32), 256, 0, h->stream>>>(m, n3, h->coarse_inv, b, x);
   h->launches++;
 }
 
@@ -387,7 +414,7 @@ static void restrict_to(amg_handle* h, int l, const T* r, T* bc) {
   h->launches++;
   if (h->saddle && nx.np > 0) {
     k_restrict1<T><<<gridn(nx.np), 256, 0, s>>>(nx.np, lv.ht_rowptr, lv.ht_col,
-                                                 LvVec<T>::htval(lv), r + 3 * lv.n, bc + 3 * nx.n);
+                                                 LvVec<T>::htval(lv), r + 4 * lv.n, bc + 4 * nx.n);
     h->launches++;
   }
 }
@@ -401,7 +428,7 @@ static void prolong_add(amg_handle* h, int l, const T* xc, T* x) {
   h->launches++;
   if (h->saddle && lv.np > 0) {
     k_prolong1<T><<<gridn(lv.np), 256, 0, s>>>(lv.np, lv.h_rowptr, lv.h_col, LvVec<T>::hval(lv),
-                                               xc + 3 * nx.n, x + 3 * lv.n);
+                                               xc + 4 * nx.n, x + 4 * lv.n);
     h->launches++;
   }
 }
@@ -423,7 +450,7 @@ static void cycle_rec(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
     zero = false;
   }
   if (zero) {   // no pre-smoothing: x is still the zero initial guess
-    k_zero<T><<<gridn(lv.dofs()), 256, 0, h->stream>>>(x, lv.dofs());
+    k_zero<T><<<gridn(lv.dofs4()), 256, 0, h->stream>>>(x, lv.dofs4());
     h->launches++;
   }
   T* r = LvVec<T>::r(lv);
@@ -455,7 +482,7 @@ void precondition_device<double>(amg_handle* h, const double* r, double* z) {
 template <>
 void precondition_device<float>(amg_handle* h, const double* r, double* z) {
   Level& lv = *h->L[0];
-  const int64_t n = lv.dofs();
+  const int64_t n = lv.dofs4();
   launch_to_float(r, lv.b32, n, h->stream, h);
   for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
     cycle_rec<float>(h, 0, lv.x32.p, lv.b32.p, c == 0);
@@ -472,6 +499,44 @@ void level_transfer(amg_handle* h, int l, bool restrict_, bool f32) {
     if (restrict_) restrict_to<double>(h, l, lv.r64.p, nx.b64.p);
     else prolong_add<double>(h, l, nx.x64.p, lv.x64.p);
   }
+}
+
+// Times the operator kernel of every level with 4, 8, 16 and 32 lanes per block
+// row (in the precision the cycle uses) and keeps the fastest.  The row kernels
+// of one level share its access pattern, so one choice serves all modes.
+void autotune_levels(amg_handle* h) {
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  const bool f32 = h->opt.precision == AMG_FP32;
+  for (auto& lp : h->L) {
+    Level& lv = *lp;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int G : {4, 8, 16, 32}) {
+      const int reps = 5;
+      for (int r = 0; r < reps + 2; ++r) {
+        if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32)
+          launch_rows_g<float, kApply>(G, s, lv.n, nullptr, lv, lv.val32.p, lv.x32.p, nullptr,
+                                       lv.r32.p, nullptr, 0.f);
+        else
+          launch_rows_g<double, kApply>(G, s, lv.n, nullptr, lv, lv.val.p, lv.x64.p, nullptr,
+                                        lv.r64.p, nullptr, 0.0);
+      }
+      AMG_CUDA(cudaEventRecord(e1, s));
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      h->launches += reps + 2;
+      if (ms < best_ms) { best_ms = ms; best = G; }
+    }
+    lv.group = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 template void level_apply<double>(amg_handle*, int, const double*, double*);

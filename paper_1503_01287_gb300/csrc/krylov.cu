@@ -192,7 +192,7 @@ void precond(amg_handle* h, const double* r, double* z) {
 void project_pressure(amg_handle* h, Ctx& c, double* v) {
   if (h->kind != AMG_STOKES || !h->pmass.p) return;
   const Level& lv = *h->L[0];
-  double* p = v + 3 * lv.n;
+  double* p = v + 4 * lv.n;
   const int64_t np = lv.np;
   c.dots(h->pmass.p, p, S_T0, nullptr, nullptr, np);
   k_shift<<<gridr(np), 256, 0, c.s>>>(np, p, h->scal.p + S_T0, h->pmass_sum);
@@ -425,13 +425,18 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
 
 }  // namespace
 
-int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st) {
+int solve_device(amg_handle* h, const double* b_user, double* x_user, double tol,
+                 amg_stats* st) {
   const Level& lv = *h->L[0];
-  const int64_t n = lv.dofs();
+  const int64_t n = lv.dofs4();
   Ctx c{h, h->stream, n};
   auto ensure = [&](DBuf<double>& v, int64_t cnt) {
-    if ((int64_t)v.n < cnt) v.alloc(cnt);
+    if ((int64_t)v.n < cnt) {
+      v.alloc(cnt);
+      AMG_CUDA(cudaMemsetAsync(v.p, 0, v.bytes(), h->stream));
+    }
   };
+  ensure(h->kb, n); ensure(h->kx, n);
   ensure(h->kr, n); ensure(h->kz, n); ensure(h->kp, n); ensure(h->kq, n); ensure(h->kw, n);
   ensure(h->red, (int64_t)kReduceBlocks * kMaxDots);
   ensure(h->scal, 64);
@@ -441,23 +446,33 @@ int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stat
                        : (h->opt.precision == AMG_FP32 ? AMG_KRYLOV_FCG : AMG_KRYLOV_PCG);
   if (h->saddle && (krylov == AMG_KRYLOV_PCG || krylov == AMG_KRYLOV_FCG))
     fail(AMG_ERR_UNSUPPORTED, "CG needs an SPD system; use FGMRES for saddle kinds");
+  launch_to_padded(b_user, h->kb, lv.n, lv.np, h->stream, h);
+  const double* b = h->kb;
+  double* x = h->kx;
+  int rc;
   switch (krylov) {
     case AMG_KRYLOV_PCG:
-      return solve_cg(h, c, b, x, tol, false, st);
+      rc = solve_cg(h, c, b, x, tol, false, st);
+      break;
     case AMG_KRYLOV_FCG:
       ensure(h->kro, n);
-      return solve_cg(h, c, b, x, tol, true, st);
+      rc = solve_cg(h, c, b, x, tol, true, st);
+      break;
     case AMG_KRYLOV_NONE:
-      return solve_amg(h, c, b, x, tol, st);
+      rc = solve_amg(h, c, b, x, tol, st);
+      break;
     case AMG_KRYLOV_FGMRES: {
       const int m = std::max(1, std::min(h->opt.gmres_restart, kMaxDots - 2));
       ensure(h->gm_V, (int64_t)(m + 1) * n);
       ensure(h->gm_Z, (int64_t)m * n);
-      return solve_fgmres(h, c, b, x, tol, st);
+      rc = solve_fgmres(h, c, b, x, tol, st);
+      break;
     }
     default:
       fail(AMG_ERR_INVALID, "unknown Krylov method");
   }
+  launch_from_padded(x, x_user, lv.n, lv.np, h->stream, h);
+  return rc;
 }
 
 }  // namespace amgp2

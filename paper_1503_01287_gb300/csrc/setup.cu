@@ -188,6 +188,38 @@ static inline int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
 }
 
+namespace {
+__global__ void k_to_padded(const double* __restrict__ u, double* __restrict__ p, int n, int np) {
+  const int64_t tot = 4 * (int64_t)n + np;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < 4 * (int64_t)n) {
+      const int64_t node = k >> 2, c = k & 3;
+      p[k] = c < 3 ? u[3 * node + c] : 0.0;
+    } else {
+      p[k] = u[k - n];
+    }
+  }
+}
+__global__ void k_from_padded(const double* __restrict__ p, double* __restrict__ u, int n, int np) {
+  const int64_t tot = 3 * (int64_t)n + np;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < 3 * (int64_t)n) u[k] = p[4 * (k / 3) + k % 3];
+    else u[k] = p[k + n];
+  }
+}
+}  // namespace
+
+void launch_to_padded(const double* u, double* p, int n, int np, cudaStream_t s, amg_handle* h) {
+  k_to_padded<<<grid_for(4 * (int64_t)n + np), 256, 0, s>>>(u, p, n, np);
+  h->launches++;
+}
+void launch_from_padded(const double* p, double* u, int n, int np, cudaStream_t s, amg_handle* h) {
+  k_from_padded<<<grid_for(3 * (int64_t)n + np), 256, 0, s>>>(p, u, n, np);
+  h->launches++;
+}
+
 void launch_copy(const double* a, double* b, int64_t n, cudaStream_t s, amg_handle* h) {
   if (n <= 0) return;
   k_copy<<<grid_for(n), 256, 0, s>>>(a, b, n);
@@ -579,16 +611,19 @@ __global__ void k_dinv(int n, const int* __restrict__ rowptr, const int* __restr
     double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
     if (!(fabs(det) > 0.0) || !isfinite(det)) { atomicOr(flag, 64); continue; }
     double r = 1.0 / det;
-    double* o = dinv + 9 * (int64_t)i;
+    double* o = dinv + 12 * (int64_t)i;
     o[0] = c00 * r;
     o[1] = (a[2] * a[7] - a[1] * a[8]) * r;
     o[2] = (a[1] * a[5] - a[2] * a[4]) * r;
-    o[3] = c01 * r;
-    o[4] = (a[0] * a[8] - a[2] * a[6]) * r;
-    o[5] = (a[2] * a[3] - a[0] * a[5]) * r;
-    o[6] = c02 * r;
-    o[7] = (a[1] * a[6] - a[0] * a[7]) * r;
-    o[8] = (a[0] * a[4] - a[1] * a[3]) * r;
+    o[3] = 0.0;
+    o[4] = c01 * r;
+    o[5] = (a[0] * a[8] - a[2] * a[6]) * r;
+    o[6] = (a[2] * a[3] - a[0] * a[5]) * r;
+    o[7] = 0.0;
+    o[8] = c02 * r;
+    o[9] = (a[1] * a[6] - a[0] * a[7]) * r;
+    o[10] = (a[0] * a[4] - a[1] * a[3]) * r;
+    o[11] = 0.0;
   }
 }
 
@@ -606,9 +641,9 @@ __global__ void k_schur_diag(int np, const int* __restrict__ brow, const int* __
     for (int q = brow[k]; q < brow[k + 1]; ++q) {
       int j = bcol[q];
       double b0 = bval[q], b1 = bval[bnnz + q], b2 = bval[2 * bnnz + q];
-      const double* d = dinv + 9 * (int64_t)j;
-      acc += b0 * (d[0] * b0 + d[1] * b1 + d[2] * b2) + b1 * (d[3] * b0 + d[4] * b1 + d[5] * b2) +
-             b2 * (d[6] * b0 + d[7] * b1 + d[8] * b2);
+      const double* d = dinv + 12 * (int64_t)j;
+      acc += b0 * (d[0] * b0 + d[1] * b1 + d[2] * b2) + b1 * (d[4] * b0 + d[5] * b1 + d[6] * b2) +
+             b2 * (d[8] * b0 + d[9] * b1 + d[10] * b2);
     }
     out[k] = s + omega * acc;
   }
@@ -988,7 +1023,7 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
   cudaStream_t s = h->stream;
   int n = lv.n;
   row_stats(h, lv);
-  lv.dinv.alloc(9 * (size_t)std::max(n, 1));
+  lv.dinv.alloc(12 * (size_t)std::max(n, 1));
   Flag f(h);
   f.reset();
   k_dinv<<<grid_for(n), 256, 0, s>>>(n, lv.rowptr, lv.col, lv.val, lv.nnzb, lv.dinv, h->flag);
@@ -997,20 +1032,28 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
   if (f.read()) fail(AMG_ERR_BREAKDOWN, "singular or non-finite 3x3 diagonal block");
   if (!coarsest && !h->saddle) colour_level(h, lv);
   bool fp32 = h->opt.precision == AMG_FP32;
-  int dofs = lv.dofs();
-  lv.x64.alloc(dofs); lv.b64.alloc(dofs); lv.r64.alloc(dofs); lv.t64.alloc(dofs);
+  const int dofs = lv.dofs4();
+  auto zalloc64 = [&](DBuf<double>& v) {
+    v.alloc(std::max(dofs, 1));
+    AMG_CUDA(cudaMemsetAsync(v.p, 0, v.bytes(), s));
+  };
+  auto zalloc32 = [&](DBuf<float>& v) {
+    v.alloc(std::max(dofs, 1));
+    AMG_CUDA(cudaMemsetAsync(v.p, 0, v.bytes(), s));
+  };
+  zalloc64(lv.x64); zalloc64(lv.b64); zalloc64(lv.r64); zalloc64(lv.t64);
   if (fp32) {
     lv.val32.alloc(9 * (size_t)std::max<int64_t>(lv.nnzb, 1));
     launch_to_float(lv.val, lv.val32, 9 * lv.nnzb, s, h);
-    lv.dinv32.alloc(9 * (size_t)std::max(n, 1));
-    launch_to_float(lv.dinv, lv.dinv32, 9 * (int64_t)n, s, h);
+    lv.dinv32.alloc(12 * (size_t)std::max(n, 1));
+    launch_to_float(lv.dinv, lv.dinv32, 12 * (int64_t)n, s, h);
     if (!coarsest) {
       lv.p_val32.alloc(std::max<int64_t>(lv.p_nnz, 1));
       launch_to_float(lv.p_val, lv.p_val32, lv.p_nnz, s, h);
       lv.r_val32.alloc(std::max<int64_t>(lv.p_nnz, 1));
       launch_to_float(lv.r_val, lv.r_val32, lv.p_nnz, s, h);
     }
-    lv.x32.alloc(dofs); lv.b32.alloc(dofs); lv.r32.alloc(dofs); lv.t32.alloc(dofs);
+    zalloc32(lv.x32); zalloc32(lv.b32); zalloc32(lv.r32); zalloc32(lv.t32);
   }
   if (h->saddle) {
     lv.schur.alloc(std::max(lv.np, 1));
@@ -1150,6 +1193,7 @@ void build_hierarchy(amg_handle* h, const amg_matrix* m, const int32_t* tags) {
   }
   for (size_t l = 0; l < h->L.size(); ++l) finish_level(h, *h->L[l], l + 1 == h->L.size());
   factor_coarsest(h);
+  autotune_levels(h);
   AMG_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -1,0 +1,47 @@
+// Node vectors of the cycle are stored 4 values per node (x, y, z, 0) so that a
+// node is one aligned 16-byte (FP32) or 32-byte (FP64) access: the gather of
+// x_j in a block row is a single vector load.  The pressure part (saddle
+// systems) follows the 4n velocity entries as plain scalars.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace amgp2 {
+
+__device__ __forceinline__ void ld3(const float* p, int j, float& a, float& b, float& c) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + j);
+  a = v.x; b = v.y; c = v.z;
+}
+
+__device__ __forceinline__ void ld3(const double* p, int j, double& a, double& b, double& c) {
+  double w;
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+      : "=d"(a), "=d"(b), "=d"(c), "=d"(w)
+      : "l"(p + 4 * (size_t)j));
+}
+
+// coherent variant for vectors written earlier in the same kernel by other threads
+__device__ __forceinline__ void ld3c(const float* p, int j, float& a, float& b, float& c) {
+  const float4 v = reinterpret_cast<const float4*>(p)[j];
+  a = v.x; b = v.y; c = v.z;
+}
+
+__device__ __forceinline__ void ld3c(const double* p, int j, double& a, double& b, double& c) {
+  double w;
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(a), "=d"(b), "=d"(c), "=d"(w)
+               : "l"(p + 4 * (size_t)j)
+               : "memory");
+}
+
+__device__ __forceinline__ void st3(float* p, int j, float a, float b, float c) {
+  reinterpret_cast<float4*>(p)[j] = make_float4(a, b, c, 0.f);
+}
+
+__device__ __forceinline__ void st3(double* p, int j, double a, double b, double c) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p + 4 * (size_t)j), "d"(a),
+               "d"(b), "d"(c), "d"(0.0)
+               : "memory");
+}
+
+}  // namespace amgp2
