@@ -76,6 +76,7 @@ struct Level {
   int max_row_blocks = 0;
   double avg_row_blocks = 0.0;
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
+  int group_gs = 0;     // the same for the colour-subset Gauss-Seidel kernel
 
   // transfer to level+1 (absent on the coarsest level)
   DBuf<int> state, cid;

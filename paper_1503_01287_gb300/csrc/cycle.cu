@@ -389,10 +389,11 @@ void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_z
     h->launches += 2;
     return;
   }
+  const int Ggs = lv.group_gs ? lv.group_gs : G;
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
-    launch_rows_g<T, kGS>(G, s, e - a, lv.colour_rows.p + a, lv, val, x, b, x, dinv, T(0));
+    launch_rows_g<T, kGS>(Ggs, s, e - a, lv.colour_rows.p + a, lv, val, x, b, x, dinv, T(0));
     h->launches++;
   }
 }
@@ -534,6 +535,25 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group = best;
+    if (lv.ncolours == 0 || h->saddle || h->opt.smoother != AMG_SMOOTHER_GS) continue;
+    // one full colour sweep per candidate
+    best = 0;
+    best_ms = 1e30f;
+    for (int G : {4, 8, 16, 32}) {
+      lv.group_gs = G;
+      for (int r = 0; r < 3; ++r) {
+        if (r == 1) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) level_smooth<float>(h, (int)(&lp - &h->L[0]), lv.x32.p, lv.b32.p, false, false);
+        else level_smooth<double>(h, (int)(&lp - &h->L[0]), lv.x64.p, lv.b64.p, false, false);
+      }
+      AMG_CUDA(cudaEventRecord(e1, s));
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = G; }
+    }
+    lv.group_gs = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

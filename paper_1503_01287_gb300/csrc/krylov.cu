@@ -329,6 +329,8 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   const int m = std::max(1, std::min(h->opt.gmres_restart, kMaxDots - 2));
   double* V = h->gm_V;
   double* Z = h->gm_Z;
+  // basis vectors start on 64-byte boundaries: node loads are 32-byte vector accesses
+  const int64_t ld = (n + 7) / 8 * 8;
   double* w = h->kw;
   AMG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   c.dots(b, b, S_BB);
@@ -343,7 +345,7 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   bool conv = false;
   auto mdot = [&](int cnt, const double* vec) {
     int nb = gridr(n);
-    k_mdot<<<nb, 256, 0, s>>>(n, cnt, V, n, vec, h->red);
+    k_mdot<<<nb, 256, 0, s>>>(n, cnt, V, ld, vec, h->red);
     k_final<<<1, 256, 0, s>>>(h->red, nb, cnt, hcol.p);
     h->launches += 2;
   };
@@ -362,14 +364,14 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
     g[0] = beta;
     int jused = 0;
     for (int j = 0; j < m; ++j) {
-      double* zj = Z + (int64_t)j * n;
-      precond(h, V + (int64_t)j * n, zj);
+      double* zj = Z + (int64_t)j * ld;
+      precond(h, V + (int64_t)j * ld, zj);
       project_pressure(h, c, zj);
       apply_K(h, zj, w);
       // classical Gram-Schmidt, applied twice (CGS2)
       for (int pass = 0; pass < 2; ++pass) {
         mdot(j + 1, w);
-        k_basis_sub<<<gridr(n), 256, 0, s>>>(n, j + 1, V, n, hcol.p, w);
+        k_basis_sub<<<gridr(n), 256, 0, s>>>(n, j + 1, V, ld, hcol.p, w);
         h->launches++;
         AMG_CUDA(cudaMemcpyAsync(hc.data(), hcol.p, (j + 1) * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
@@ -380,7 +382,7 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
       const double hn = std::sqrt(read_scalar(h, S_T0));
       H[(j + 1) * m + j] = hn;
       if (hn != 0.0) {
-        k_scale<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / hn, V + (int64_t)(j + 1) * n);
+        k_scale<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / hn, V + (int64_t)(j + 1) * ld);
         h->launches++;
       }
       for (int i = 0; i < j; ++i) {
@@ -412,7 +414,7 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
       y[i] = t / H[i * m + i];
     }
     AMG_CUDA(cudaMemcpyAsync(ydev.p, y.data(), jused * sizeof(double), cudaMemcpyHostToDevice, s));
-    k_basis_add<<<gridr(n), 256, 0, s>>>(n, jused, Z, n, ydev.p, x);
+    k_basis_add<<<gridr(n), 256, 0, s>>>(n, jused, Z, ld, ydev.p, x);
     h->launches++;
     AMG_CUDA(cudaStreamSynchronize(s));
   }
@@ -463,8 +465,9 @@ int solve_device(amg_handle* h, const double* b_user, double* x_user, double tol
       break;
     case AMG_KRYLOV_FGMRES: {
       const int m = std::max(1, std::min(h->opt.gmres_restart, kMaxDots - 2));
-      ensure(h->gm_V, (int64_t)(m + 1) * n);
-      ensure(h->gm_Z, (int64_t)m * n);
+      const int64_t ld = (n + 7) / 8 * 8;
+      ensure(h->gm_V, (int64_t)(m + 1) * ld);
+      ensure(h->gm_Z, (int64_t)m * ld);
       rc = solve_fgmres(h, c, b, x, tol, st);
       break;
     }
