@@ -125,7 +125,9 @@ typedef struct amg_options {
                                0: graph of the whole matrix (Table 2, row 3)    */
   int32_t max_iterations;   /* Krylov iteration limit (default 1000)            */
   int32_t use_graphs;       /* 1: replay each Krylov iteration as a CUDA graph  */
-  int32_t verbose;
+  int32_t cluster_from;     /* coarse levels from this level down run as one
+                               thread-block-cluster launch: -1 chosen by timing
+                               at setup (default), 0 never, k >= 1 from level k */
   double omega;             /* block Jacobi damping (default 0.5)               */
   double omega_p;           /* sGS pressure step omega (default 0.125)          */
 } amg_options;

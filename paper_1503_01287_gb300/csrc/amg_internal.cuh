@@ -142,6 +142,11 @@ struct amg_handle {
   double setup_ms = 0.0;
   cudaGraphExec_t cycle_graph = nullptr;  // one preconditioner application
   bool cycle_graph_valid = false;
+  // coarse levels from `sub_from` down run as one cluster launch (0: off)
+  int sub_from = 0;
+  int sub_cluster = 0;                    // CTAs in the cluster (0: clusters unavailable)
+  amgp2::DBuf<unsigned char> sub_ph32, sub_ph64;   // recorded phase lists
+  int sub_n32 = 0, sub_n64 = 0;
   ~amg_handle();
 };
 
@@ -175,8 +180,11 @@ void precondition_device(amg_handle* h, const double* r, double* z);
 // the level work vectors, in FP32 or FP64
 void level_transfer(amg_handle* h, int l, bool restrict_, bool f32);
 
-// picks the lanes-per-row of each level by timing the operator kernel
+// picks the lanes-per-row of each level by timing the operator kernel and the
+// level from which the cycle runs as one cluster launch
 void autotune_levels(amg_handle* h);
+// records the cluster sub-cycle from level `from` (0 disables it)
+void set_subcycle(amg_handle* h, int from);
 
 // krylov (krylov.cu)
 int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st);

@@ -72,7 +72,7 @@ void amg_default_options(amg_options* o) {
   o->separate = 1;
   o->max_iterations = 1000;
   o->use_graphs = 1;
-  o->verbose = 0;
+  o->cluster_from = -1;
   o->omega = 0.5;
   o->omega_p = 0.125;
 }

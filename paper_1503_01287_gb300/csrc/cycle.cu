@@ -2,10 +2,22 @@
 // application, residual, multicolour block Gauss-Seidel, damped block Jacobi),
 // transfers P / R = P^T, the dense coarsest solve, and the saddle-point
 // segregated Gauss-Seidel sweep of Eq. (uzsm).
+//
+// Every operation has one __device__ body.  The cycle is written once against
+// an emitter that either launches one kernel per operation or records it as a
+// phase.  The recorded phases of the small coarse levels run in one launch of a
+// thread-block cluster, separated by cluster barriers, so both paths perform the
+// same operations in the same order.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "amg_internal.cuh"
 #include "vec.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace amgp2 {
 
@@ -16,90 +28,127 @@ enum RowMode { kApply = 0, kResid = 1, kGS = 2, kJacobi = 3 };
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-// One group of G lanes per block row.  Each lane walks the row's blocks with
-// stride G; block values come from the 9 planes (consecutive lanes read
-// consecutive addresses of each plane), x_j is one vector load of the padded
-// node; the three partial sums are reduced with shuffles inside the group.
+// Vector loads.  COH = false: read-only path (vectors written by earlier
+// kernels).  COH = true: through L2 only, for vectors written earlier in the
+// same cluster launch by other CTAs.
+template <bool COH>
+struct VL;
+template <>
+struct VL<false> {
+  template <typename T>
+  __device__ static void node(const T* p, int j, T& a, T& b, T& c) { ld3(p, j, a, b, c); }
+  template <typename T>
+  __device__ static T one(const T* p) { return __ldg(p); }
+};
+template <>
+struct VL<true> {
+  __device__ static void node(const float* p, int j, float& a, float& b, float& c) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p) + j);
+    a = v.x; b = v.y; c = v.z;
+  }
+  __device__ static void node(const double* p, int j, double& a, double& b, double& c) {
+    double w;
+    asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];"
+                 : "=d"(a), "=d"(b), "=d"(c), "=d"(w)
+                 : "l"(p + 4 * (size_t)j)
+                 : "memory");
+  }
+  template <typename T>
+  __device__ static T one(const T* p) { return __ldcg(p); }
+};
+
+// ------------------------------------------------------------------- bodies
+
+// One group of G lanes per block row, 32/G rows per warp, warp-uniform loop.
+// Each lane walks the row's blocks with stride G; block values come from the 9
+// planes (consecutive lanes read consecutive addresses of each plane), x_j is
+// one vector load of the padded node; the three partial sums are reduced with
+// shuffles inside the group.
 //   kApply : y_i = (A x)_i
 //   kResid : y_i = b_i - (A x)_i
 //   kGS    : x_i += D_i^{-1} (b_i - (A x)_i)   for the rows listed in `rows`
 //   kJacobi: y_i = x_i + omega D_i^{-1} (b_i - (A x)_i)
 // D^{-1} is stored as 3 padded rows per node (12 values).
-template <typename T, int G, int MODE>
-__global__ void __launch_bounds__(256) k_block_rows(
-    int nrows, const int* __restrict__ rows, const int* __restrict__ rowptr,
-    const int* __restrict__ col, const T* __restrict__ val, int64_t nnzb, const T* x,
-    const T* __restrict__ b, T* y, const T* __restrict__ dinv, T omega) {
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const int lane = threadIdx.x & (G - 1);
-  const bool active = g < nrows;
-  int i = 0;
-  T s0 = T(0), s1 = T(0), s2 = T(0);
-  if (active) {
-    i = rows ? ldg(rows + g) : g;
-    const int a = ldg(rowptr + i), e = ldg(rowptr + i + 1);
-    for (int k = a + lane; k < e; k += G) {
-      const int j = ldg(col + k);
-      T x0, x1, x2;
-      ld3(x, j, x0, x1, x2);
-      const T* v = val + k;
-      s0 = fma(ldg(v), x0, s0);
-      s0 = fma(ldg(v + nnzb), x1, s0);
-      s0 = fma(ldg(v + 2 * nnzb), x2, s0);
-      s1 = fma(ldg(v + 3 * nnzb), x0, s1);
-      s1 = fma(ldg(v + 4 * nnzb), x1, s1);
-      s1 = fma(ldg(v + 5 * nnzb), x2, s1);
-      s2 = fma(ldg(v + 6 * nnzb), x0, s2);
-      s2 = fma(ldg(v + 7 * nnzb), x1, s2);
-      s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+template <typename T, int G, int MODE, bool COH>
+__device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ rows,
+                                          const int* __restrict__ rowptr,
+                                          const int* __restrict__ col,
+                                          const T* __restrict__ val, int64_t nnzb, const T* x,
+                                          const T* b, T* y, const T* __restrict__ dinv,
+                                          T omega, int warp, int nwarps) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / G, gl = lane & (G - 1);
+  for (int base = warp * RPW; base < nrows; base += nwarps * RPW) {
+    const int g = base + sub;
+    const bool active = g < nrows;
+    int i = 0;
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    if (active) {
+      i = rows ? ldg(rows + g) : g;
+      const int a = ldg(rowptr + i), e = ldg(rowptr + i + 1);
+      for (int k = a + gl; k < e; k += G) {
+        const int j = ldg(col + k);
+        T x0, x1, x2;
+        VL<COH>::node(x, j, x0, x1, x2);
+        const T* v = val + k;
+        s0 = fma(ldg(v), x0, s0);
+        s0 = fma(ldg(v + nnzb), x1, s0);
+        s0 = fma(ldg(v + 2 * nnzb), x2, s0);
+        s1 = fma(ldg(v + 3 * nnzb), x0, s1);
+        s1 = fma(ldg(v + 4 * nnzb), x1, s1);
+        s1 = fma(ldg(v + 5 * nnzb), x2, s1);
+        s2 = fma(ldg(v + 6 * nnzb), x0, s2);
+        s2 = fma(ldg(v + 7 * nnzb), x1, s2);
+        s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+      }
     }
-  }
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  }
-  if (!active || lane != 0) return;
-  if (MODE == kApply) {
-    st3(y, i, s0, s1, s2);
-    return;
-  }
-  T b0, b1, b2;
-  ld3(b, i, b0, b1, b2);
-  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
-  if (MODE == kResid) {
-    st3(y, i, r0, r1, r2);
-    return;
-  }
-  const T* d = dinv + 12 * (int64_t)i;
-  T d0, d1, d2;
-  ld3(d, 0, d0, d1, d2);
-  const T c0 = d0 * r0 + d1 * r1 + d2 * r2;
-  ld3(d, 1, d0, d1, d2);
-  const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
-  ld3(d, 2, d0, d1, d2);
-  const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
-  T x0, x1, x2;
-  ld3(x, i, x0, x1, x2);
-  if (MODE == kGS) {
-    st3(y, i, x0 + c0, x1 + c1, x2 + c2);
-  } else {
-    st3(y, i, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (!active || gl != 0) continue;
+    if (MODE == kApply) {
+      st3(y, i, s0, s1, s2);
+      continue;
+    }
+    T b0, b1, b2;
+    VL<COH>::node(b, i, b0, b1, b2);
+    const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+    if (MODE == kResid) {
+      st3(y, i, r0, r1, r2);
+      continue;
+    }
+    const T* d = dinv + 12 * (int64_t)i;
+    T d0, d1, d2;
+    ld3(d, 0, d0, d1, d2);
+    const T c0 = d0 * r0 + d1 * r1 + d2 * r2;
+    ld3(d, 1, d0, d1, d2);
+    const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
+    ld3(d, 2, d0, d1, d2);
+    const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
+    T x0, x1, x2;
+    VL<COH>::node(x, i, x0, x1, x2);
+    if (MODE == kGS) st3(y, i, x0 + c0, x1 + c1, x2 + c2);
+    else st3(y, i, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
   }
 }
 
 // R = P^T gather: bc_I = sum_t w_t r_{i_t} (3 components, same weight)
-template <typename T>
-__global__ void k_restrict(int nc, const int* __restrict__ rrow, const int* __restrict__ rcol,
-                           const T* __restrict__ rval, const T* __restrict__ r, T* __restrict__ bc) {
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+template <typename T, bool COH>
+__device__ __forceinline__ void restrict_body(int nc, const int* __restrict__ rrow,
+                                              const int* __restrict__ rcol,
+                                              const T* __restrict__ rval, const T* r, T* bc,
+                                              int tid, int nthr) {
+  for (int I = tid; I < nc; I += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int t = rrow[I]; t < rrow[I + 1]; ++t) {
       const int i = rcol[t];
       const T w = rval[t];
       T r0, r1, r2;
-      ld3(r, i, r0, r1, r2);
+      VL<COH>::node(r, i, r0, r1, r2);
       s0 = fma(w, r0, s0);
       s1 = fma(w, r1, s1);
       s2 = fma(w, r2, s2);
@@ -109,135 +158,304 @@ __global__ void k_restrict(int nc, const int* __restrict__ rrow, const int* __re
 }
 
 // x_i += sum_q P_iq xc_q
-template <typename T>
-__global__ void k_prolong(int n, const int* __restrict__ prow, const int* __restrict__ pcol,
-                          const T* __restrict__ pval, const T* __restrict__ xc, T* __restrict__ x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+template <typename T, bool COH>
+__device__ __forceinline__ void prolong_body(int n, const int* __restrict__ prow,
+                                             const int* __restrict__ pcol,
+                                             const T* __restrict__ pval, const T* xc, T* x,
+                                             int tid, int nthr) {
+  for (int i = tid; i < n; i += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int q = prow[i]; q < prow[i + 1]; ++q) {
       const int J = pcol[q];
       const T w = pval[q];
       T c0, c1, c2;
-      ld3(xc, J, c0, c1, c2);
+      VL<COH>::node(xc, J, c0, c1, c2);
       s0 = fma(w, c0, s0);
       s1 = fma(w, c1, s1);
       s2 = fma(w, c2, s2);
     }
     T x0, x1, x2;
-    ld3(x, i, x0, x1, x2);
+    VL<COH>::node(x, i, x0, x1, x2);
     st3(x, i, x0 + s0, x1 + s1, x2 + s2);
   }
 }
 
-// scalar versions for the pressure (H, H^T)
-template <typename T>
-__global__ void k_restrict1(int nc, const int* __restrict__ rrow, const int* __restrict__ rcol,
-                            const T* __restrict__ rval, const T* __restrict__ r, T* __restrict__ bc) {
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+// scalar versions for the pressure (H^T restriction, H prolongation)
+template <typename T, bool COH>
+__device__ __forceinline__ void restrict1_body(int nc, const int* __restrict__ rrow,
+                                               const int* __restrict__ rcol,
+                                               const T* __restrict__ rval, const T* r, T* bc,
+                                               int tid, int nthr) {
+  for (int I = tid; I < nc; I += nthr) {
     T s = T(0);
-    for (int t = rrow[I]; t < rrow[I + 1]; ++t) s = fma(rval[t], r[rcol[t]], s);
+    for (int t = rrow[I]; t < rrow[I + 1]; ++t) s = fma(rval[t], VL<COH>::one(r + rcol[t]), s);
     bc[I] = s;
   }
 }
 
-template <typename T>
-__global__ void k_prolong1(int n, const int* __restrict__ prow, const int* __restrict__ pcol,
-                           const T* __restrict__ pval, const T* __restrict__ xc, T* __restrict__ x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+template <typename T, bool COH>
+__device__ __forceinline__ void prolong1_body(int n, const int* __restrict__ prow,
+                                              const int* __restrict__ pcol,
+                                              const T* __restrict__ pval, const T* xc, T* x,
+                                              int tid, int nthr) {
+  for (int i = tid; i < n; i += nthr) {
     T s = T(0);
-    for (int q = prow[i]; q < prow[i + 1]; ++q) s = fma(pval[q], xc[pcol[q]], s);
-    x[i] += s;
+    for (int q = prow[i]; q < prow[i + 1]; ++q) s = fma(pval[q], VL<COH>::one(xc + pcol[q]), s);
+    x[i] = VL<COH>::one(x + i) + s;
   }
 }
 
-// x = X b with the FP64 generalised inverse of the coarsest matrix (warp per row).
-// X is indexed in the unpadded order (3 per node, then pressure); n3 = 3 n.
+// x = X b with the FP64 generalised inverse of the coarsest matrix (warp per
+// row).  X is indexed in the unpadded order (3 per node, then pressure).
 __device__ __forceinline__ int pad_index(int j, int n3) {
   return j < n3 ? 4 * (j / 3) + j % 3 : j + n3 / 3;
 }
 
-template <typename T>
-__global__ void k_coarse_solve(int m, int n3, const double* __restrict__ X,
-                               const T* __restrict__ b, T* __restrict__ x) {
+template <typename T, bool COH>
+__device__ __forceinline__ void coarse_body(int m, int n3, const double* __restrict__ X,
+                                            const T* b, T* x, int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = w; i < m; i += nw) {
+  for (int i = warp; i < m; i += nwarps) {
     double s = 0.0;
     for (int j = lane; j < m; j += 32)
-      s = fma(X[(int64_t)i * m + j], (double)b[pad_index(j, n3)], s);
+      s = fma(X[(int64_t)i * m + j], (double)VL<COH>::one(b + pad_index(j, n3)), s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) x[pad_index(i, n3)] = (T)s;
   }
 }
 
-template <typename T>
-__global__ void k_zero(T* a, int64_t n) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    a[k] = T(0);
+template <typename T, bool COH>
+__device__ __forceinline__ void copy_body(const T* a, T* b, int64_t n, int tid, int nthr) {
+  for (int64_t k = tid; k < n; k += nthr) b[k] = VL<COH>::one(a + k);
 }
 
 template <typename T>
-__global__ void k_copyT(const T* __restrict__ a, T* __restrict__ b, int64_t n) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = a[k];
+__device__ __forceinline__ void zero_body(T* a, int64_t n, int tid, int nthr) {
+  for (int64_t k = tid; k < n; k += nthr) a[k] = T(0);
 }
 
-// ---- saddle-point parts: y_u (+)= B^T p per velocity node, y_p = B u - C p ---------
-
-// yu_i += sum_k B_ki^T p_k (rows of B^T are velocity nodes)
-template <typename T>
-__global__ void k_bt_add(int n, const int* __restrict__ row, const int* __restrict__ col,
-                         const T* __restrict__ val, int64_t nnz, const T* __restrict__ p,
-                         T sign, T* __restrict__ y) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// y_i += sign * sum_k B_ki^T p_k (rows of B^T are velocity nodes)
+template <typename T, bool COH>
+__device__ __forceinline__ void bt_add_body(int n, const int* __restrict__ row,
+                                            const int* __restrict__ col,
+                                            const T* __restrict__ val, int64_t nnz, const T* p,
+                                            T sign, T* y, int tid, int nthr) {
+  for (int i = tid; i < n; i += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int q = row[i]; q < row[i + 1]; ++q) {
-      const T pk = p[col[q]];
+      const T pk = VL<COH>::one(p + col[q]);
       s0 = fma(val[q], pk, s0);
       s1 = fma(val[nnz + q], pk, s1);
       s2 = fma(val[2 * nnz + q], pk, s2);
     }
     T y0, y1, y2;
-    ld3(y, i, y0, y1, y2);
+    VL<COH>::node(y, i, y0, y1, y2);
     st3(y, i, y0 + sign * s0, y1 + sign * s1, y2 + sign * s2);
   }
 }
 
 // MODE 0: yp = B u - C p;  MODE 1: yp = g - B u + C p (residual);
-// MODE 2: p += omega * (B u - C p - g) / S_D (sGS pressure step, in place)
-template <typename T, int MODE>
-__global__ void k_pressure_rows(int np, const int* __restrict__ brow, const int* __restrict__ bcol,
-                                const T* __restrict__ bval, int64_t bnnz,
-                                const int* __restrict__ crow, const int* __restrict__ ccol,
-                                const T* __restrict__ cval, const T* __restrict__ u,
-                                const T* p, const T* __restrict__ g, T* yp,
-                                const T* __restrict__ sd, T omega) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+// MODE 2: yp = p + omega (B u - C p - g) / S_D (sGS pressure step)
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
+                                           const int* __restrict__ bcol,
+                                           const T* __restrict__ bval, int64_t bnnz,
+                                           const int* __restrict__ crow,
+                                           const int* __restrict__ ccol,
+                                           const T* __restrict__ cval, const T* u, const T* p,
+                                           const T* g, T* yp, const T* __restrict__ sd, T omega,
+                                           int tid, int nthr) {
+  for (int k = tid; k < np; k += nthr) {
     T s = T(0);
     for (int q = brow[k]; q < brow[k + 1]; ++q) {
       const int j = bcol[q];
       T u0, u1, u2;
-      ld3(u, j, u0, u1, u2);
+      VL<COH>::node(u, j, u0, u1, u2);
       s = fma(bval[q], u0, s);
       s = fma(bval[bnnz + q], u1, s);
       s = fma(bval[2 * bnnz + q], u2, s);
     }
     T cp = T(0);
-    for (int q = crow[k]; q < crow[k + 1]; ++q) cp = fma(cval[q], p[ccol[q]], cp);
+    for (int q = crow[k]; q < crow[k + 1]; ++q) cp = fma(cval[q], VL<COH>::one(p + ccol[q]), cp);
     if (MODE == 0) {
       yp[k] = s - cp;
     } else if (MODE == 1) {
-      yp[k] = g[k] - s + cp;
+      yp[k] = VL<COH>::one(g + k) - s + cp;
     } else {
       const T d = sd[k];
-      const T r = s - cp - g[k];
-      yp[k] = p[k] + (d != T(0) ? omega * r / d : T(0));
+      const T r = s - cp - VL<COH>::one(g + k);
+      yp[k] = VL<COH>::one(p + k) + (d != T(0) ? omega * r / d : T(0));
     }
   }
+}
+
+// ------------------------------------------------------------------- phases
+
+enum PhaseType : int {
+  PH_ZERO = 0, PH_COPY, PH_ROWS, PH_RESTRICT, PH_PROLONG, PH_RESTRICT1, PH_PROLONG1,
+  PH_COARSE, PH_BT_ADD, PH_PROWS
+};
+
+// One operation of the cycle with its operands (a plain record, copied to the
+// device for the cluster launch or passed by value to a single launch).
+struct Phase {
+  int type, mode, G, n;   // n: rows / nodes / entries
+  const int* rows;
+  const int* rowptr;
+  const int* col;
+  const void* val;
+  int64_t nnz;
+  const void* dinv;
+  const void* x;
+  const void* b;
+  void* y;
+  const int* crow;
+  const int* ccol;
+  const void* cval;
+  const void* sd;
+  const void* p;          // pressure iterate (PH_PROWS)
+  const double* X;
+  int m, n3;
+  double omega;
+};
+
+template <typename T, bool COH>
+__device__ void dispatch_rows(const Phase& P, int warp, int nwarps) {
+  const T* val = (const T*)P.val;
+  const T* x = (const T*)P.x;
+  const T* b = (const T*)P.b;
+  T* y = (T*)P.y;
+  const T* d = (const T*)P.dinv;
+  const T om = (T)P.omega;
+#define AMG_ROWS_MODE(GG, MM)                                                                \
+  rows_body<T, GG, MM, COH>(P.n, P.rows, P.rowptr, P.col, val, P.nnz, x, b, y, d, om, warp, \
+                            nwarps)
+#define AMG_ROWS_G(GG)                              \
+  switch (P.mode) {                                 \
+    case kApply: AMG_ROWS_MODE(GG, kApply); break;  \
+    case kResid: AMG_ROWS_MODE(GG, kResid); break;  \
+    case kGS: AMG_ROWS_MODE(GG, kGS); break;        \
+    default: AMG_ROWS_MODE(GG, kJacobi); break;     \
+  }
+  switch (P.G) {
+    case 4: AMG_ROWS_G(4) break;
+    case 8: AMG_ROWS_G(8) break;
+    case 16: AMG_ROWS_G(16) break;
+    default: AMG_ROWS_G(32) break;
+  }
+#undef AMG_ROWS_G
+#undef AMG_ROWS_MODE
+}
+
+template <typename T, bool COH>
+__device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
+  const int warp = tid >> 5, nwarps = nthr >> 5;
+  switch (P.type) {
+    case PH_ZERO: zero_body<T>((T*)P.y, P.n, tid, nthr); break;
+    case PH_COPY: copy_body<T, COH>((const T*)P.x, (T*)P.y, P.n, tid, nthr); break;
+    case PH_ROWS: dispatch_rows<T, COH>(P, warp, nwarps); break;
+    case PH_RESTRICT:
+      restrict_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
+                            nthr);
+      break;
+    case PH_PROLONG:
+      prolong_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
+                           nthr);
+      break;
+    case PH_RESTRICT1:
+      restrict1_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
+                             nthr);
+      break;
+    case PH_PROLONG1:
+      prolong1_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
+                            nthr);
+      break;
+    case PH_COARSE:
+      coarse_body<T, COH>(P.m, P.n3, P.X, (const T*)P.b, (T*)P.y, warp, nwarps);
+      break;
+    case PH_BT_ADD:
+      bt_add_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, P.nnz, (const T*)P.x,
+                          (T)P.omega, (T*)P.y, tid, nthr);
+      break;
+    case PH_PROWS: {
+      const T* u = (const T*)P.x;
+      const T* p = (const T*)P.p;
+      const T om = (T)P.omega;
+#define AMG_PROWS(MM)                                                                        \
+  prows_body<T, MM, COH>(P.n, P.rowptr, P.col, (const T*)P.val, P.nnz, P.crow, P.ccol,      \
+                         (const T*)P.cval, u, p, (const T*)P.b, (T*)P.y, (const T*)P.sd, om, \
+                         tid, nthr)
+      if (P.mode == 0) AMG_PROWS(0);
+      else if (P.mode == 1) AMG_PROWS(1);
+      else AMG_PROWS(2);
+#undef AMG_PROWS
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// one operation as its own kernel
+template <typename T>
+__global__ void __launch_bounds__(256) k_phase(const Phase P) {
+  exec_phase<T, false>(P, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// the block-row operations as their own specialised kernels (the hot path)
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(256) k_rows(const Phase P) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  rows_body<T, G, MODE, false>(P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz,
+                               (const T*)P.x, (const T*)P.b, (T*)P.y, (const T*)P.dinv,
+                               (T)P.omega, tid >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
+template <typename T, int G>
+void launch_rows_mode(const Phase& P, int grid, cudaStream_t s) {
+  switch (P.mode) {
+    case kApply: k_rows<T, G, kApply><<<grid, 256, 0, s>>>(P); break;
+    case kResid: k_rows<T, G, kResid><<<grid, 256, 0, s>>>(P); break;
+    case kGS: k_rows<T, G, kGS><<<grid, 256, 0, s>>>(P); break;
+    default: k_rows<T, G, kJacobi><<<grid, 256, 0, s>>>(P); break;
+  }
+}
+
+template <typename T>
+void launch_rows(const Phase& P, cudaStream_t s) {
+  // one group of G lanes per row: nrows * G threads
+  const int grid = (int)(((int64_t)P.n * P.G + 255) / 256);
+  switch (P.G) {
+    case 4: launch_rows_mode<T, 4>(P, grid, s); break;
+    case 8: launch_rows_mode<T, 8>(P, grid, s); break;
+    case 16: launch_rows_mode<T, 16>(P, grid, s); break;
+    default: launch_rows_mode<T, 32>(P, grid, s); break;
+  }
+}
+
+// The recorded phases of the small coarse levels in one thread-block cluster.
+// The cluster barrier (arrive.release / wait.acquire) orders every phase's
+// writes before the next phase's reads; vectors are read through L2.
+constexpr int kSubThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kSubThreads, 1) k_subcycle(const Phase* __restrict__ ph,
+                                                               int nph) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int nthr = blockDim.x * (int)cl.num_blocks();
+  const int tid = (int)cl.block_rank() * blockDim.x + threadIdx.x;
+  for (int p = 0; p < nph; ++p) {
+    const Phase P = ph[p];
+    exec_phase<T, true>(P, tid, nthr);
+    cl.sync();
+  }
+}
+
+// ------------------------------------------------------------------- emitter
+
+inline int gridn(int64_t n, int t = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 152 * 16));
 }
 
 template <typename T> struct LvVec;
@@ -274,10 +492,6 @@ template <> struct LvVec<float> {
   static const float* schur(Level& l) { return l.schur32; }
 };
 
-inline int gridn(int64_t n, int t = 256) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 152 * 16));
-}
-
 // lanes per block row: the autotuned value, else from the average row length
 inline int group_for(const Level& lv) {
   if (lv.group) return lv.group;
@@ -287,63 +501,92 @@ inline int group_for(const Level& lv) {
   return 4;
 }
 
-template <typename T, int MODE>
-void launch_rows_g(int G, cudaStream_t s, int nrows, const int* rows, const Level& lv,
-                   const T* val, const T* x, const T* b, T* y, const T* dinv, T omega) {
-  if (nrows <= 0) return;
-  int64_t threads = (int64_t)nrows * G;
-  int grid = (int)((threads + 255) / 256);
-#define AMG_ROWS_CASE(GG)                                                                   \
-  case GG:                                                                                  \
-    k_block_rows<T, GG, MODE><<<grid, 256, 0, s>>>(nrows, rows, lv.rowptr, lv.col, val,      \
-                                                   lv.nnzb, x, b, y, dinv, omega);          \
-    break;
-  switch (G) {
-    AMG_ROWS_CASE(4)
-    AMG_ROWS_CASE(8)
-    AMG_ROWS_CASE(16)
-    default:
-    AMG_ROWS_CASE(32)
+// Launches each operation as a kernel (rec == nullptr) or appends it to `rec`.
+template <typename T>
+struct Emit {
+  amg_handle* h;
+  std::vector<Phase>* rec = nullptr;
+
+  void put(const Phase& P, int64_t work, int threads_per_item = 1) {
+    if (rec) {
+      rec->push_back(P);
+      return;
+    }
+    if (work <= 0) return;
+    if (P.type == PH_ROWS) launch_rows<T>(P, h->stream);
+    else k_phase<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
+    h->launches++;
   }
-#undef AMG_ROWS_CASE
+  static Phase blank(int type) {
+    Phase P;
+    std::memset(&P, 0, sizeof(P));
+    P.type = type;
+    return P;
+  }
+  void rows(int mode, const Level& lv, int G, int nrows, const int* rows, const T* val,
+            const T* x, const T* b, T* y, const T* dinv, T omega) {
+    Phase P = blank(PH_ROWS);
+    P.mode = mode; P.G = G; P.n = nrows; P.rows = rows; P.rowptr = lv.rowptr; P.col = lv.col;
+    P.val = val; P.nnz = lv.nnzb; P.x = x; P.b = b; P.y = y; P.dinv = dinv; P.omega = omega;
+    put(P, nrows, G);
+  }
+  void zero(T* a, int64_t n) {
+    Phase P = blank(PH_ZERO);
+    P.y = a; P.n = (int)n;
+    put(P, n);
+  }
+  void copy(const T* a, T* b, int64_t n) {
+    Phase P = blank(PH_COPY);
+    P.x = a; P.y = b; P.n = (int)n;
+    put(P, n);
+  }
+  void transfer(int type, int n, const int* row, const int* col, const T* val, const T* src,
+                T* dst) {
+    Phase P = blank(type);
+    P.n = n; P.rowptr = row; P.col = col; P.val = val; P.x = src; P.y = dst;
+    put(P, n);
+  }
+  void coarse(const T* b, T* x) {
+    Phase P = blank(PH_COARSE);
+    P.m = h->coarse_m; P.n3 = 3 * h->L.back()->n; P.X = h->coarse_inv; P.b = b; P.y = x;
+    put(P, P.m, 32);
+  }
+  void bt_add(Level& lv, const T* p, T sign, T* y) {
+    Phase P = blank(PH_BT_ADD);
+    P.n = lv.n; P.rowptr = lv.bt_rowptr; P.col = lv.bt_col; P.val = LvVec<T>::btval(lv);
+    P.nnz = lv.b_nnz; P.x = p; P.omega = (double)sign; P.y = y;
+    put(P, lv.n);
+  }
+  void prows(int mode, Level& lv, const T* u, const T* p, const T* g, T* yp, T omega) {
+    Phase P = blank(PH_PROWS);
+    P.mode = mode; P.n = lv.np; P.rowptr = lv.b_rowptr; P.col = lv.b_col;
+    P.val = LvVec<T>::bval(lv); P.nnz = lv.b_nnz; P.crow = lv.c_rowptr; P.ccol = lv.c_col;
+    P.cval = LvVec<T>::cval(lv); P.x = u; P.p = p; P.b = g; P.y = yp;
+    P.sd = LvVec<T>::schur(lv); P.omega = (double)omega;
+    put(P, lv.np);
+  }
+};
+
+// ------------------------------------------------------------------- level operations
+
+template <typename T>
+void e_apply(Emit<T>& e, Level& lv, const T* x, T* y, bool saddle) {
+  e.rows(kApply, lv, group_for(lv), lv.n, nullptr, LvVec<T>::val(lv), x, nullptr, y, nullptr,
+         T(0));
+  if (saddle && lv.np > 0) {
+    const T* p = x + 4 * lv.n;
+    e.bt_add(lv, p, T(1), y);
+    e.prows(0, lv, x, p, nullptr, y + 4 * lv.n, T(0));
+  }
 }
 
-}  // namespace
-
-// y = K_l x (saddle: [A B^T; B -C])
 template <typename T>
-void level_apply(amg_handle* h, int l, const T* x, T* y) {
-  Level& lv = *h->L[l];
-  cudaStream_t s = h->stream;
-  launch_rows_g<T, kApply>(group_for(lv), s, lv.n, nullptr, lv, LvVec<T>::val(lv), x, nullptr, y,
-                           nullptr, T(0));
-  h->launches++;
-  if (h->saddle && lv.np > 0) {
+void e_residual(Emit<T>& e, Level& lv, const T* x, const T* b, T* r, bool saddle) {
+  e.rows(kResid, lv, group_for(lv), lv.n, nullptr, LvVec<T>::val(lv), x, b, r, nullptr, T(0));
+  if (saddle && lv.np > 0) {
     const T* p = x + 4 * lv.n;
-    k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
-                                            lv.b_nnz, p, T(1), y);
-    k_pressure_rows<T, 0><<<gridn(lv.np), 256, 0, s>>>(
-        lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, p, nullptr, y + 4 * lv.n, nullptr, T(0));
-    h->launches += 2;
-  }
-}
-
-template <typename T>
-void level_residual(amg_handle* h, int l, const T* x, const T* b, T* r) {
-  Level& lv = *h->L[l];
-  cudaStream_t s = h->stream;
-  launch_rows_g<T, kResid>(group_for(lv), s, lv.n, nullptr, lv, LvVec<T>::val(lv), x, b, r,
-                           nullptr, T(0));
-  h->launches++;
-  if (h->saddle && lv.np > 0) {
-    const T* p = x + 4 * lv.n;
-    k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
-                                            lv.b_nnz, p, T(-1), r);
-    k_pressure_rows<T, 1><<<gridn(lv.np), 256, 0, s>>>(
-        lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, p, b + 4 * lv.n, r + 4 * lv.n, nullptr, T(0));
-    h->launches += 2;
+    e.bt_add(lv, p, T(-1), r);
+    e.prows(1, lv, x, p, b + 4 * lv.n, r + 4 * lv.n, T(0));
   }
 }
 
@@ -351,95 +594,89 @@ void level_residual(amg_handle* h, int l, const T* x, const T* b, T* r) {
 // ascending before the coarse correction, descending after it) or damped block
 // Jacobi.  Saddle: segregated Gauss-Seidel, Eq. (uzsm).
 template <typename T>
-void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_zero) {
-  Level& lv = *h->L[l];
-  cudaStream_t s = h->stream;
+void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
+              bool x_is_zero) {
   const int dofs = lv.dofs4();
-  if (x_is_zero) {
-    k_zero<T><<<gridn(dofs), 256, 0, s>>>(x, dofs);
-    h->launches++;
-  }
+  if (x_is_zero) e.zero(x, dofs);
   const int G = group_for(lv);
   const T* val = LvVec<T>::val(lv);
   const T* dinv = LvVec<T>::dinv(lv);
   if (h->saddle) {
-    // u <- u + omega D^{-1} (f - A u - B^T p)   (M_A = damped block Jacobi)
     T* t = LvVec<T>::t(lv);
     T* r = LvVec<T>::r(lv);
     const T* p = x + 4 * lv.n;
-    // r_u = f - B^T p, then t_u = u + omega D^{-1} (r_u - A u)
-    k_copyT<T><<<gridn(4 * lv.n), 256, 0, s>>>(b, r, 4 * (int64_t)lv.n);
-    k_bt_add<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv),
-                                            lv.b_nnz, p, T(-1), r);
-    launch_rows_g<T, kJacobi>(G, s, lv.n, nullptr, lv, val, x, r, t, dinv, (T)h->opt.omega);
-    k_copyT<T><<<gridn(4 * lv.n), 256, 0, s>>>(t, x, 4 * (int64_t)lv.n);
+    // u <- u + omega D^{-1} (f - B^T p - A u)    (M_A = damped block Jacobi)
+    e.copy(b, r, 4 * (int64_t)lv.n);
+    e.bt_add(lv, p, T(-1), r);
+    e.rows(kJacobi, lv, G, lv.n, nullptr, val, x, r, t, dinv, (T)h->opt.omega);
+    e.copy(t, x, 4 * (int64_t)lv.n);
     // p <- p + omega_p S_D^{-1} (B u_new - C p - g)
-    k_pressure_rows<T, 2><<<gridn(lv.np), 256, 0, s>>>(
-        lv.np, lv.b_rowptr, lv.b_col, LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col,
-        LvVec<T>::cval(lv), x, x + 4 * lv.n, b + 4 * lv.n, t + 4 * lv.n, LvVec<T>::schur(lv),
-        (T)h->opt.omega_p);
-    k_copyT<T><<<gridn(lv.np), 256, 0, s>>>(t + 4 * lv.n, x + 4 * lv.n, lv.np);
-    h->launches += 6;
+    e.prows(2, lv, x, x + 4 * lv.n, b + 4 * lv.n, t + 4 * lv.n, (T)h->opt.omega_p);
+    e.copy(t + 4 * lv.n, x + 4 * lv.n, lv.np);
     return;
   }
   if (h->opt.smoother == AMG_SMOOTHER_JACOBI) {
     T* t = LvVec<T>::t(lv);
-    launch_rows_g<T, kJacobi>(G, s, lv.n, nullptr, lv, val, x, b, t, dinv, (T)h->opt.omega);
-    k_copyT<T><<<gridn(dofs), 256, 0, s>>>(t, x, dofs);
-    h->launches += 2;
+    e.rows(kJacobi, lv, G, lv.n, nullptr, val, x, b, t, dinv, (T)h->opt.omega);
+    e.copy(t, x, dofs);
     return;
   }
   const int Ggs = lv.group_gs ? lv.group_gs : G;
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
-    const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
-    launch_rows_g<T, kGS>(Ggs, s, e - a, lv.colour_rows.p + a, lv, val, x, b, x, dinv, T(0));
-    h->launches++;
+    const int a = lv.colour_ptr[c], e2 = lv.colour_ptr[c + 1];
+    e.rows(kGS, lv, Ggs, e2 - a, lv.colour_rows.p + a, val, x, b, x, dinv, T(0));
   }
 }
 
 template <typename T>
-static void coarse_solve(amg_handle* h, const T* b, T* x) {
-  const int m = h->coarse_m;
-  const int n3 = 3 * h->L.back()->n;
-  k_coarse_solve<T><<<gridn((int64_t)m * 32), 256, 0, h->stream>>>(m, n3, h->coarse_inv, b, x);
-  h->launches++;
-}
-
-template <typename T>
-static void restrict_to(amg_handle* h, int l, const T* r, T* bc) {
+void e_restrict(Emit<T>& e, amg_handle* h, int l, const T* r, T* bc) {
   Level& lv = *h->L[l];
   Level& nx = *h->L[l + 1];
-  cudaStream_t s = h->stream;
-  k_restrict<T><<<gridn(nx.n), 256, 0, s>>>(nx.n, lv.r_rowptr, lv.r_col, LvVec<T>::rval(lv), r, bc);
-  h->launches++;
-  if (h->saddle && nx.np > 0) {
-    k_restrict1<T><<<gridn(nx.np), 256, 0, s>>>(nx.np, lv.ht_rowptr, lv.ht_col,
-                                                 LvVec<T>::htval(lv), r + 4 * lv.n, bc + 4 * nx.n);
-    h->launches++;
-  }
+  e.transfer(PH_RESTRICT, nx.n, lv.r_rowptr, lv.r_col, LvVec<T>::rval(lv), r, bc);
+  if (h->saddle && nx.np > 0)
+    e.transfer(PH_RESTRICT1, nx.np, lv.ht_rowptr, lv.ht_col, LvVec<T>::htval(lv), r + 4 * lv.n,
+               bc + 4 * nx.n);
 }
 
 template <typename T>
-static void prolong_add(amg_handle* h, int l, const T* xc, T* x) {
+void e_prolong(Emit<T>& e, amg_handle* h, int l, const T* xc, T* x) {
   Level& lv = *h->L[l];
   Level& nx = *h->L[l + 1];
-  cudaStream_t s = h->stream;
-  k_prolong<T><<<gridn(lv.n), 256, 0, s>>>(lv.n, lv.p_rowptr, lv.p_col, LvVec<T>::pval(lv), xc, x);
-  h->launches++;
-  if (h->saddle && lv.np > 0) {
-    k_prolong1<T><<<gridn(lv.np), 256, 0, s>>>(lv.np, lv.h_rowptr, lv.h_col, LvVec<T>::hval(lv),
-                                               xc + 4 * nx.n, x + 4 * lv.n);
-    h->launches++;
-  }
+  e.transfer(PH_PROLONG, lv.n, lv.p_rowptr, lv.p_col, LvVec<T>::pval(lv), xc, x);
+  if (h->saddle && lv.np > 0)
+    e.transfer(PH_PROLONG1, lv.np, lv.h_rowptr, lv.h_col, LvVec<T>::hval(lv), xc + 4 * nx.n,
+               x + 4 * lv.n);
 }
 
-// Algorithm 1 on level l with iterate x and right-hand side b.
 template <typename T>
-static void cycle_rec(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
+struct SubCycle;
+
+template <typename T>
+void cycle_rec(Emit<T>& e, amg_handle* h, int l, T* x, const T* b, bool x_is_zero);
+
+// Steps 5-11 of Algorithm 1 seen from level l-1: the coarse solve when l is the
+// coarsest level, else nu recursive calls from x_l = 0.  From the cluster level
+// down they run as one recorded launch.
+template <typename T>
+void coarse_calls(Emit<T>& e, amg_handle* h, int l, T* xc, const T* bc) {
+  const int L = (int)h->L.size() - 1;
+  if (!e.rec && h->sub_from > 0 && l == h->sub_from) {
+    SubCycle<T>::launch(h);
+    return;
+  }
+  if (l == L) {
+    e.coarse(bc, xc);
+    return;
+  }
+  for (int k = 0; k < std::max(1, h->opt.nu); ++k) cycle_rec<T>(e, h, l, xc, bc, k == 0);
+}
+
+template <typename T>
+void cycle_rec(Emit<T>& e, amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
   const int L = (int)h->L.size() - 1;
   if (l == L) {
-    coarse_solve<T>(h, b, x);
+    e.coarse(b, x);
     return;
   }
   Level& lv = *h->L[l];
@@ -447,37 +684,128 @@ static void cycle_rec(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
   const amg_options& o = h->opt;
   bool zero = x_is_zero;
   for (int k = 0; k < o.m_pre; ++k) {
-    level_smooth<T>(h, l, x, b, false, zero);
+    e_smooth<T>(e, h, lv, x, b, false, zero);
     zero = false;
   }
-  if (zero) {   // no pre-smoothing: x is still the zero initial guess
-    k_zero<T><<<gridn(lv.dofs4()), 256, 0, h->stream>>>(x, lv.dofs4());
-    h->launches++;
-  }
+  if (zero) e.zero(x, lv.dofs4());   // no pre-smoothing: x is still the zero initial guess
   T* r = LvVec<T>::r(lv);
-  level_residual<T>(h, l, x, b, r);
+  e_residual<T>(e, lv, x, b, r, h->saddle);
   T* bc = LvVec<T>::b(nx);
   T* xc = LvVec<T>::x(nx);
-  restrict_to<T>(h, l, r, bc);
-  if (l + 1 == L) {
-    coarse_solve<T>(h, bc, xc);
-  } else {
-    for (int k = 0; k < std::max(1, o.nu); ++k) cycle_rec<T>(h, l + 1, xc, bc, k == 0);
+  e_restrict<T>(e, h, l, r, bc);
+  coarse_calls<T>(e, h, l + 1, xc, bc);
+  e_prolong<T>(e, h, l, xc, x);
+  for (int k = 0; k < o.m_post; ++k) e_smooth<T>(e, h, lv, x, b, true, false);
+}
+
+template <typename T>
+DBuf<unsigned char>& sub_buf(amg_handle* h);
+template <>
+DBuf<unsigned char>& sub_buf<float>(amg_handle* h) { return h->sub_ph32; }
+template <>
+DBuf<unsigned char>& sub_buf<double>(amg_handle* h) { return h->sub_ph64; }
+template <typename T>
+int& sub_count(amg_handle* h);
+template <>
+int& sub_count<float>(amg_handle* h) { return h->sub_n32; }
+template <>
+int& sub_count<double>(amg_handle* h) { return h->sub_n64; }
+
+template <typename T>
+struct SubCycle {
+  // records what coarse_calls(from) does, on the level's own vectors
+  static void record(amg_handle* h, int from) {
+    std::vector<Phase> ph;
+    Emit<T> e{h, &ph};
+    Level& lv = *h->L[from];
+    coarse_calls<T>(e, h, from, LvVec<T>::x(lv), LvVec<T>::b(lv));
+    DBuf<unsigned char>& d = sub_buf<T>(h);
+    d.alloc(ph.size() * sizeof(Phase));
+    AMG_CUDA(cudaMemcpyAsync(d.p, ph.data(), ph.size() * sizeof(Phase), cudaMemcpyHostToDevice,
+                             h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    sub_count<T>(h) = (int)ph.size();
   }
-  prolong_add<T>(h, l, xc, x);
-  for (int k = 0; k < o.m_post; ++k) level_smooth<T>(h, l, x, b, true, false);
+
+  static void launch(amg_handle* h) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(h->sub_cluster);
+    cfg.blockDim = dim3(kSubThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->sub_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_subcycle<T>,
+                                reinterpret_cast<const Phase*>(sub_buf<T>(h).p), sub_count<T>(h)));
+    h->launches++;
+  }
+};
+
+template <typename T>
+int max_clusters(int size) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(size);
+  cfg.blockDim = dim3(kSubThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = size;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (size > 8 &&
+      cudaFuncSetAttribute(k_subcycle<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_subcycle<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- entry points
+
+template <typename T>
+void level_apply(amg_handle* h, int l, const T* x, T* y) {
+  Emit<T> e{h};
+  e_apply<T>(e, *h->L[l], x, y, h->saddle);
+}
+
+template <typename T>
+void level_residual(amg_handle* h, int l, const T* x, const T* b, T* r) {
+  Emit<T> e{h};
+  e_residual<T>(e, *h->L[l], x, b, r, h->saddle);
+}
+
+template <typename T>
+void level_smooth(amg_handle* h, int l, T* x, const T* b, bool post, bool x_is_zero) {
+  Emit<T> e{h};
+  e_smooth<T>(e, h, *h->L[l], x, b, post, x_is_zero);
 }
 
 template <typename T>
 void vcycle(amg_handle* h, int l, bool x_is_zero) {
+  Emit<T> e{h};
   Level& lv = *h->L[l];
-  cycle_rec<T>(h, l, LvVec<T>::x(lv), LvVec<T>::b(lv), x_is_zero);
+  cycle_rec<T>(e, h, l, LvVec<T>::x(lv), LvVec<T>::b(lv), x_is_zero);
 }
 
 // z = M^{-1} r: opt.cycles applications of Algorithm 1 from zero.
 template <>
 void precondition_device<double>(amg_handle* h, const double* r, double* z) {
-  for (int c = 0; c < std::max(1, h->opt.cycles); ++c) cycle_rec<double>(h, 0, z, r, c == 0);
+  Emit<double> e{h};
+  for (int c = 0; c < std::max(1, h->opt.cycles); ++c) cycle_rec<double>(e, h, 0, z, r, c == 0);
 }
 
 template <>
@@ -485,8 +813,9 @@ void precondition_device<float>(amg_handle* h, const double* r, double* z) {
   Level& lv = *h->L[0];
   const int64_t n = lv.dofs4();
   launch_to_float(r, lv.b32, n, h->stream, h);
+  Emit<float> e{h};
   for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
-    cycle_rec<float>(h, 0, lv.x32.p, lv.b32.p, c == 0);
+    cycle_rec<float>(e, h, 0, lv.x32.p, lv.b32.p, c == 0);
   launch_to_double(lv.x32, z, n, h->stream, h);
 }
 
@@ -494,66 +823,102 @@ void level_transfer(amg_handle* h, int l, bool restrict_, bool f32) {
   Level& lv = *h->L[l];
   Level& nx = *h->L[l + 1];
   if (f32) {
-    if (restrict_) restrict_to<float>(h, l, lv.r32.p, nx.b32.p);
-    else prolong_add<float>(h, l, nx.x32.p, lv.x32.p);
+    Emit<float> e{h};
+    if (restrict_) e_restrict<float>(e, h, l, lv.r32.p, nx.b32.p);
+    else e_prolong<float>(e, h, l, nx.x32.p, lv.x32.p);
   } else {
-    if (restrict_) restrict_to<double>(h, l, lv.r64.p, nx.b64.p);
-    else prolong_add<double>(h, l, nx.x64.p, lv.x64.p);
+    Emit<double> e{h};
+    if (restrict_) e_restrict<double>(e, h, l, lv.r64.p, nx.b64.p);
+    else e_prolong<double>(e, h, l, nx.x64.p, lv.x64.p);
   }
 }
 
-// Times the operator kernel of every level with 4, 8, 16 and 32 lanes per block
-// row (in the precision the cycle uses) and keeps the fastest.  The row kernels
-// of one level share its access pattern, so one choice serves all modes.
+void set_subcycle(amg_handle* h, int from) {
+  h->sub_from = 0;
+  if (from <= 0 || from >= (int)h->L.size() || h->sub_cluster <= 0) return;
+  if (h->opt.precision == AMG_FP32) SubCycle<float>::record(h, from);
+  else SubCycle<double>::record(h, from);
+  h->sub_from = from;
+}
+
+// Lanes per block row (4, 8, 16 or 32) of every level, from timing the operator
+// kernel and, separately, one colour sweep; then the level from which the cycle
+// runs as one cluster launch, from timing whole preconditioner applications.
 void autotune_levels(amg_handle* h) {
   cudaStream_t s = h->stream;
   cudaEvent_t e0, e1;
   AMG_CUDA(cudaEventCreate(&e0));
   AMG_CUDA(cudaEventCreate(&e1));
+  auto elapsed = [&]() {
+    AMG_CUDA(cudaEventRecord(e1, s));
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
   const bool f32 = h->opt.precision == AMG_FP32;
-  for (auto& lp : h->L) {
-    Level& lv = *lp;
+  for (size_t l = 0; l < h->L.size(); ++l) {
+    Level& lv = *h->L[l];
     int best = 0;
     float best_ms = 1e30f;
     for (int G : {4, 8, 16, 32}) {
-      const int reps = 5;
-      for (int r = 0; r < reps + 2; ++r) {
+      lv.group = G;
+      for (int r = 0; r < 7; ++r) {
         if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
-        if (f32)
-          launch_rows_g<float, kApply>(G, s, lv.n, nullptr, lv, lv.val32.p, lv.x32.p, nullptr,
-                                       lv.r32.p, nullptr, 0.f);
-        else
-          launch_rows_g<double, kApply>(G, s, lv.n, nullptr, lv, lv.val.p, lv.x64.p, nullptr,
-                                        lv.r64.p, nullptr, 0.0);
+        if (f32) level_apply<float>(h, (int)l, lv.x32.p, lv.r32.p);
+        else level_apply<double>(h, (int)l, lv.x64.p, lv.r64.p);
       }
-      AMG_CUDA(cudaEventRecord(e1, s));
-      AMG_LAUNCH_CHECK();
-      AMG_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      h->launches += reps + 2;
+      const float ms = elapsed();
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group = best;
     if (lv.ncolours == 0 || h->saddle || h->opt.smoother != AMG_SMOOTHER_GS) continue;
-    // one full colour sweep per candidate
     best = 0;
     best_ms = 1e30f;
     for (int G : {4, 8, 16, 32}) {
       lv.group_gs = G;
       for (int r = 0; r < 3; ++r) {
         if (r == 1) AMG_CUDA(cudaEventRecord(e0, s));
-        if (f32) level_smooth<float>(h, (int)(&lp - &h->L[0]), lv.x32.p, lv.b32.p, false, false);
-        else level_smooth<double>(h, (int)(&lp - &h->L[0]), lv.x64.p, lv.b64.p, false, false);
+        if (f32) level_smooth<float>(h, (int)l, lv.x32.p, lv.b32.p, false, false);
+        else level_smooth<double>(h, (int)l, lv.x64.p, lv.b64.p, false, false);
       }
-      AMG_CUDA(cudaEventRecord(e1, s));
-      AMG_LAUNCH_CHECK();
-      AMG_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      const float ms = elapsed();
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group_gs = best;
+  }
+  // cluster sub-cycle: the largest cluster that fits (16, else 8 CTAs), then the
+  // fastest start level among 1..L (or none)
+  const int L = (int)h->L.size() - 1;
+  h->sub_cluster = 0;
+  if (L >= 1 && h->opt.cluster_from != 0) {
+    for (int size : {16, 8}) {
+      const int n = f32 ? max_clusters<float>(size) : max_clusters<double>(size);
+      if (n >= 1) { h->sub_cluster = size; break; }
+    }
+  }
+  if (h->sub_cluster > 0 && h->opt.cluster_from >= 0) {
+    set_subcycle(h, std::min(h->opt.cluster_from, L));
+  } else if (h->sub_cluster > 0) {
+    DBuf<double> r, z;
+    const int64_t n4 = h->L[0]->dofs4();
+    r.alloc(n4);
+    z.alloc(n4);
+    AMG_CUDA(cudaMemsetAsync(r.p, 0, r.bytes(), s));
+    int best_from = 0;
+    float best_ms = 1e30f;
+    for (int from = 0; from <= L; ++from) {
+      set_subcycle(h, from);
+      for (int rep = 0; rep < 5; ++rep) {
+        if (rep == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) precondition_device<float>(h, r, z);
+        else precondition_device<double>(h, r, z);
+      }
+      const float ms = elapsed();
+      if (ms < best_ms * 0.98f) { best_ms = ms; best_from = from; }
+    }
+    set_subcycle(h, best_from);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -45,8 +45,8 @@ def test_struct_layout_matches_header(lib):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(amg_matrix), sizeof(amg_options), sizeof(amg_stats),
          sizeof(amg_level_info));
-  printf("%zu %zu %zu\n", offsetof(amg_matrix, device_ptrs), offsetof(amg_options, omega_p),
-         offsetof(amg_stats, level_colours));
+  printf("%zu %zu %zu %zu\n", offsetof(amg_matrix, device_ptrs), offsetof(amg_options, omega_p),
+         offsetof(amg_stats, level_colours), offsetof(amg_options, cluster_from));
   return 0;
 }
 '''
@@ -64,6 +64,7 @@ int main(void) {
     assert sizes[4] == B.AmgMatrix.device_ptrs.offset
     assert sizes[5] == B.AmgOptions.omega_p.offset
     assert sizes[6] == B.AmgStats.level_colours.offset
+    assert sizes[7] == B.AmgOptions.cluster_from.offset
 
 
 def test_default_options(lib):
