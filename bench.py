@@ -238,6 +238,20 @@ def run_gpu(args, rank, world):
     gs_bytes = 40 * info0.nnzb + 80 * info0.n_nodes
     spmv_ms, _ = chosen.time_level_op("apply", 0, B.AMG_FP64, reps=20, warmup=3)
     spmv_bytes = 76 * info0.nnzb + 52 * info0.n_nodes
+    # per-level device times of the cycle operations (CUDA events, handle stream)
+    breakdown = []
+    for l in range(chosen.n_levels):
+        inf = chosen.level_info(l)
+        row = {"level": l, "nodes": inf.n_nodes, "nnzb": inf.nnzb, "colours": inf.n_colours}
+        row["apply_ms"] = chosen.time_level_op("apply", l, B.AMG_FP32, reps=10, warmup=2)[0]
+        if not inf.is_coarsest:
+            row["smooth_ms"], row["smooth_launches"] = chosen.time_level_op(
+                "smooth", l, B.AMG_FP32, reps=10, warmup=2)
+            row["residual_ms"] = chosen.time_level_op("residual", l, B.AMG_FP32, reps=10,
+                                                      warmup=2)[0]
+        breakdown.append(row)
+    precond_ms, precond_launches = chosen.time_level_op("precond", 0, B.AMG_FP32, reps=10,
+                                                        warmup=2)
     peak, peak_kind = peaks()
     achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
     traffic = None
@@ -288,7 +302,9 @@ def run_gpu(args, rank, world):
                      "unit_bytes": gs_bytes, "ms_per_unit": sweep_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs"},
         "kernels": {"spmv_fp64_level0": {"ms": spmv_ms, "bytes": spmv_bytes,
-                                         "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9}},
+                                         "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9},
+                    "precond_fp32": {"ms": precond_ms, "launches": precond_launches},
+                    "levels_fp32": breakdown},
         "clocks": clocks,
     }
     if cpu is not None:

@@ -87,20 +87,29 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
     if (active) {
       i = rows ? ldg(rows + g) : g;
       const int a = ldg(rowptr + i), e = ldg(rowptr + i + 1);
-      for (int k = a + gl; k < e; k += G) {
-        const int j = ldg(col + k);
-        T x0, x1, x2;
-        VL<COH>::node(x, j, x0, x1, x2);
-        const T* v = val + k;
-        s0 = fma(ldg(v), x0, s0);
-        s0 = fma(ldg(v + nnzb), x1, s0);
-        s0 = fma(ldg(v + 2 * nnzb), x2, s0);
-        s1 = fma(ldg(v + 3 * nnzb), x0, s1);
-        s1 = fma(ldg(v + 4 * nnzb), x1, s1);
-        s1 = fma(ldg(v + 5 * nnzb), x2, s1);
-        s2 = fma(ldg(v + 6 * nnzb), x0, s2);
-        s2 = fma(ldg(v + 7 * nnzb), x1, s2);
-        s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+      // U blocks per lane per step: all column indices of the step are loaded
+      // before the gathers that depend on them
+      constexpr int U = G >= 16 ? 2 : 4;
+      for (int k0 = a + gl; k0 < e; k0 += U * G) {
+        int j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) j[u] = (k0 + u * G < e) ? ldg(col + k0 + u * G) : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (j[u] < 0) continue;
+          T x0, x1, x2;
+          VL<COH>::node(x, j[u], x0, x1, x2);
+          const T* v = val + k0 + u * G;
+          s0 = fma(ldg(v), x0, s0);
+          s0 = fma(ldg(v + nnzb), x1, s0);
+          s0 = fma(ldg(v + 2 * nnzb), x2, s0);
+          s1 = fma(ldg(v + 3 * nnzb), x0, s1);
+          s1 = fma(ldg(v + 4 * nnzb), x1, s1);
+          s1 = fma(ldg(v + 5 * nnzb), x2, s1);
+          s2 = fma(ldg(v + 6 * nnzb), x0, s2);
+          s2 = fma(ldg(v + 7 * nnzb), x1, s2);
+          s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+        }
       }
     }
 #pragma unroll
