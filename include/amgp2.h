@@ -128,6 +128,10 @@ typedef struct amg_options {
   int32_t cluster_from;     /* coarse levels from this level down run as one
                                thread-block-cluster launch: -1 chosen by timing
                                at setup (default), 0 never, k >= 1 from level k */
+  int32_t cycle_kernel;     /* 0: chosen by timing at setup (default); 1: one
+                               launch per operation (with the cluster levels);
+                               2: the whole cycle as one persistent cooperative
+                               launch with grid barriers                       */
   double omega;             /* block Jacobi damping (default 0.5)               */
   double omega_p;           /* sGS pressure step omega (default 0.125)          */
 } amg_options;

@@ -58,7 +58,8 @@ class AmgOptions(C.Structure):
                 ("krylov", C.c_int32), ("max_levels", C.c_int32), ("coarse_dofs", C.c_int32),
                 ("gmres_restart", C.c_int32), ("separate", C.c_int32),
                 ("max_iterations", C.c_int32), ("use_graphs", C.c_int32),
-                ("cluster_from", C.c_int32), ("omega", C.c_double), ("omega_p", C.c_double)]
+                ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
+                ("omega", C.c_double), ("omega_p", C.c_double)]
 
 
 class AmgStats(C.Structure):

@@ -67,12 +67,22 @@ struct Level {
   int64_t nnzb = 0;
   DBuf<int> rowptr, col, tags;
   DBuf<double> val;     // 9 * nnzb, plane-major
-  DBuf<float> val32;
+  DBuf<float> val32;     // FP32 copy of the kernel layout (k_val)
   DBuf<double> dinv;    // 12 * n: per node 3 padded rows (4 values) of the inverse
   DBuf<float> dinv32;
   int ncolours = 0;
   std::vector<int> colour_ptr;  // host: offsets into colour_rows, ncolours+1
   DBuf<int> colour, colour_rows;
+  // Coloured levels keep a second copy of A whose block rows are stored in
+  // colour order (stored row k is node colour_rows[k]; column ids unchanged), so
+  // a colour sweep reads one contiguous range.  The cycle's row kernels use it.
+  bool stored = false;
+  DBuf<int> srowptr, scol;
+  DBuf<double> sval;            // 9 planes, stored order
+  const int* k_rowptr() const { return stored ? srowptr.p : rowptr.p; }
+  const int* k_col() const { return stored ? scol.p : col.p; }
+  const double* k_val() const { return stored ? sval.p : val.p; }
+  const int* k_rows() const { return stored ? colour_rows.p : nullptr; }
   int max_row_blocks = 0;
   double avg_row_blocks = 0.0;
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
@@ -136,6 +146,12 @@ struct amg_handle {
   amgp2::DBuf<double> pmass;       // Stokes pressure weights
   double pmass_sum = 0.0;
   double* host_scal = nullptr;     // pinned
+  int* host_int = nullptr;         // pinned
+  amgp2::DBuf<int> it_dev;         // device iteration counter of the graph loop
+  cudaGraphExec_t cg_loop_pcg = nullptr, cg_loop_fcg = nullptr;   // whole-solve loops
+  int64_t cg_loop_pcg_launches = 0, cg_loop_fcg_launches = 0;
+  bool cg_loop_failed = false;
+  bool iter_graph_failed = false;
   amgp2::DBuf<int> flag;           // device error word
   std::string last_error;
   int64_t launches = 0;
@@ -147,6 +163,12 @@ struct amg_handle {
   int sub_cluster = 0;                    // CTAs in the cluster (0: clusters unavailable)
   amgp2::DBuf<unsigned char> sub_ph32, sub_ph64;   // recorded phase lists
   int sub_n32 = 0, sub_n64 = 0;
+  // or the whole cycle as one persistent cooperative launch
+  bool use_full = false;
+  int grid_ctas = 0;
+  amgp2::DBuf<unsigned char> full_ph32, full_ph64;
+  int full_n32 = 0, full_n64 = 0;
+  amgp2::DBuf<unsigned> grid_bar;
   ~amg_handle();
 };
 

@@ -48,7 +48,10 @@ using namespace amgp2;
 
 amg_handle::~amg_handle() {
   if (host_scal) cudaFreeHost(host_scal);
+  if (host_int) cudaFreeHost(host_int);
   if (cycle_graph) cudaGraphExecDestroy(cycle_graph);
+  if (cg_loop_pcg) cudaGraphExecDestroy(cg_loop_pcg);
+  if (cg_loop_fcg) cudaGraphExecDestroy(cg_loop_fcg);
   L.clear();
   coarse_inv.release();
   if (own_stream) cudaStreamDestroy(own_stream);
@@ -73,6 +76,7 @@ void amg_default_options(amg_options* o) {
   o->max_iterations = 1000;
   o->use_graphs = 1;
   o->cluster_from = -1;
+  o->cycle_kernel = 0;
   o->omega = 0.5;
   o->omega_p = 0.125;
 }
@@ -117,6 +121,7 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
     }
     h->flag.alloc(1);
     AMG_CUDA(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
+    AMG_CUDA(cudaMallocHost(&h->host_int, 8 * sizeof(int)));
     auto t0 = std::chrono::steady_clock::now();
     nvtxRangePushA("amg_setup");
     struct Pop { ~Pop() { nvtxRangePop(); } } pop;
@@ -217,6 +222,12 @@ int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t
     }
     AMG_CUDA(cudaEventRecord(e1, h->stream));
     AMG_CUDA(cudaEventSynchronize(e1));
+    int ferr = 0;
+    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ferr) {
+      AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
+      fail(AMG_ERR_TIMEOUT, "a bounded device wait (grid barrier) timed out during the solve");
+    }
     float ms = 0.f;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);

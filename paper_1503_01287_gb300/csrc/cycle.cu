@@ -66,9 +66,10 @@ struct VL<true> {
 // shuffles inside the group.
 //   kApply : y_i = (A x)_i
 //   kResid : y_i = b_i - (A x)_i
-//   kGS    : x_i += D_i^{-1} (b_i - (A x)_i)   for the rows listed in `rows`
+//   kGS    : x_i += D_i^{-1} (b_i - (A x)_i)
 //   kJacobi: y_i = x_i + omega D_i^{-1} (b_i - (A x)_i)
-// D^{-1} is stored as 3 padded rows per node (12 values).
+// Stored row g holds the blocks rowptr[g]..rowptr[g+1] of node i = rows[g]
+// (i = g when rows is null).  D^{-1} is stored as 3 padded rows per node.
 template <typename T, int G, int MODE, bool COH>
 __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ rows,
                                           const int* __restrict__ rowptr,
@@ -86,7 +87,7 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
     T s0 = T(0), s1 = T(0), s2 = T(0);
     if (active) {
       i = rows ? ldg(rows + g) : g;
-      const int a = ldg(rowptr + i), e = ldg(rowptr + i + 1);
+      const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
       // U blocks per lane per step: all column indices of the step are loaded
       // before the gathers that depend on them
       constexpr int U = G >= 16 ? 2 : 4;
@@ -461,6 +462,50 @@ __global__ void __launch_bounds__(kSubThreads, 1) k_subcycle(const Phase* __rest
   }
 }
 
+// Grid-wide barrier of the persistent cycle kernel (all CTAs co-resident by
+// cooperative launch).  `count` only grows during a launch: barrier number k
+// completes when it reaches k * gridDim.x.  Every wait is bounded: after
+// kBarrierSpins polls the CTA records a timeout in *err and stops waiting; once
+// *err is set no CTA waits any more, so the kernel always ends.
+constexpr unsigned kBarrierSpins = 1u << 22;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned target, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    while (ld_acquire(count) < target) {
+      if (++spins > kBarrierSpins) { atomicOr(err, 1); break; }
+      if ((spins & 1023u) == 0 && *((volatile int*)err)) break;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// The whole recorded cycle as one persistent launch over all SMs.
+constexpr int kGridThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kGridThreads, 1) k_grid_cycle(const Phase* __restrict__ ph,
+                                                                  int nph, unsigned* bar,
+                                                                  int* err) {
+  const int nthr = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int p = 0; p < nph; ++p) {
+    const Phase P = ph[p];
+    exec_phase<T, true>(P, tid, nthr);
+    if (p + 1 < nph) grid_barrier(bar, (unsigned)(p + 1) * gridDim.x, err);
+  }
+}
+
 // ------------------------------------------------------------------- emitter
 
 inline int gridn(int64_t n, int t = 256) {
@@ -473,7 +518,7 @@ template <> struct LvVec<double> {
   static double* b(Level& l) { return l.b64; }
   static double* r(Level& l) { return l.r64; }
   static double* t(Level& l) { return l.t64; }
-  static const double* val(Level& l) { return l.val; }
+  static const double* val(Level& l) { return l.k_val(); }
   static const double* dinv(Level& l) { return l.dinv; }
   static const double* pval(Level& l) { return l.p_val; }
   static const double* rval(Level& l) { return l.r_val; }
@@ -532,10 +577,13 @@ struct Emit {
     P.type = type;
     return P;
   }
-  void rows(int mode, const Level& lv, int G, int nrows, const int* rows, const T* val,
-            const T* x, const T* b, T* y, const T* dinv, T omega) {
+  // block rows [first, first + nrows) of the level's kernel layout
+  void rows(int mode, const Level& lv, int G, int first, int nrows, const T* val, const T* x,
+            const T* b, T* y, const T* dinv, T omega) {
     Phase P = blank(PH_ROWS);
-    P.mode = mode; P.G = G; P.n = nrows; P.rows = rows; P.rowptr = lv.rowptr; P.col = lv.col;
+    const int* order = lv.k_rows();
+    P.mode = mode; P.G = G; P.n = nrows; P.rows = order ? order + first : nullptr;
+    P.rowptr = lv.k_rowptr() + first; P.col = lv.k_col();
     P.val = val; P.nnz = lv.nnzb; P.x = x; P.b = b; P.y = y; P.dinv = dinv; P.omega = omega;
     put(P, nrows, G);
   }
@@ -580,8 +628,7 @@ struct Emit {
 
 template <typename T>
 void e_apply(Emit<T>& e, Level& lv, const T* x, T* y, bool saddle) {
-  e.rows(kApply, lv, group_for(lv), lv.n, nullptr, LvVec<T>::val(lv), x, nullptr, y, nullptr,
-         T(0));
+  e.rows(kApply, lv, group_for(lv), 0, lv.n, LvVec<T>::val(lv), x, nullptr, y, nullptr, T(0));
   if (saddle && lv.np > 0) {
     const T* p = x + 4 * lv.n;
     e.bt_add(lv, p, T(1), y);
@@ -591,7 +638,7 @@ void e_apply(Emit<T>& e, Level& lv, const T* x, T* y, bool saddle) {
 
 template <typename T>
 void e_residual(Emit<T>& e, Level& lv, const T* x, const T* b, T* r, bool saddle) {
-  e.rows(kResid, lv, group_for(lv), lv.n, nullptr, LvVec<T>::val(lv), x, b, r, nullptr, T(0));
+  e.rows(kResid, lv, group_for(lv), 0, lv.n, LvVec<T>::val(lv), x, b, r, nullptr, T(0));
   if (saddle && lv.np > 0) {
     const T* p = x + 4 * lv.n;
     e.bt_add(lv, p, T(-1), r);
@@ -617,7 +664,7 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
     // u <- u + omega D^{-1} (f - B^T p - A u)    (M_A = damped block Jacobi)
     e.copy(b, r, 4 * (int64_t)lv.n);
     e.bt_add(lv, p, T(-1), r);
-    e.rows(kJacobi, lv, G, lv.n, nullptr, val, x, r, t, dinv, (T)h->opt.omega);
+    e.rows(kJacobi, lv, G, 0, lv.n, val, x, r, t, dinv, (T)h->opt.omega);
     e.copy(t, x, 4 * (int64_t)lv.n);
     // p <- p + omega_p S_D^{-1} (B u_new - C p - g)
     e.prows(2, lv, x, x + 4 * lv.n, b + 4 * lv.n, t + 4 * lv.n, (T)h->opt.omega_p);
@@ -626,7 +673,7 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
   }
   if (h->opt.smoother == AMG_SMOOTHER_JACOBI) {
     T* t = LvVec<T>::t(lv);
-    e.rows(kJacobi, lv, G, lv.n, nullptr, val, x, b, t, dinv, (T)h->opt.omega);
+    e.rows(kJacobi, lv, G, 0, lv.n, val, x, b, t, dinv, (T)h->opt.omega);
     e.copy(t, x, dofs);
     return;
   }
@@ -634,7 +681,7 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e2 = lv.colour_ptr[c + 1];
-    e.rows(kGS, lv, Ggs, e2 - a, lv.colour_rows.p + a, val, x, b, x, dinv, T(0));
+    e.rows(kGS, lv, Ggs, a, e2 - a, val, x, b, x, dinv, T(0));
   }
 }
 
@@ -756,6 +803,74 @@ struct SubCycle {
 };
 
 template <typename T>
+DBuf<unsigned char>& full_buf(amg_handle* h);
+template <>
+DBuf<unsigned char>& full_buf<float>(amg_handle* h) { return h->full_ph32; }
+template <>
+DBuf<unsigned char>& full_buf<double>(amg_handle* h) { return h->full_ph64; }
+template <typename T>
+int& full_count(amg_handle* h);
+template <>
+int& full_count<float>(amg_handle* h) { return h->full_n32; }
+template <>
+int& full_count<double>(amg_handle* h) { return h->full_n64; }
+
+// The whole preconditioner application (opt.cycles cycles of Algorithm 1 from
+// zero on the level-0 work vectors), recorded for the persistent kernel.
+template <typename T>
+struct FullCycle {
+  static void record(amg_handle* h) {
+    std::vector<Phase> ph;
+    Emit<T> e{h, &ph};
+    Level& lv = *h->L[0];
+    const int sub = h->sub_from;
+    h->sub_from = 0;   // record every level's operations
+    for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
+      cycle_rec<T>(e, h, 0, LvVec<T>::x(lv), LvVec<T>::b(lv), c == 0);
+    h->sub_from = sub;
+    DBuf<unsigned char>& d = full_buf<T>(h);
+    d.alloc(ph.size() * sizeof(Phase));
+    AMG_CUDA(cudaMemcpyAsync(d.p, ph.data(), ph.size() * sizeof(Phase), cudaMemcpyHostToDevice,
+                             h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    full_count<T>(h) = (int)ph.size();
+  }
+
+  static void launch(amg_handle* h) {
+    AMG_CUDA(cudaMemsetAsync(h->grid_bar.p, 0, sizeof(unsigned), h->stream));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(h->grid_ctas);
+    cfg.blockDim = dim3(kGridThreads);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_grid_cycle<T>,
+                                reinterpret_cast<const Phase*>(full_buf<T>(h).p),
+                                full_count<T>(h), h->grid_bar.p, h->flag.p));
+    h->launches++;
+  }
+};
+
+template <typename T>
+int grid_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  AMG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_grid_cycle<T>, kGridThreads, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * std::min(per, 1);
+}
+
+template <typename T>
 int max_clusters(int size) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(size);
@@ -813,6 +928,13 @@ void vcycle(amg_handle* h, int l, bool x_is_zero) {
 // z = M^{-1} r: opt.cycles applications of Algorithm 1 from zero.
 template <>
 void precondition_device<double>(amg_handle* h, const double* r, double* z) {
+  if (h->use_full) {
+    Level& lv = *h->L[0];
+    launch_copy(r, lv.b64, lv.dofs4(), h->stream, h);
+    FullCycle<double>::launch(h);
+    launch_copy(lv.x64, z, lv.dofs4(), h->stream, h);
+    return;
+  }
   Emit<double> e{h};
   for (int c = 0; c < std::max(1, h->opt.cycles); ++c) cycle_rec<double>(e, h, 0, z, r, c == 0);
 }
@@ -822,9 +944,13 @@ void precondition_device<float>(amg_handle* h, const double* r, double* z) {
   Level& lv = *h->L[0];
   const int64_t n = lv.dofs4();
   launch_to_float(r, lv.b32, n, h->stream, h);
-  Emit<float> e{h};
-  for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
-    cycle_rec<float>(e, h, 0, lv.x32.p, lv.b32.p, c == 0);
+  if (h->use_full) {
+    FullCycle<float>::launch(h);
+  } else {
+    Emit<float> e{h};
+    for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
+      cycle_rec<float>(e, h, 0, lv.x32.p, lv.b32.p, c == 0);
+  }
   launch_to_double(lv.x32, z, n, h->stream, h);
 }
 
@@ -928,6 +1054,37 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms * 0.98f) { best_ms = ms; best_from = from; }
     }
     set_subcycle(h, best_from);
+  }
+  // the whole cycle as one persistent cooperative launch, if it is faster
+  h->use_full = false;
+  h->grid_ctas = (h->opt.cycle_kernel != 1) ? (f32 ? grid_ctas<float>() : grid_ctas<double>()) : 0;
+  if (h->grid_ctas > 0) {
+    if (!h->grid_bar.p) h->grid_bar.alloc(1);
+    if (f32) FullCycle<float>::record(h);
+    else FullCycle<double>::record(h);
+    if (h->opt.cycle_kernel == 2) {
+      h->use_full = true;
+    } else {
+      DBuf<double> r, z;
+      const int64_t n4 = h->L[0]->dofs4();
+      r.alloc(n4);
+      z.alloc(n4);
+      AMG_CUDA(cudaMemsetAsync(r.p, 0, r.bytes(), s));
+      float t[2];
+      for (int mode = 0; mode < 2; ++mode) {
+        h->use_full = mode == 1;
+        for (int rep = 0; rep < 5; ++rep) {
+          if (rep == 2) AMG_CUDA(cudaEventRecord(e0, s));
+          if (f32) precondition_device<float>(h, r, z);
+          else precondition_device<double>(h, r, z);
+        }
+        t[mode] = elapsed();
+      }
+      h->use_full = t[1] < t[0];
+    }
+    int ferr = 0;
+    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ferr) fail(AMG_ERR_TIMEOUT, "grid barrier of the persistent cycle kernel timed out");
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

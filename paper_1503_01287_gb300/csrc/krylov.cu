@@ -15,7 +15,7 @@ namespace amgp2 {
 
 namespace {
 
-enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZN, S_ZRO, S_BB, S_BETA, S_T0, S_T1, S_NSLOTS };
+enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZN, S_ZRO, S_BB, S_BETA, S_T0, S_T1, S_TOL2, S_NSLOTS };
 constexpr int kMaxDots = 64;   // multi-dot width (FGMRES restart + 2)
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -102,6 +102,18 @@ __global__ void k_cg_beta(double* s, int flexible) {
   s[S_BETA] = num / s[S_RZ];
   s[S_RZ] = s[S_RZN];
 }
+
+// stopping rule on the device: continue while ||r||^2 > tol^2 ||b||^2, the
+// iteration limit is not reached and the residual is finite
+__global__ void k_cg_check(cudaGraphConditionalHandle cond, const double* __restrict__ s,
+                           int* it, int maxit) {
+  const int k = ++(*it);
+  const double rr = s[S_RR];
+  const bool go = !(rr <= s[S_TOL2] * s[S_BB]) && k < maxit && isfinite(rr);
+  cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+__global__ void k_set_tol2(double* s, double tol) { s[S_TOL2] = tol * tol; }
 
 __global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z,
                          const double* __restrict__ s) {
@@ -261,23 +273,93 @@ int solve_cg(amg_handle* h, Ctx& c, const double* b, double* x, double tol, bool
   body(true);
   ++it;
   rel = std::sqrt(std::max(0.0, read_scalar(h, S_RR))) / bnorm;
+  // All further iterations in one graph launch: a conditional WHILE node whose
+  // body is one iteration followed by the stopping test (k_cg_check).
+  if (h->opt.use_graphs && !(rel <= tol) && it < h->opt.max_iterations && std::isfinite(rel)) {
+    cudaGraphExec_t& wexec = flexible ? h->cg_loop_fcg : h->cg_loop_pcg;
+    int64_t& per_iter = flexible ? h->cg_loop_fcg_launches : h->cg_loop_pcg_launches;
+    if (!wexec && !h->cg_loop_failed) {
+      const int64_t l0 = h->launches;
+      cudaGraph_t g = nullptr;
+      bool capturing = false;
+      try {
+        AMG_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle cond;
+        AMG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        AMG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        AMG_CUDA(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        body(false);
+        k_cg_check<<<1, 1, 0, s>>>(cond, h->scal.p, h->it_dev.p, h->opt.max_iterations);
+        AMG_LAUNCH_CHECK();
+        capturing = false;
+        AMG_CUDA(cudaStreamEndCapture(s, &bodyg));
+        AMG_CUDA(cudaGraphInstantiate(&wexec, g, 0));
+        per_iter = h->launches - l0 + 1;
+      } catch (const Error&) {
+        if (capturing) {
+          cudaGraph_t junk = nullptr;
+          cudaStreamEndCapture(s, &junk);
+          if (junk) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        if (wexec) cudaGraphExecDestroy(wexec);
+        wexec = nullptr;
+        h->cg_loop_failed = true;   // fall back to one graph launch per iteration
+      }
+      if (g) cudaGraphDestroy(g);
+      h->launches = l0;
+    }
+    if (wexec) {
+      k_set_tol2<<<1, 1, 0, s>>>(h->scal.p, tol);
+      *h->host_int = it;
+      AMG_CUDA(cudaMemcpyAsync(h->it_dev.p, h->host_int, sizeof(int), cudaMemcpyHostToDevice, s));
+      AMG_CUDA(cudaGraphLaunch(wexec, s));
+      AMG_CUDA(cudaMemcpyAsync(h->host_int, h->it_dev.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      rel = std::sqrt(std::max(0.0, read_scalar(h, S_RR))) / bnorm;   // synchronises
+      h->launches += (int64_t)(*h->host_int - it) * per_iter + 1;
+      it = *h->host_int;
+    }
+  }
   cudaGraphExec_t exec = nullptr;
   int64_t per_iter = 0;
   const bool use_graph = h->opt.use_graphs != 0;
   while (!(rel <= tol) && it < h->opt.max_iterations) {
     if (!std::isfinite(rel)) fail(AMG_ERR_BREAKDOWN, "non-finite residual in CG");
-    if (use_graph) {
-      if (!exec) {
-        int64_t l0 = h->launches;
-        cudaGraph_t g;
+    if (use_graph && !exec && !h->iter_graph_failed) {
+      const int64_t l0 = h->launches;
+      cudaGraph_t g = nullptr;
+      bool capturing = false;
+      try {
         AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
         body(false);
+        capturing = false;
         AMG_CUDA(cudaStreamEndCapture(s, &g));
         AMG_CUDA(cudaGraphInstantiate(&exec, g, 0));
-        AMG_CUDA(cudaGraphDestroy(g));
         per_iter = h->launches - l0;
-        h->launches = l0;
+      } catch (const Error&) {
+        if (capturing) {
+          cudaGraph_t junk = nullptr;
+          cudaStreamEndCapture(s, &junk);
+          if (junk) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        exec = nullptr;
+        h->iter_graph_failed = true;   // run the iterations as plain launches
       }
+      if (g) cudaGraphDestroy(g);
+      h->launches = l0;
+    }
+    if (exec) {
       AMG_CUDA(cudaGraphLaunch(exec, s));
       h->launches += per_iter;
     } else {
@@ -442,6 +524,7 @@ int solve_device(amg_handle* h, const double* b_user, double* x_user, double tol
   ensure(h->kr, n); ensure(h->kz, n); ensure(h->kp, n); ensure(h->kq, n); ensure(h->kw, n);
   ensure(h->red, (int64_t)kReduceBlocks * kMaxDots);
   ensure(h->scal, 64);
+  if (!h->it_dev.p) h->it_dev.alloc(1);
   int krylov = h->opt.krylov;
   if (krylov == AMG_KRYLOV_AUTO)
     krylov = h->saddle ? AMG_KRYLOV_FGMRES

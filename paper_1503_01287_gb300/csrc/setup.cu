@@ -590,6 +590,33 @@ __global__ void k_colour_scatter(int n, const int* __restrict__ colour, int c,
     if (colour[i] == c) rows[offset + pos[i]] = i;
 }
 
+// stored-row lengths and block copy into colour order
+__global__ void k_stored_len(int n, const int* __restrict__ order, const int* __restrict__ rowptr,
+                             int* __restrict__ len) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int i = order[k];
+    len[k] = rowptr[i + 1] - rowptr[i];
+  }
+}
+
+__global__ void k_stored_copy(int n, const int* __restrict__ order, const int* __restrict__ rowptr,
+                              const int* __restrict__ col, const double* __restrict__ val,
+                              int64_t nnzb, const int* __restrict__ srowptr, int* __restrict__ scol,
+                              double* __restrict__ sval) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int k = w; k < n; k += nw) {
+    const int i = order[k];
+    const int a = rowptr[i], len = rowptr[i + 1] - a, o = srowptr[k];
+    for (int q = lane; q < len; q += 32) {
+      scol[o + q] = col[a + q];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) sval[e * nnzb + o + q] = val[e * nnzb + a + q];
+    }
+  }
+}
+
 // ============================================================================ block inverses
 
 __global__ void k_dinv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
@@ -1030,7 +1057,23 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
   AMG_LAUNCH_CHECK();
   h->launches++;
   if (f.read()) fail(AMG_ERR_BREAKDOWN, "singular or non-finite 3x3 diagonal block");
-  if (!coarsest && !h->saddle) colour_level(h, lv);
+  if (!coarsest && !h->saddle) {
+    colour_level(h, lv);
+    // colour-major copy of A for the cycle kernels
+    DBuf<int> len;
+    len.alloc(std::max(n, 1));
+    k_stored_len<<<grid_for(n), 256, 0, s>>>(n, lv.colour_rows, lv.rowptr, len);
+    lv.srowptr.alloc(n + 1);
+    exclusive_scan(len, lv.srowptr, n, s, h);
+    lv.scol.alloc(std::max<int64_t>(lv.nnzb, 1));
+    lv.sval.alloc(9 * (size_t)std::max<int64_t>(lv.nnzb, 1));
+    k_stored_copy<<<grid_for((int64_t)n * 32), 256, 0, s>>>(n, lv.colour_rows, lv.rowptr, lv.col,
+                                                          lv.val, lv.nnzb, lv.srowptr, lv.scol,
+                                                          lv.sval);
+    AMG_LAUNCH_CHECK();
+    h->launches += 2;
+    lv.stored = true;
+  }
   bool fp32 = h->opt.precision == AMG_FP32;
   const int dofs = lv.dofs4();
   auto zalloc64 = [&](DBuf<double>& v) {
@@ -1044,7 +1087,7 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
   zalloc64(lv.x64); zalloc64(lv.b64); zalloc64(lv.r64); zalloc64(lv.t64);
   if (fp32) {
     lv.val32.alloc(9 * (size_t)std::max<int64_t>(lv.nnzb, 1));
-    launch_to_float(lv.val, lv.val32, 9 * lv.nnzb, s, h);
+    launch_to_float(lv.k_val(), lv.val32, 9 * lv.nnzb, s, h);
     lv.dinv32.alloc(12 * (size_t)std::max(n, 1));
     launch_to_float(lv.dinv, lv.dinv32, 12 * (int64_t)n, s, h);
     if (!coarsest) {

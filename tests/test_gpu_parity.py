@@ -199,17 +199,20 @@ def test_smoothing_sweep_matches_oracle(smoother):
             assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("kind,cluster_from", [
-    ("elasticity", 0), ("elasticity", 1), ("elasticity", 2), ("laplace", -1), ("laplace", 1),
-    ("mixed", 0), ("mixed", 1), ("stokes", 0), ("stokes", 1)])
-def test_preconditioner_matches_oracle(kind, cluster_from):
-    """One preconditioner application; cluster_from selects from which level the
-    cycle runs as one thread-block-cluster launch (0: one launch per operation)."""
+@pytest.mark.parametrize("kind,cluster_from,cycle_kernel", [
+    ("elasticity", 0, 1), ("elasticity", 1, 1), ("elasticity", 2, 1), ("elasticity", 0, 2),
+    ("laplace", -1, 0), ("laplace", 1, 1), ("laplace", 0, 2),
+    ("mixed", 0, 1), ("mixed", 1, 1), ("mixed", 0, 2), ("stokes", 0, 1), ("stokes", 1, 1),
+    ("stokes", 0, 2)])
+def test_preconditioner_matches_oracle(kind, cluster_from, cycle_kernel):
+    """One preconditioner application.  cluster_from: from which level the cycle
+    runs as one thread-block-cluster launch (0: one launch per operation);
+    cycle_kernel 2: the whole cycle as one persistent launch."""
     prob = {"elasticity": lambda: fp.elasticity_problem(8, seed=7),
             "laplace": lambda: fp.vector_laplace_problem(5, seed=1),
             "mixed": lambda: fp.mixed_elasticity_problem(4, nu=0.49, seed=5),
             "stokes": lambda: fp.stokes_lid_problem(4)}[kind]()
-    h = gpu(prob, cluster_from=cluster_from)
+    h = gpu(prob, cluster_from=cluster_from, cycle_kernel=cycle_kernel)
     oh = amg.build_hierarchy(prob, oracle_opts(prob))
     if kind == "stokes":
         # The Galerkin Stokes coarsest matrix is singular; any solution of a consistent
@@ -263,6 +266,8 @@ def test_solve_vector_laplace_workload():
     ({"cluster_from": 0}, {}),
     ({"cluster_from": 1, "nu": 2}, {"nu": 2}),
     ({"cluster_from": 2, "smoother": 1}, {"smoother": "jacobi"}),
+    ({"cycle_kernel": 2}, {}),
+    ({"cycle_kernel": 2, "nu": 2, "m_pre": 2, "m_post": 2}, {"nu": 2, "m_pre": 2, "m_post": 2}),
     ({"smoother": 1}, {"smoother": "jacobi"}),
     ({"nu": 2}, {"nu": 2}),
     ({"m_pre": 2, "m_post": 2}, {"m_pre": 2, "m_post": 2}),
@@ -296,10 +301,10 @@ def test_standalone_amg_matches_oracle():
     assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("cluster_from", [0, 1, 2])
-def test_fp32_cycle_flexible_cg(cluster_from):
+@pytest.mark.parametrize("cluster_from,cycle_kernel", [(0, 1), (1, 1), (2, 1), (0, 2)])
+def test_fp32_cycle_flexible_cg(cluster_from, cycle_kernel):
     prob = fp.elasticity_problem(10, seed=1)
-    h = gpu(prob, precision=B().AMG_FP32, cluster_from=cluster_from)
+    h = gpu(prob, precision=B().AMG_FP32, cluster_from=cluster_from, cycle_kernel=cycle_kernel)
     st, x = _solve(h, prob, 1e-8)
     ref, _ = amg.solve(prob, tol=1e-12)
     assert st.converged and st.true_rel_residual <= 1.5e-8
@@ -331,9 +336,10 @@ def test_saddle_fgmres_matches_oracle(kind):
         assert abs(prob.p_weights @ x[n3:]) <= 1e-12 * np.abs(x[n3:]).max() * prob.n_pres
 
 
-def test_fp32_saddle():
+@pytest.mark.parametrize("cycle_kernel", [1, 2])
+def test_fp32_saddle(cycle_kernel):
     prob = fp.mixed_elasticity_problem(5, nu=0.499, seed=5)
-    h = gpu(prob, precision=B().AMG_FP32)
+    h = gpu(prob, precision=B().AMG_FP32, cycle_kernel=cycle_kernel)
     st, x = _solve(h, prob, 1e-8)
     assert st.converged and st.true_rel_residual <= 1.5e-8
 

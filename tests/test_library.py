@@ -46,7 +46,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(amg_matrix), sizeof(amg_options), sizeof(amg_stats),
          sizeof(amg_level_info));
   printf("%zu %zu %zu %zu\n", offsetof(amg_matrix, device_ptrs), offsetof(amg_options, omega_p),
-         offsetof(amg_stats, level_colours), offsetof(amg_options, cluster_from));
+         offsetof(amg_stats, level_colours), offsetof(amg_options, cycle_kernel));
   return 0;
 }
 '''
@@ -64,7 +64,7 @@ int main(void) {
     assert sizes[4] == B.AmgMatrix.device_ptrs.offset
     assert sizes[5] == B.AmgOptions.omega_p.offset
     assert sizes[6] == B.AmgStats.level_colours.offset
-    assert sizes[7] == B.AmgOptions.cluster_from.offset
+    assert sizes[7] == B.AmgOptions.cycle_kernel.offset
 
 
 def test_default_options(lib):
