@@ -165,6 +165,7 @@ struct amg_handle {
   int sub_n32 = 0, sub_n64 = 0;
   // or the whole cycle as one persistent cooperative launch
   bool use_full = false;
+  bool use_pdl = true;      // colour kernels with programmatic dependent launch
   int grid_ctas = 0;
   amgp2::DBuf<unsigned char> full_ph32, full_ph64;
   int full_n32 = 0, full_n64 = 0;

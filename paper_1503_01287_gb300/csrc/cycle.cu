@@ -85,12 +85,19 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
     const bool active = g < nrows;
     int i = 0;
     T s0 = T(0), s1 = T(0), s2 = T(0);
+    // operands of the row update that depend only on the row: loaded before the
+    // row's blocks so that they are not on the critical path
+    T b0 = T(0), b1 = T(0), b2 = T(0), xi0 = T(0), xi1 = T(0), xi2 = T(0);
     if (active) {
       i = rows ? ldg(rows + g) : g;
+      if (MODE != kApply && gl == 0) {
+        VL<COH>::node(b, i, b0, b1, b2);
+        if (MODE != kResid) VL<COH>::node(x, i, xi0, xi1, xi2);
+      }
       const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
       // U blocks per lane per step: all column indices of the step are loaded
       // before the gathers that depend on them
-      constexpr int U = G >= 16 ? 2 : 4;
+      constexpr int U = G >= 32 ? 3 : (G >= 16 ? 2 : 4);
       for (int k0 = a + gl; k0 < e; k0 += U * G) {
         int j[U];
 #pragma unroll
@@ -124,8 +131,6 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
       st3(y, i, s0, s1, s2);
       continue;
     }
-    T b0, b1, b2;
-    VL<COH>::node(b, i, b0, b1, b2);
     const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
     if (MODE == kResid) {
       st3(y, i, r0, r1, r2);
@@ -139,10 +144,8 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
     const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
     ld3(d, 2, d0, d1, d2);
     const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
-    T x0, x1, x2;
-    VL<COH>::node(x, i, x0, x1, x2);
-    if (MODE == kGS) st3(y, i, x0 + c0, x1 + c1, x2 + c2);
-    else st3(y, i, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
+    if (MODE == kGS) st3(y, i, xi0 + c0, xi1 + c1, xi2 + c2);
+    else st3(y, i, xi0 + omega * c0, xi1 + omega * c1, xi2 + omega * c2);
   }
 }
 
@@ -407,6 +410,112 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
   }
 }
 
+// Multicolour Gauss-Seidel for one colour, launched with programmatic dependent
+// launch: everything the row update reads except x (row ids, block columns and
+// values, b_i, D_i^{-1}) is loaded before griddepcontrol.wait, so this prologue
+// overlaps the previous colour's kernel; after the wait only the x gathers and
+// the update remain.  Neither the previous colour's kernel nor any operation
+// it overlaps writes those operands (it writes x of its own rows only).
+// One group of G lanes per stored row; each lane prefetches up to U blocks.
+template <typename T, int G, int U>
+__global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict__ rows,
+                                                const int* __restrict__ rowptr,
+                                                const int* __restrict__ col,
+                                                const T* __restrict__ val, int64_t nnzb, T* x,
+                                                const T* __restrict__ b,
+                                                const T* __restrict__ dinv) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int gl = threadIdx.x & (G - 1);
+  const bool active = g < nrows;
+  int i = 0, a = 0, e = 0;
+  int j[U];
+  T v[U][9];
+  T b0 = T(0), b1 = T(0), b2 = T(0);
+  T d[9];
+#pragma unroll
+  for (int u = 0; u < U; ++u) j[u] = -1;
+  if (active) {
+    i = ldg(rows + g);
+    a = ldg(rowptr + g);
+    e = ldg(rowptr + g + 1);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = a + gl + u * G;
+      if (k < e) {
+        j[u] = ldg(col + k);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[u][q] = ldg(val + q * nnzb + k);
+      }
+    }
+    if (gl == 0) {
+      ld3(b, i, b0, b1, b2);
+      const T* dp = dinv + 12 * (int64_t)i;
+      ld3(dp, 0, d[0], d[1], d[2]);
+      ld3(dp, 1, d[3], d[4], d[5]);
+      ld3(dp, 2, d[6], d[7], d[8]);
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  T xi0 = T(0), xi1 = T(0), xi2 = T(0);
+  if (active) {
+    if (gl == 0) VL<true>::node(x, i, xi0, xi1, xi2);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j[u] < 0) continue;
+      T x0, x1, x2;
+      VL<true>::node(x, j[u], x0, x1, x2);
+      s0 = fma(v[u][0], x0, s0); s0 = fma(v[u][1], x1, s0); s0 = fma(v[u][2], x2, s0);
+      s1 = fma(v[u][3], x0, s1); s1 = fma(v[u][4], x1, s1); s1 = fma(v[u][5], x2, s1);
+      s2 = fma(v[u][6], x0, s2); s2 = fma(v[u][7], x1, s2); s2 = fma(v[u][8], x2, s2);
+    }
+    // blocks beyond the prefetched U per lane
+    for (int k = a + gl + U * G; k < e; k += G) {
+      const int jj = ldg(col + k);
+      T x0, x1, x2;
+      VL<true>::node(x, jj, x0, x1, x2);
+      const T* vv = val + k;
+      s0 = fma(ldg(vv), x0, s0);
+      s0 = fma(ldg(vv + nnzb), x1, s0);
+      s0 = fma(ldg(vv + 2 * nnzb), x2, s0);
+      s1 = fma(ldg(vv + 3 * nnzb), x0, s1);
+      s1 = fma(ldg(vv + 4 * nnzb), x1, s1);
+      s1 = fma(ldg(vv + 5 * nnzb), x2, s1);
+      s2 = fma(ldg(vv + 6 * nnzb), x0, s2);
+      s2 = fma(ldg(vv + 7 * nnzb), x1, s2);
+      s2 = fma(ldg(vv + 8 * nnzb), x2, s2);
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (!active || gl != 0) return;
+  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+  st3(x, i, xi0 + d[0] * r0 + d[1] * r1 + d[2] * r2, xi1 + d[3] * r0 + d[4] * r1 + d[5] * r2,
+      xi2 + d[6] * r0 + d[7] * r1 + d[8] * r2);
+}
+
+template <typename T, int G>
+void launch_gs_pdl(const Phase& P, cudaStream_t s) {
+  constexpr int U = (sizeof(T) == 8) ? (G >= 16 ? 2 : 3) : (G >= 16 ? 3 : 4);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(((int64_t)P.n * G + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U>, P.n, P.rows, P.rowptr, P.col,
+                              (const T*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
+                              (const T*)P.dinv));
+}
+
 // one operation as its own kernel
 template <typename T>
 __global__ void __launch_bounds__(256) k_phase(const Phase P) {
@@ -433,7 +542,15 @@ void launch_rows_mode(const Phase& P, int grid, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_rows(const Phase& P, cudaStream_t s) {
+void launch_rows(const Phase& P, cudaStream_t s, bool pdl) {
+  if (pdl && P.mode == kGS && P.rows) {
+    switch (P.G) {
+      case 4: launch_gs_pdl<T, 4>(P, s); return;
+      case 8: launch_gs_pdl<T, 8>(P, s); return;
+      case 16: launch_gs_pdl<T, 16>(P, s); return;
+      default: launch_gs_pdl<T, 32>(P, s); return;
+    }
+  }
   // one group of G lanes per row: nrows * G threads
   const int grid = (int)(((int64_t)P.n * P.G + 255) / 256);
   switch (P.G) {
@@ -567,7 +684,7 @@ struct Emit {
       return;
     }
     if (work <= 0) return;
-    if (P.type == PH_ROWS) launch_rows<T>(P, h->stream);
+    if (P.type == PH_ROWS) launch_rows<T>(P, h->stream, h->opt.use_graphs != 0 && h->use_pdl);
     else k_phase<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
     h->launches++;
   }
