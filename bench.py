@@ -328,7 +328,11 @@ def run_profile(args):
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
     for prec in (B.AMG_FP32, B.AMG_FP64):
-        h = B.setup_problem(prob, B.default_options(precision=prec), stream=stream.cuda_stream)
+        # the launch configuration the bench selects (one launch per operation with
+        # programmatic dependent launch), without graph replay so that a profiler
+        # sees every kernel
+        opts = B.default_options(precision=prec, cycle_kernel=1, cluster_from=0, use_graphs=0)
+        h = B.setup_problem(prob, opts, stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)
         h.free()

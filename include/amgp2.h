@@ -250,6 +250,30 @@ int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t
  */
 int amg_set_pressure_weights(amg_handle* h, const double* w, int32_t device_ptrs);
 
+/*
+ * amg_solve_batched -- several SPD problems (each set up by amg_setup, kinds
+ * AMG_VECTOR_LAPLACE / AMG_ELASTICITY, any sizes), each with n_rhs right-hand
+ * sides, solved together: the multi-right-hand-side form of amg_solve.  The
+ * cycle kernels work on all right-hand sides of a problem at once (block-row
+ * times 16-column block: SpMM), each right-hand side runs its own flexible CG
+ * with the stopping rule of amg_solve, and all problems run as parallel
+ * branches of ONE CUDA graph launch (each branch an initial block and a
+ * device-side loop with its own stopping test).
+ *   handles     n_problems handles (their precision and options apply).
+ *   n_rhs       1..16 right-hand sides per problem.
+ *   B, X        per problem: device pointers to n_rhs vectors of 3*n_nodes
+ *               doubles, vector r at offset r*3*n_nodes; X receives the
+ *               solutions (x0 = 0).
+ *   stats       NULL or an array of n_problems; solve_ms is the graph's device
+ *               time, iterations the loop count (the slowest right-hand side),
+ *               true_rel_residual the worst right-hand side.
+ * Returns AMG_OK when every right-hand side converged, AMG_NOT_CONVERGED when
+ * some stopped at max_iterations.  Synchronises the first handle's stream.
+ */
+int amg_solve_batched(amg_handle* const* handles, int32_t n_problems, int32_t n_rhs,
+                      const double* const* B, double* const* X, double rel_tol,
+                      amg_stats* stats);
+
 /* Releases the handle and all its device memory.  NULL is accepted. */
 void amg_free(amg_handle* h);
 

@@ -39,7 +39,7 @@ KINDS = {"laplace": AMG_VECTOR_LAPLACE, "elasticity": AMG_ELASTICITY,
 EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
             "amg_level_info_get", "amg_level_copy", "amg_apply_preconditioner",
             "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
-            "amg_time_level_op"]
+            "amg_time_level_op", "amg_solve_batched"]
 
 OPS = {"apply": 0, "residual": 1, "smooth": 2, "restrict": 3, "prolong": 4, "precond": 5}
 
@@ -131,6 +131,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_time_level_op.argtypes = [vp, i32, i32, i32, i32, i32, C.POINTER(dbl),
                                       C.POINTER(i32)]
     lib.amg_time_level_op.restype = C.c_int
+    lib.amg_solve_batched.argtypes = [C.POINTER(vp), i32, i32, C.POINTER(vp), C.POINTER(vp), dbl,
+                                      C.POINTER(AmgStats)]
+    lib.amg_solve_batched.restype = C.c_int
     _lib = lib
     return lib
 
@@ -296,3 +299,18 @@ def setup_problem(prob, options: AmgOptions | None = None, stream=None) -> Handl
     if prob.kind == "stokes" and getattr(prob, "p_weights", None) is not None:
         h.set_pressure_weights(np.ascontiguousarray(prob.p_weights, dtype=np.float64))
     return h
+
+
+def solve_batched(handles, B_list, X_list, n_rhs: int, tol: float):
+    """amg_solve_batched over device tensors: B_list[p], X_list[p] hold n_rhs vectors of
+    3*n_nodes doubles each (vector r at offset r*3*n_nodes).  Returns (rc, [stats])."""
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.h.value for h in handles])
+    bs = (C.c_void_p * n)(*[_ptr(b) for b in B_list])
+    xs = (C.c_void_p * n)(*[_ptr(x) for x in X_list])
+    st = (AmgStats * n)()
+    rc = load_library().amg_solve_batched(C.cast(hs, C.POINTER(C.c_void_p)), n, n_rhs,
+                                          C.cast(bs, C.POINTER(C.c_void_p)),
+                                          C.cast(xs, C.POINTER(C.c_void_p)), tol, st)
+    _check(rc, handles[0].h)
+    return rc, [st[i] for i in range(n)]

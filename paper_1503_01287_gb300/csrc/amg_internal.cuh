@@ -87,6 +87,7 @@ struct Level {
   double avg_row_blocks = 0.0;
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
   int group_gs = 0;     // the same for the colour-subset Gauss-Seidel kernel
+  int group64 = 0;      // the FP64 operator kernel when the cycle runs in FP32
 
   // transfer to level+1 (absent on the coarsest level)
   DBuf<int> state, cid;
@@ -123,6 +124,13 @@ struct Level {
 
   int dofs() const { return 3 * n + np; }    // unknowns (user layout)
   int dofs4() const { return 4 * n + np; }   // padded cycle layout
+};
+
+// multi-right-hand-side work vectors of one level ([node][kRhs][4])
+constexpr int kRhs = 16;
+struct BatchLevel {
+  DBuf<double> x64, b64, r64, t64;
+  DBuf<float> x32, b32, r32, t32;
 };
 
 }  // namespace amgp2
@@ -170,6 +178,10 @@ struct amg_handle {
   amgp2::DBuf<unsigned char> full_ph32, full_ph64;
   int full_n32 = 0, full_n64 = 0;
   amgp2::DBuf<unsigned> grid_bar;
+  // batched (multi-right-hand-side) solves
+  std::vector<amgp2::BatchLevel> B;
+  amgp2::DBuf<double> mb, mx, mr, mz, mp, mq, mro, bred, bscal;
+  amgp2::DBuf<int> bit;
   ~amg_handle();
 };
 
@@ -211,6 +223,10 @@ void set_subcycle(amg_handle* h, int from);
 
 // krylov (krylov.cu)
 int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st);
+
+// batched.cu: all problems and right-hand sides in one graph launch
+int solve_batched(amg_handle* const* hs, int np, int nrhs, const double* const* B,
+                  double* const* X, double tol, amg_stats* stats, double* ms_out);
 
 // small kernels shared across files
 void launch_copy(const double* a, double* b, int64_t n, cudaStream_t s, amg_handle* h);

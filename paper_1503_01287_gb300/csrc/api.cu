@@ -507,4 +507,20 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
   });
 }
 
+int amg_solve_batched(amg_handle* const* handles, int32_t n_problems, int32_t n_rhs,
+                      const double* const* B, double* const* X, double rel_tol,
+                      amg_stats* stats) {
+  amg_handle* h0 = (handles && n_problems > 0) ? handles[0] : nullptr;
+  return guarded(h0, [&]() -> int {
+    if (!handles || !B || !X || n_problems <= 0) fail(AMG_ERR_INVALID, "null argument");
+    if (!(rel_tol > 0.0)) fail(AMG_ERR_INVALID, "rel_tol must be > 0");
+    for (int p = 0; p < n_problems; ++p)
+      if (!handles[p] || !B[p] || !X[p]) fail(AMG_ERR_INVALID, "null handle or vector");
+    nvtxRangePushA("amg_solve_batched");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
+    double ms = 0.0;
+    return solve_batched(handles, n_problems, n_rhs, B, X, rel_tol, stats, &ms);
+  });
+}
+
 }  // extern "C"

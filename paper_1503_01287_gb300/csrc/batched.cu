@@ -1,0 +1,680 @@
+// Batched solves: several SPD problems (each with its own hierarchy from
+// amg_setup), each with up to kRhs right-hand sides, solved together.
+//
+// Multi-right-hand-side vectors are stored [node][rhs][4] (padded nodes, the
+// right-hand sides of one node contiguous), so the block-row kernels are SpMM:
+// one lane per right-hand side, the 9 block values and the column index are
+// the same address for all lanes of a row (broadcast), and the gather of x_j
+// for all right-hand sides is one contiguous 16 x 16-byte (FP32) access.
+//
+// Each problem runs flexible CG per right-hand side (Polak-Ribiere beta, the
+// FP64 outer iteration of the FP32 or FP64 cycle); converged right-hand sides
+// are frozen (alpha = beta = 0).  The whole batch is ONE CUDA graph: one branch
+// per problem, each branch an initial block followed by a conditional WHILE
+// node whose body is one iteration and its device-side stopping test.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "amg_internal.cuh"
+#include "vec.cuh"
+
+namespace amgp2 {
+
+namespace {
+
+constexpr int K = kRhs;   // right-hand sides per block vector
+
+enum MMode { mApply = 0, mResid = 1, mGS = 2, mJacobi = 3 };
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// 16 lanes per stored row, lane r = right-hand side r.  Row data at
+// rowptr[g]..rowptr[g+1] (colour-major storage when rows != null).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict__ rows,
+                                                const int* __restrict__ rowptr,
+                                                const int* __restrict__ col,
+                                                const T* __restrict__ val, int64_t nnzb,
+                                                const T* x, const T* __restrict__ b, T* y,
+                                                const T* __restrict__ dinv, T omega) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / K;
+  const int r = threadIdx.x % K;
+  if (g >= nrows) return;
+  const int i = rows ? ldg(rows + g) : g;
+  const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll 2
+  for (int k = a; k < e; ++k) {
+    const int j = ldg(col + k);
+    T x0, x1, x2;
+    ld3(x, j * K + r, x0, x1, x2);
+    const T* v = val + k;
+    s0 = fma(ldg(v), x0, s0);
+    s0 = fma(ldg(v + nnzb), x1, s0);
+    s0 = fma(ldg(v + 2 * nnzb), x2, s0);
+    s1 = fma(ldg(v + 3 * nnzb), x0, s1);
+    s1 = fma(ldg(v + 4 * nnzb), x1, s1);
+    s1 = fma(ldg(v + 5 * nnzb), x2, s1);
+    s2 = fma(ldg(v + 6 * nnzb), x0, s2);
+    s2 = fma(ldg(v + 7 * nnzb), x1, s2);
+    s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+  }
+  const int o = i * K + r;
+  if (MODE == mApply) {
+    st3(y, o, s0, s1, s2);
+    return;
+  }
+  T b0, b1, b2;
+  ld3(b, o, b0, b1, b2);
+  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+  if (MODE == mResid) {
+    st3(y, o, r0, r1, r2);
+    return;
+  }
+  const T* d = dinv + 12 * (int64_t)i;
+  T d0, d1, d2;
+  ld3(d, 0, d0, d1, d2);
+  const T c0 = d0 * r0 + d1 * r1 + d2 * r2;
+  ld3(d, 1, d0, d1, d2);
+  const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
+  ld3(d, 2, d0, d1, d2);
+  const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
+  T x0, x1, x2;
+  ld3(x, o, x0, x1, x2);
+  if (MODE == mGS) st3(y, o, x0 + c0, x1 + c1, x2 + c2);
+  else st3(y, o, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
+}
+
+// bc_(I,r) = sum_t w_t v_(i_t, r)
+template <typename T>
+__global__ void k_restrict_m(int nc, const int* __restrict__ rrow, const int* __restrict__ rcol,
+                             const T* __restrict__ rval, const T* __restrict__ v,
+                             T* __restrict__ bc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = t / K, r = t % K;
+  if (I >= nc) return;
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  for (int q = rrow[I]; q < rrow[I + 1]; ++q) {
+    const T w = rval[q];
+    T a0, a1, a2;
+    ld3(v, rcol[q] * K + r, a0, a1, a2);
+    s0 = fma(w, a0, s0);
+    s1 = fma(w, a1, s1);
+    s2 = fma(w, a2, s2);
+  }
+  st3(bc, I * K + r, s0, s1, s2);
+}
+
+// x_(i,r) += sum_q P_iq xc_(q,r)
+template <typename T>
+__global__ void k_prolong_m(int n, const int* __restrict__ prow, const int* __restrict__ pcol,
+                            const T* __restrict__ pval, const T* __restrict__ xc, T* x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / K, r = t % K;
+  if (i >= n) return;
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  for (int q = prow[i]; q < prow[i + 1]; ++q) {
+    const T w = pval[q];
+    T a0, a1, a2;
+    ld3(xc, pcol[q] * K + r, a0, a1, a2);
+    s0 = fma(w, a0, s0);
+    s1 = fma(w, a1, s1);
+    s2 = fma(w, a2, s2);
+  }
+  T x0, x1, x2;
+  ld3(x, i * K + r, x0, x1, x2);
+  st3(x, i * K + r, x0 + s0, x1 + s1, x2 + s2);
+}
+
+// coarsest solve x = X b per right-hand side (X indexed 3 per node)
+template <typename T>
+__global__ void k_coarse_m(int m, const double* __restrict__ X, const T* __restrict__ b,
+                           T* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / K, r = t % K;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int j = 0; j < m; ++j)
+    s = fma(X[(int64_t)i * m + j], (double)b[((j / 3) * K + r) * 4 + j % 3], s);
+  x[((i / 3) * K + r) * 4 + i % 3] = (T)s;
+}
+
+template <typename T>
+__global__ void k_fill_m(T* a, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    a[k] = T(0);
+}
+
+template <typename T>
+__global__ void k_copy_m(const T* __restrict__ a, T* __restrict__ b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = a[k];
+}
+
+__global__ void k_sub_m(const double* __restrict__ a, const double* __restrict__ b,
+                        double* __restrict__ c, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    c[k] = a[k] - b[k];
+}
+
+__global__ void k_d2f_m(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = (float)a[k];
+}
+
+__global__ void k_f2d_m(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = (double)a[k];
+}
+
+// user layout (nrhs vectors of 3n, vector r at offset r*3n) <-> [node][K][4]
+__global__ void k_user_to_m(const double* __restrict__ u, double* __restrict__ v, int n,
+                            int nrhs) {
+  const int64_t tot = (int64_t)n * K * 4;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < tot;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(f & 3);
+    const int r = (int)((f >> 2) % K);
+    const int64_t node = (f >> 2) / K;
+    v[f] = (c < 3 && r < nrhs) ? u[(int64_t)r * 3 * n + 3 * node + c] : 0.0;
+  }
+}
+
+__global__ void k_m_to_user(const double* __restrict__ v, double* __restrict__ u, int n,
+                            int nrhs) {
+  const int64_t tot = (int64_t)nrhs * 3 * n;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < tot;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = f / (3 * (int64_t)n);
+    const int64_t rem = f % (3 * (int64_t)n);
+    u[f] = v[((rem / 3) * K + r) * 4 + rem % 3];
+  }
+}
+
+// ---------------------------------------------------------------- Krylov per right-hand side
+
+constexpr int kDotBlocks = 304;
+constexpr int kDotThreads = 256;   // a multiple of 4K: a thread always sees one rhs
+
+// partial[blk][d][r] = sum of a_d * b_d over the block's entries of right-hand side r
+__global__ void k_dots_m(int64_t nel, int nd, const double* a0, const double* b0,
+                         const double* a1, const double* b1, double* __restrict__ partial) {
+  __shared__ double sh[kDotThreads];
+  const int rr = (threadIdx.x >> 2) % K;
+  for (int d = 0; d < nd; ++d) {
+    const double* x = d == 0 ? a0 : a1;
+    const double* y = d == 0 ? b0 : b1;
+    double acc = 0.0;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nel;
+         f += (int64_t)gridDim.x * blockDim.x)
+      acc = fma(x[f], y[f], acc);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double t = 0.0;
+      for (int q = 0; q < kDotThreads; ++q)
+        if (((q >> 2) % K) == (int)threadIdx.x) t += sh[q];
+      partial[(blockIdx.x * nd + d) * K + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  (void)rr;
+}
+
+__global__ void k_final_m(const double* __restrict__ partial, int nblk, int nd,
+                          double* __restrict__ out) {
+  const int t = threadIdx.x;   // nd * K threads
+  if (t >= nd * K) return;
+  const int d = t / K, r = t % K;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(b * nd + d) * K + r];
+  out[d * K + r] = s;
+}
+
+// scalar slots, each K wide
+enum MSlot { M_RZ = 0, M_PQ, M_RR, M_RZN, M_ZRO, M_BB, M_BETA, M_ACT, M_TOL2, M_ITS, M_NS };
+
+__global__ void k_update_m(int64_t nel, double* __restrict__ x, double* __restrict__ r,
+                           const double* __restrict__ p, const double* __restrict__ q,
+                           double* __restrict__ ro, const double* __restrict__ s,
+                           double* __restrict__ partial) {
+  __shared__ double sh[kDotThreads];
+  const int rhs = (threadIdx.x >> 2) % K;
+  const bool act = s[M_ACT * K + rhs] != 0.0;
+  const double pq = s[M_PQ * K + rhs];
+  const double alpha = (act && pq != 0.0) ? s[M_RZ * K + rhs] / pq : 0.0;
+  double acc = 0.0;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nel;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    x[f] = fma(alpha, p[f], x[f]);
+    const double rk = r[f];
+    ro[f] = rk;
+    const double rn = fma(-alpha, q[f], rk);
+    r[f] = rn;
+    acc = fma(rn, rn, acc);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int qq = 0; qq < kDotThreads; ++qq)
+      if (((qq >> 2) % K) == (int)threadIdx.x) t += sh[qq];
+    partial[blockIdx.x * K + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_beta_m(double* s) {
+  const int r = threadIdx.x;
+  if (r >= K) return;
+  const bool act = s[M_ACT * K + r] != 0.0;
+  const double rz = s[M_RZ * K + r];
+  s[M_BETA * K + r] = (act && rz != 0.0) ? (s[M_RZN * K + r] - s[M_ZRO * K + r]) / rz : 0.0;
+  s[M_RZ * K + r] = s[M_RZN * K + r];
+}
+
+__global__ void k_dir_m(int64_t nel, double* __restrict__ p, const double* __restrict__ z,
+                        const double* __restrict__ s) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nel;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int rhs = (int)((f >> 2) % K);
+    p[f] = fma(s[M_BETA * K + rhs], p[f], z[f]);
+  }
+}
+
+// active_r = b_r != 0 at the start
+__global__ void k_init_m(double* s, double tol, int nrhs, int* it) {
+  const int r = threadIdx.x;
+  if (r < K) {
+    s[M_ACT * K + r] = (r < nrhs && s[M_BB * K + r] > 0.0) ? 1.0 : 0.0;
+    s[M_TOL2 * K + r] = tol * tol;
+    s[M_ITS * K + r] = 0.0;
+  }
+  if (r == 0) *it = 0;
+}
+
+// after an update: freeze converged right-hand sides; continue while any is
+// active, the iteration limit is not reached and no residual is non-finite
+__global__ void k_check_m(cudaGraphConditionalHandle cond, double* s, int* it, int maxit) {
+  __shared__ int any;
+  const int r = threadIdx.x;
+  if (r == 0) any = 0;
+  __syncthreads();
+  const int k = *it + 1;
+  if (r < K && s[M_ACT * K + r] != 0.0) {
+    const double rr = s[M_RR * K + r];
+    if (!(rr > s[M_TOL2 * K + r] * s[M_BB * K + r]) || !isfinite(rr)) {
+      s[M_ACT * K + r] = 0.0;
+      s[M_ITS * K + r] = (double)k;
+    } else {
+      atomicOr(&any, 1);
+      s[M_ITS * K + r] = (double)k;
+    }
+  }
+  __syncthreads();
+  if (r == 0) {
+    *it = k;
+    cudaGraphSetConditional(cond, (any && k < maxit) ? 1u : 0u);
+  }
+}
+
+inline int gridk(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+}
+
+// ---------------------------------------------------------------- multi-RHS cycle
+
+template <typename T> struct MV;
+template <> struct MV<double> {
+  static double* x(BatchLevel& l) { return l.x64; }
+  static double* b(BatchLevel& l) { return l.b64; }
+  static double* r(BatchLevel& l) { return l.r64; }
+  static double* t(BatchLevel& l) { return l.t64; }
+  static const double* val(Level& l) { return l.k_val(); }
+  static const double* dinv(Level& l) { return l.dinv; }
+  static const double* pval(Level& l) { return l.p_val; }
+  static const double* rval(Level& l) { return l.r_val; }
+};
+template <> struct MV<float> {
+  static float* x(BatchLevel& l) { return l.x32; }
+  static float* b(BatchLevel& l) { return l.b32; }
+  static float* r(BatchLevel& l) { return l.r32; }
+  static float* t(BatchLevel& l) { return l.t32; }
+  static const float* val(Level& l) { return l.val32; }
+  static const float* dinv(Level& l) { return l.dinv32; }
+  static const float* pval(Level& l) { return l.p_val32; }
+  static const float* rval(Level& l) { return l.r_val32; }
+};
+
+template <typename T>
+void rows_m(amg_handle* h, int mode, Level& lv, int first, int nrows, const T* val, const T* x,
+            const T* b, T* y, const T* dinv, T omega) {
+  if (nrows <= 0) return;
+  const int* order = lv.k_rows();
+  const int* rows = order ? order + first : nullptr;
+  const int* rowptr = lv.k_rowptr() + first;
+  const int grid = (int)(((int64_t)nrows * K + 255) / 256);
+  cudaStream_t s = h->stream;
+  switch (mode) {
+    case mApply:
+      k_rows_m<T, mApply><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      break;
+    case mResid:
+      k_rows_m<T, mResid><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      break;
+    case mGS:
+      k_rows_m<T, mGS><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      break;
+    default:
+      k_rows_m<T, mJacobi><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      break;
+  }
+  h->launches++;
+}
+
+template <typename T>
+void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
+  Level& lv = *h->L[l];
+  BatchLevel& bl = h->B[l];
+  if (h->opt.smoother == AMG_SMOOTHER_JACOBI) {
+    T* t = MV<T>::t(bl);
+    rows_m<T>(h, mJacobi, lv, 0, lv.n, MV<T>::val(lv), x, b, t, MV<T>::dinv(lv), (T)h->opt.omega);
+    k_copy_m<T><<<gridk(4 * (int64_t)K * lv.n), 256, 0, h->stream>>>(t, x, 4 * (int64_t)K * lv.n);
+    h->launches++;
+    return;
+  }
+  for (int q = 0; q < lv.ncolours; ++q) {
+    const int c = post ? lv.ncolours - 1 - q : q;
+    const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
+    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(0));
+  }
+}
+
+// Algorithm 1 on level l for all right-hand sides at once
+template <typename T>
+void cycle_m(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
+  const int L = (int)h->L.size() - 1;
+  cudaStream_t s = h->stream;
+  if (l == L) {
+    const int m = h->coarse_m;
+    k_coarse_m<T><<<gridk((int64_t)m * K), 256, 0, s>>>(m, h->coarse_inv, b, x);
+    h->launches++;
+    return;
+  }
+  Level& lv = *h->L[l];
+  Level& nx = *h->L[l + 1];
+  BatchLevel& bl = h->B[l];
+  BatchLevel& bn = h->B[l + 1];
+  const int64_t nel = 4 * (int64_t)K * lv.n;
+  bool zero = x_is_zero;
+  for (int k = 0; k < h->opt.m_pre; ++k) {
+    if (zero) {
+      k_fill_m<T><<<gridk(nel), 256, 0, s>>>(x, nel);
+      h->launches++;
+    }
+    smooth_m<T>(h, l, x, b, false);
+    zero = false;
+  }
+  if (zero) {
+    k_fill_m<T><<<gridk(nel), 256, 0, s>>>(x, nel);
+    h->launches++;
+  }
+  T* r = MV<T>::r(bl);
+  rows_m<T>(h, mResid, lv, 0, lv.n, MV<T>::val(lv), x, b, r, nullptr, T(0));
+  k_restrict_m<T><<<gridk((int64_t)nx.n * K), 256, 0, s>>>(nx.n, lv.r_rowptr, lv.r_col,
+                                                          MV<T>::rval(lv), r, MV<T>::b(bn));
+  h->launches++;
+  for (int k = 0; k < std::max(1, (l + 1 == L) ? 1 : h->opt.nu); ++k)
+    cycle_m<T>(h, l + 1, MV<T>::x(bn), MV<T>::b(bn), k == 0);
+  k_prolong_m<T><<<gridk((int64_t)lv.n * K), 256, 0, s>>>(lv.n, lv.p_rowptr, lv.p_col,
+                                                          MV<T>::pval(lv), MV<T>::x(bn), x);
+  h->launches++;
+  for (int k = 0; k < h->opt.m_post; ++k) smooth_m<T>(h, l, x, b, true);
+}
+
+// z = M^{-1} r for all right-hand sides (FP64 [node][K][4] in and out)
+void precond_m(amg_handle* h, const double* r, double* z) {
+  Level& l0 = *h->L[0];
+  BatchLevel& b0 = h->B[0];
+  const int64_t nel = 4 * (int64_t)K * l0.n;
+  cudaStream_t s = h->stream;
+  if (h->opt.precision == AMG_FP32) {
+    k_d2f_m<<<gridk(nel), 256, 0, s>>>(r, b0.b32, nel);
+    h->launches++;
+    for (int c = 0; c < std::max(1, h->opt.cycles); ++c)
+      cycle_m<float>(h, 0, b0.x32.p, b0.b32.p, c == 0);
+    k_f2d_m<<<gridk(nel), 256, 0, s>>>(b0.x32, z, nel);
+    h->launches++;
+  } else {
+    for (int c = 0; c < std::max(1, h->opt.cycles); ++c) cycle_m<double>(h, 0, z, r, c == 0);
+  }
+}
+
+void apply_m64(amg_handle* h, const double* x, double* y) {
+  Level& lv = *h->L[0];
+  rows_m<double>(h, mApply, lv, 0, lv.n, lv.k_val(), x, nullptr, y, nullptr, 0.0);
+}
+
+void dots_m(amg_handle* h, int slot, const double* a0, const double* b0,
+            const double* a1 = nullptr, const double* b1 = nullptr) {
+  const int nd = a1 ? 2 : 1;
+  const int64_t nel = 4 * (int64_t)K * h->L[0]->n;
+  k_dots_m<<<kDotBlocks, kDotThreads, 0, h->stream>>>(nel, nd, a0, b0, a1, b1, h->bred);
+  k_final_m<<<1, 64, 0, h->stream>>>(h->bred, kDotBlocks, nd, h->bscal.p + slot * K);
+  h->launches += 2;
+}
+
+void alloc_batch(amg_handle* h) {
+  if (!h->B.empty()) return;
+  if (h->saddle) fail(AMG_ERR_UNSUPPORTED, "batched solves are provided for the SPD kinds");
+  h->B.resize(h->L.size());
+  const bool f32 = h->opt.precision == AMG_FP32;
+  auto z64 = [&](DBuf<double>& v, int64_t n) {
+    v.alloc(n);
+    AMG_CUDA(cudaMemsetAsync(v.p, 0, v.bytes(), h->stream));
+  };
+  auto z32 = [&](DBuf<float>& v, int64_t n) {
+    v.alloc(n);
+    AMG_CUDA(cudaMemsetAsync(v.p, 0, v.bytes(), h->stream));
+  };
+  for (size_t l = 0; l < h->L.size(); ++l) {
+    const int64_t n = 4 * (int64_t)K * std::max(h->L[l]->n, 1);
+    BatchLevel& b = h->B[l];
+    if (f32) { z32(b.x32, n); z32(b.b32, n); z32(b.r32, n); z32(b.t32, n); }
+    else { z64(b.x64, n); z64(b.b64, n); z64(b.r64, n); z64(b.t64, n); }
+  }
+  const int64_t n0 = 4 * (int64_t)K * h->L[0]->n;
+  z64(h->mb, n0); z64(h->mx, n0); z64(h->mr, n0); z64(h->mz, n0);
+  z64(h->mp, n0); z64(h->mq, n0); z64(h->mro, n0);
+  h->bred.alloc((size_t)kDotBlocks * 2 * K);
+  h->bscal.alloc((size_t)M_NS * K);
+  h->bit.alloc(1);
+  AMG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// initial block of one problem: x = 0, r = b, z = M r, rz, p = z, active set
+void emit_init(amg_handle* h, const double* bu, int nrhs, double tol) {
+  cudaStream_t s = h->stream;
+  const int n = h->L[0]->n;
+  const int64_t nel = 4 * (int64_t)K * n;
+  k_user_to_m<<<gridk(nel), 256, 0, s>>>(bu, h->mb, n, nrhs);
+  k_fill_m<double><<<gridk(nel), 256, 0, s>>>(h->mx, nel);
+  k_copy_m<double><<<gridk(nel), 256, 0, s>>>(h->mb, h->mr, nel);
+  h->launches += 3;
+  dots_m(h, M_BB, h->mb, h->mb);
+  k_init_m<<<1, 32, 0, s>>>(h->bscal, tol, nrhs, h->bit);
+  h->launches++;
+  precond_m(h, h->mr, h->mz);
+  dots_m(h, M_RZ, h->mr, h->mz);
+  k_copy_m<double><<<gridk(nel), 256, 0, s>>>(h->mz, h->mp, nel);
+  h->launches++;
+}
+
+// one iteration of flexible CG per right-hand side and the stopping test
+void emit_iteration(amg_handle* h, cudaGraphConditionalHandle cond) {
+  cudaStream_t s = h->stream;
+  const int64_t nel = 4 * (int64_t)K * h->L[0]->n;
+  apply_m64(h, h->mp, h->mq);
+  dots_m(h, M_PQ, h->mp, h->mq);
+  k_update_m<<<kDotBlocks, kDotThreads, 0, s>>>(nel, h->mx, h->mr, h->mp, h->mq, h->mro,
+                                                h->bscal, h->bred);
+  k_final_m<<<1, 64, 0, s>>>(h->bred, kDotBlocks, 1, h->bscal.p + M_RR * K);
+  k_check_m<<<1, 32, 0, s>>>(cond, h->bscal, h->bit, h->opt.max_iterations);
+  h->launches += 3;
+  precond_m(h, h->mr, h->mz);
+  dots_m(h, M_RZN, h->mr, h->mz, h->mz, h->mro);
+  k_beta_m<<<1, 32, 0, s>>>(h->bscal);
+  k_dir_m<<<gridk(nel), 256, 0, s>>>(nel, h->mp, h->mz, h->bscal);
+  h->launches += 2;
+}
+
+void emit_final(amg_handle* h, double* xu, int nrhs) {
+  const int n = h->L[0]->n;
+  k_m_to_user<<<gridk((int64_t)nrhs * 3 * n), 256, 0, h->stream>>>(h->mx, xu, n, nrhs);
+  h->launches++;
+}
+
+cudaGraph_t capture(cudaStream_t s, const std::function<void()>& f) {
+  cudaGraph_t g = nullptr;
+  AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  try {
+    f();
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(s, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    throw;
+  }
+  AMG_CUDA(cudaStreamEndCapture(s, &g));
+  return g;
+}
+
+}  // namespace
+
+// Builds (or reuses) the batch graph and runs it.
+int solve_batched(amg_handle* const* hs, int np, int nrhs, const double* const* B,
+                  double* const* X, double tol, amg_stats* stats, double* ms_out) {
+  if (np <= 0 || nrhs <= 0 || nrhs > K) fail(AMG_ERR_INVALID, "need 1..16 right-hand sides");
+  amg_handle* h0 = hs[0];
+  for (int p = 0; p < np; ++p) {
+    if (!hs[p]) fail(AMG_ERR_INVALID, "null handle");
+    alloc_batch(hs[p]);
+  }
+  // one graph: per problem, init -> while(iteration) -> final
+  cudaGraph_t g = nullptr;
+  AMG_CUDA(cudaGraphCreate(&g, 0));
+  std::vector<int64_t> l0(np);
+  std::vector<int64_t> per_iter(np);
+  try {
+    for (int p = 0; p < np; ++p) {
+      amg_handle* h = hs[p];
+      l0[p] = h->launches;
+      cudaGraph_t gi = capture(h->stream, [&]() { emit_init(h, B[p], nrhs, tol); });
+      cudaGraphNode_t ni, nc, nf;
+      AMG_CUDA(cudaGraphAddChildGraphNode(&ni, g, nullptr, 0, gi));
+      cudaGraphDestroy(gi);
+      cudaGraphConditionalHandle cond;
+      AMG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      AMG_CUDA(cudaGraphAddNode(&nc, g, &ni, nullptr, 1, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      const int64_t b0 = h->launches;
+      AMG_CUDA(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      try {
+        emit_iteration(h, cond);
+      } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(h->stream, &junk);
+        throw;
+      }
+      AMG_CUDA(cudaStreamEndCapture(h->stream, &body));
+      per_iter[p] = h->launches - b0;
+      cudaGraph_t gf = capture(h->stream, [&]() { emit_final(h, X[p], nrhs); });
+      AMG_CUDA(cudaGraphAddChildGraphNode(&nf, g, &nc, 1, gf));
+      cudaGraphDestroy(gf);
+    }
+  } catch (...) {
+    cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraphExec_t exec = nullptr;
+  AMG_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  cudaGraphDestroy(g);
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  AMG_CUDA(cudaEventRecord(e0, h0->stream));
+  AMG_CUDA(cudaGraphLaunch(exec, h0->stream));
+  AMG_CUDA(cudaEventRecord(e1, h0->stream));
+  AMG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  if (ms_out) *ms_out = ms;
+  // statistics: iterations and true residuals per problem (max over right-hand sides)
+  int rc = AMG_OK;
+  for (int p = 0; p < np; ++p) {
+    amg_handle* h = hs[p];
+    int it = 0;
+    AMG_CUDA(cudaMemcpy(&it, h->bit.p, sizeof(int), cudaMemcpyDeviceToHost));
+    // true residuals r = b - A x per right-hand side (slots reused after the solve)
+    const int64_t nel = 4 * (int64_t)K * h->L[0]->n;
+    apply_m64(h, h->mx, h->mq);
+    k_sub_m<<<gridk(nel), 256, 0, h->stream>>>(h->mb, h->mq, h->mr, nel);
+    AMG_LAUNCH_CHECK();
+    dots_m(h, M_RZN, h->mr, h->mr, h->mb, h->mb);
+    std::vector<double> sc((size_t)M_NS * K);
+    AMG_CUDA(cudaMemcpyAsync(sc.data(), h->bscal.p, sc.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<double> rr(K), bb(K);
+    for (int r = 0; r < K; ++r) {
+      rr[r] = sc[M_RZN * K + r];
+      bb[r] = sc[M_ZRO * K + r];
+    }
+    double worst = 0.0;
+    bool conv = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rel = bb[r] > 0 ? std::sqrt(rr[r] / bb[r]) : 0.0;
+      worst = std::max(worst, rel);
+      if (sc[M_ACT * K + r] != 0.0) conv = false;
+    }
+    if (!conv) rc = AMG_NOT_CONVERGED;
+    h->launches = l0[p] + per_iter[p] * it;
+    if (stats) {
+      amg_stats& st = stats[p];
+      std::memset(&st, 0, sizeof(st));
+      st.iterations = it;
+      st.converged = conv;
+      st.n_levels = (int)h->L.size();
+      st.true_rel_residual = worst;
+      st.rel_residual = worst;
+      st.solve_ms = ms;
+      st.setup_ms = h->setup_ms;
+      st.kernel_launches = per_iter[p] * it;
+      for (int l = 0; l < AMG_MAX_LEVELS && l < (int)h->L.size(); ++l) {
+        st.level_nodes[l] = h->L[l]->n;
+        st.level_nnzb[l] = h->L[l]->nnzb;
+        st.level_colours[l] = h->L[l]->ncolours;
+      }
+    }
+  }
+  return rc;
+}
+
+}  // namespace amgp2

@@ -99,24 +99,33 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
       // before the gathers that depend on them
       constexpr int U = G >= 32 ? 3 : (G >= 16 ? 2 : 4);
       for (int k0 = a + gl; k0 < e; k0 += U * G) {
+        // the matrix is streamed once per pass: evict-first loads keep the
+        // gathered vector resident in L2; values do not wait for the columns
         int j[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) j[u] = (k0 + u * G < e) ? ldg(col + k0 + u * G) : -1;
+        T v[U][9];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (j[u] < 0) continue;
+          const int k = k0 + u * G;
+          if (k < e) {
+            j[u] = __ldcs(col + k);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[u][q] = __ldcs(val + q * nnzb + k);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (k0 + u * G >= e) continue;
           T x0, x1, x2;
           VL<COH>::node(x, j[u], x0, x1, x2);
-          const T* v = val + k0 + u * G;
-          s0 = fma(ldg(v), x0, s0);
-          s0 = fma(ldg(v + nnzb), x1, s0);
-          s0 = fma(ldg(v + 2 * nnzb), x2, s0);
-          s1 = fma(ldg(v + 3 * nnzb), x0, s1);
-          s1 = fma(ldg(v + 4 * nnzb), x1, s1);
-          s1 = fma(ldg(v + 5 * nnzb), x2, s1);
-          s2 = fma(ldg(v + 6 * nnzb), x0, s2);
-          s2 = fma(ldg(v + 7 * nnzb), x1, s2);
-          s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+          s0 = fma(v[u][0], x0, s0);
+          s0 = fma(v[u][1], x1, s0);
+          s0 = fma(v[u][2], x2, s0);
+          s1 = fma(v[u][3], x0, s1);
+          s1 = fma(v[u][4], x1, s1);
+          s1 = fma(v[u][5], x2, s1);
+          s2 = fma(v[u][6], x0, s2);
+          s2 = fma(v[u][7], x1, s2);
+          s2 = fma(v[u][8], x2, s2);
         }
       }
     }
@@ -443,9 +452,9 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
     for (int u = 0; u < U; ++u) {
       const int k = a + gl + u * G;
       if (k < e) {
-        j[u] = ldg(col + k);
+        j[u] = __ldcs(col + k);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) v[u][q] = ldg(val + q * nnzb + k);
+        for (int q = 0; q < 9; ++q) v[u][q] = __ldcs(val + q * nnzb + k);
       }
     }
     if (gl == 0) {
@@ -684,7 +693,7 @@ struct Emit {
       return;
     }
     if (work <= 0) return;
-    if (P.type == PH_ROWS) launch_rows<T>(P, h->stream, h->opt.use_graphs != 0 && h->use_pdl);
+    if (P.type == PH_ROWS) launch_rows<T>(P, h->stream, h->use_pdl);
     else k_phase<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
     h->launches++;
   }
@@ -745,7 +754,8 @@ struct Emit {
 
 template <typename T>
 void e_apply(Emit<T>& e, Level& lv, const T* x, T* y, bool saddle) {
-  e.rows(kApply, lv, group_for(lv), 0, lv.n, LvVec<T>::val(lv), x, nullptr, y, nullptr, T(0));
+  const int G = (sizeof(T) == 8 && lv.group64) ? lv.group64 : group_for(lv);
+  e.rows(kApply, lv, G, 0, lv.n, LvVec<T>::val(lv), x, nullptr, y, nullptr, T(0));
   if (saddle && lv.np > 0) {
     const T* p = x + 4 * lv.n;
     e.bt_add(lv, p, T(1), y);
@@ -1125,6 +1135,20 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group = best;
+    if (f32 && l == 0) {   // the outer Krylov operator is FP64 on level 0
+      best = 0;
+      best_ms = 1e30f;
+      for (int G : {4, 8, 16, 32}) {
+        lv.group64 = G;
+        for (int r = 0; r < 7; ++r) {
+          if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+          level_apply<double>(h, 0, lv.x64.p, lv.r64.p);
+        }
+        const float ms = elapsed();
+        if (ms < best_ms) { best_ms = ms; best = G; }
+      }
+      lv.group64 = best;
+    }
     if (lv.ncolours == 0 || h->saddle || h->opt.smoother != AMG_SMOOTHER_GS) continue;
     best = 0;
     best_ms = 1e30f;

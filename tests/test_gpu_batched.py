@@ -1,0 +1,81 @@
+"""Batched multi-right-hand-side solves (amg_solve_batched) against single solves
+and a sparse direct solve: uneven problems, 1..16 right-hand sides, FP32 and
+FP64 cycles, all problems in one graph launch."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+from fem_inputs import problems as fp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def B():
+    from paper_1503_01287_gb300 import binding
+    return binding
+
+
+def _problems():
+    return [fp.elasticity_problem(4, seed=1, nu=0.3),
+            fp.elasticity_problem((5, 7, 4), seed=2, lengths=(1.0, 2.5, 3.0), nu=0.42),
+            fp.elasticity_problem(6, seed=3, nu=0.25, n_rhs=5, traction="gaussian")]
+
+
+def _rhs(prob, k, rng):
+    """k right-hand sides of the problem: its own load(s) then seeded Gaussian ones
+    (zero on Dirichlet nodes)."""
+    n3 = 3 * prob.n_nodes
+    d = np.repeat((prob.tags & fp.TAG_DIRICHLET) != 0, 3)
+    out = np.zeros((k, n3))
+    f = prob.f.reshape(-1, n3) if prob.f.ndim == 3 else prob.f.reshape(1, n3)
+    for r in range(k):
+        out[r] = f[r] if r < len(f) else rng.standard_normal(n3)
+        out[r][d] = 0.0
+    return out
+
+
+@pytest.mark.parametrize("precision,k", [(0, 5), (1, 5), (1, 16), (1, 1)])
+def test_batched_matches_single_and_direct(precision, k):
+    probs = _problems()
+    rng = np.random.default_rng(7)
+    handles, Bs, Xs, rhs = [], [], [], []
+    for p in probs:
+        h = B().setup_problem(p, B().default_options(precision=precision))
+        r = _rhs(p, k, rng)
+        if k >= 3:
+            r[2] = 0.0                       # a zero right-hand side converges at once
+        handles.append(h)
+        rhs.append(r)
+        Bs.append(torch.from_numpy(r.ravel()).cuda())
+        Xs.append(torch.zeros(k * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
+    rc, stats = B().solve_batched(handles, Bs, Xs, k, 1e-8)
+    assert rc == 0
+    for p, h, r, X, st in zip(probs, handles, rhs, Xs, stats):
+        A = p.a_scipy().tocsc()
+        x = X.cpu().numpy().reshape(k, -1)
+        for j in range(k):
+            nb = np.linalg.norm(r[j])
+            if nb == 0:
+                assert np.all(x[j] == 0)
+                continue
+            assert np.linalg.norm(r[j] - A @ x[j]) <= 1.5e-8 * nb
+            xd = spl.spsolve(A, r[j])
+            assert np.linalg.norm(x[j] - xd) <= 1e-5 * np.linalg.norm(xd)
+        assert st.true_rel_residual <= 1.5e-8 and st.converged
+        # the same right-hand side through amg_solve
+        b0 = torch.from_numpy(np.ascontiguousarray(r[0])).cuda()
+        x0 = torch.zeros_like(b0)
+        s1 = h.solve(b0, x0, 1e-8, device_ptrs=True)
+        # the batch loop runs until its slowest right-hand side has converged
+        assert st.iterations >= s1.iterations - 1
+        if precision == 0:
+            assert np.linalg.norm(x0.cpu().numpy() - x[0]) <= 1e-7 * np.linalg.norm(x[0])
