@@ -108,8 +108,33 @@ def _csr_from_keys(rows: np.ndarray, cols: np.ndarray, n_rows: int, n_cols: int)
     return rowptr, col, inv
 
 
+def _uniform(mesh: BoxMesh) -> bool:
+    """True when every brick is a translate of the first (an unjittered box mesh):
+    the 6 element matrices of the first brick then serve all bricks."""
+    h = np.array(mesh.lengths) / np.array([mesh.nx, mesh.ny, mesh.nz])
+    return bool(np.array_equal(mesh.coords, mesh.grid.astype(np.float64) * h))
+
+
+def _element_stream(mesh: BoxMesh, fn, chunk: int):
+    """Yields (start, element arrays) over chunks of tetrahedra; on uniform meshes
+    the first brick's 6 element arrays are tiled (tetrahedra are brick-major)."""
+    X = mesh.coords[mesh.tets]
+    T = len(X)
+    if _uniform(mesh):
+        ref = fn(X[:6])
+        for s in range(0, T, chunk):
+            cnt = min(chunk, T - s)
+            reps = -(-cnt // 6) + 1
+            tiled = np.concatenate([ref] * reps, axis=0)
+            off = s % 6
+            yield s, tiled[off:off + cnt]
+        return
+    for s in range(0, T, chunk):
+        yield s, fn(X[s:s + chunk])
+
+
 def assemble_velocity(mesh: BoxMesh, kind: str, mu: float = 1.0, lam: float = 1.0,
-                      chunk: int = 16384):
+                      chunk: int = 16386):
     """Global 3x3-block CSR of A over all P2 nodes, structural pattern = node pairs
     sharing a tetrahedron.  Returns rowptr (N+1,), col (nnzb,), val (nnzb, 3, 3)."""
     tn = mesh.tet_nodes()                                # (T, 10)
@@ -120,16 +145,15 @@ def assemble_velocity(mesh: BoxMesh, kind: str, mu: float = 1.0, lam: float = 1.
     inv = inv.reshape(len(tn), 100)
     nnzb = len(col)
     val = np.zeros((nnzb, 9))
-    X = mesh.coords[mesh.tets]
-    for s in range(0, len(tn), chunk):
-        Ke = element_blocks(X[s:s + chunk], kind, mu, lam).reshape(-1, 9)
-        idx = inv[s:s + chunk].ravel()
+    for s, Ke in _element_stream(mesh, lambda X: element_blocks(X, kind, mu, lam), chunk):
+        Ke = Ke.reshape(-1, 9)
+        idx = inv[s:s + len(Ke) // 100].ravel()
         for comp in range(9):
             val[:, comp] += np.bincount(idx, weights=Ke[:, comp], minlength=nnzb)
     return rowptr, col, val.reshape(nnzb, 3, 3)
 
 
-def assemble_divergence(mesh: BoxMesh, chunk: int = 16384):
+def assemble_divergence(mesh: BoxMesh, chunk: int = 16386):
     """B as 1x3-block CSR: rows = pressure nodes (vertices), cols = velocity nodes."""
     tn = mesh.tet_nodes()
     rows = np.repeat(mesh.tets, 10, axis=1).ravel()
@@ -138,16 +162,15 @@ def assemble_divergence(mesh: BoxMesh, chunk: int = 16384):
     inv = inv.reshape(len(tn), 40)
     nnz = len(col)
     val = np.zeros((nnz, 3))
-    X = mesh.coords[mesh.tets]
-    for s in range(0, len(tn), chunk):
-        Be = element_divergence(X[s:s + chunk]).reshape(-1, 3)
-        idx = inv[s:s + chunk].ravel()
+    for s, Be in _element_stream(mesh, element_divergence, chunk):
+        Be = Be.reshape(-1, 3)
+        idx = inv[s:s + len(Be) // 40].ravel()
         for comp in range(3):
             val[:, comp] += np.bincount(idx, weights=Be[:, comp], minlength=nnz)
     return rowptr, col, val
 
 
-def assemble_pressure_mass(mesh: BoxMesh, scale: float, chunk: int = 65536):
+def assemble_pressure_mass(mesh: BoxMesh, scale: float, chunk: int = 65538):
     """scale * int lambda_k lambda_l as scalar CSR over vertices (the P1 pattern)."""
     rows = np.repeat(mesh.tets, 4, axis=1).ravel()
     cols = np.tile(mesh.tets, (1, 4)).ravel()
@@ -155,10 +178,9 @@ def assemble_pressure_mass(mesh: BoxMesh, scale: float, chunk: int = 65536):
     rowptr, col, inv = _csr_from_keys(rows, cols, nv, nv)
     inv = inv.reshape(len(mesh.tets), 16)
     val = np.zeros(len(col))
-    X = mesh.coords[mesh.tets]
-    for s in range(0, len(mesh.tets), chunk):
-        Me = element_pressure_mass(X[s:s + chunk]).reshape(-1) * scale
-        val += np.bincount(inv[s:s + chunk].ravel(), weights=Me, minlength=len(col))
+    for s, Me in _element_stream(mesh, element_pressure_mass, chunk):
+        Me = Me.reshape(-1) * scale
+        val += np.bincount(inv[s:s + len(Me) // 16].ravel(), weights=Me, minlength=len(col))
     return rowptr, col, val
 
 

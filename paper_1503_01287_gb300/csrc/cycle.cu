@@ -97,7 +97,8 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
       const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
       // U blocks per lane per step: all column indices of the step are loaded
       // before the gathers that depend on them
-      constexpr int U = G >= 32 ? 3 : (G >= 16 ? 2 : 4);
+      // FP64 keeps fewer blocks in flight per lane (register budget)
+      constexpr int U = sizeof(T) == 8 ? (G >= 16 ? 1 : 2) : (G >= 32 ? 3 : (G >= 16 ? 2 : 4));
       for (int k0 = a + gl; k0 < e; k0 += U * G) {
         // the matrix is streamed once per pass: evict-first loads keep the
         // gathered vector resident in L2; values do not wait for the columns
