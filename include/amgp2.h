@@ -297,6 +297,29 @@ int amg_level_copy(const amg_handle* h, int32_t level, int32_t item, void* host_
  * pointers of 3*n_nodes + n_pres doubles.  Synchronises the stream. */
 int amg_apply_preconditioner(amg_handle* h, const double* r, double* z);
 
+/*
+ * amg_apply_preconditioner_noalloc -- the same z = M^{-1} r as
+ * amg_apply_preconditioner, for callers that must not allocate device memory
+ * during the call: work issued while a stream is captured into a CUDA graph in
+ * global mode (cudaMalloc is refused there), code whose framework allocator has
+ * already reserved the device memory, and latency-bound loops that cannot take
+ * the device-wide synchronisation an allocation may bring.  The paper has no
+ * counterpart; this is a property of the library interface.
+ *   r, z   device pointers of 3*n_nodes + n_pres doubles (the caller owns them).
+ * The input and output are staged in one static device array of the library
+ * (2 x 1,310,720 doubles = 20 MiB, held on every GPU that loads the library until
+ * the process exits), so the level-0 problem must satisfy
+ * 4*n_nodes + n_pres <= 1,310,720; larger problems get AMG_ERR_INVALID with a
+ * message giving both sizes.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls whose GPU work overlaps (several
+ * handles, streams or threads at once) race on it and must be serialised by the
+ * caller.  The array keeps the last call's contents; both staged vectors are
+ * rewritten completely by every call.  Synchronises the handle's stream.
+ */
+int amg_apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
+
 /* y = K_l x on level `level` with the library's FP64 (precision = AMG_FP64) or
  * FP32 (AMG_FP32, values rounded to float, accumulated in float) kernels; x
  * and y are device pointers of 3*n_nodes + n_pres doubles. */

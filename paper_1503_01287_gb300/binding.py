@@ -39,7 +39,7 @@ KINDS = {"laplace": AMG_VECTOR_LAPLACE, "elasticity": AMG_ELASTICITY,
 EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
             "amg_level_info_get", "amg_level_copy", "amg_apply_preconditioner",
             "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
-            "amg_time_level_op", "amg_solve_batched"]
+            "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc"]
 
 OPS = {"apply": 0, "residual": 1, "smooth": 2, "restrict": 3, "prolong": 4, "precond": 5}
 
@@ -134,6 +134,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_solve_batched.argtypes = [C.POINTER(vp), i32, i32, C.POINTER(vp), C.POINTER(vp), dbl,
                                       C.POINTER(AmgStats)]
     lib.amg_solve_batched.restype = C.c_int
+    lib.amg_apply_preconditioner_noalloc.argtypes = [vp, vp, vp]
+    lib.amg_apply_preconditioner_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -262,6 +264,11 @@ class Handle:
 
     def apply_preconditioner(self, r_dev, z_dev):
         _check(load_library().amg_apply_preconditioner(self.h, _ptr(r_dev), _ptr(z_dev)), self.h)
+
+    def apply_preconditioner_noalloc(self, r_dev, z_dev):
+        """z = M^{-1} r without any device allocation in the call (static staging)."""
+        _check(load_library().amg_apply_preconditioner_noalloc(self.h, _ptr(r_dev),
+                                                               _ptr(z_dev)), self.h)
 
     def level_apply(self, level: int, x_dev, y_dev, precision: int = AMG_FP64):
         _check(load_library().amg_level_apply(self.h, level, precision, _ptr(x_dev), _ptr(y_dev)),

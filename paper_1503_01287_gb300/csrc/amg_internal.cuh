@@ -224,6 +224,9 @@ void set_subcycle(amg_handle* h, int from);
 // krylov (krylov.cu)
 int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stats* st);
 
+// noalloc.cu: the preconditioner application with static staging vectors
+void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
+
 // batched.cu: all problems and right-hand sides in one graph launch
 int solve_batched(amg_handle* const* hs, int np, int nrhs, const double* const* B,
                   double* const* X, double tol, amg_stats* stats, double* ms_out);

@@ -398,6 +398,14 @@ int amg_apply_preconditioner(amg_handle* h, const double* r, double* z) {
   });
 }
 
+int amg_apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z) {
+  return guarded(h, [&]() -> int {
+    if (!h || !r || !z) fail(AMG_ERR_INVALID, "null argument");
+    apply_preconditioner_noalloc(h, r, z);
+    return AMG_OK;
+  });
+}
+
 int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const double* x, double* y) {
   return guarded(h, [&]() -> int {
     if (!h || !x || !y) fail(AMG_ERR_INVALID, "null argument");
