@@ -254,13 +254,14 @@ def run_gpu(args, rank, world):
                                                         warmup=2)
     peak, peak_kind = peaks()
     achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
+    # DRAM bytes of one level-0 sweep from the committed ncu summary of this kernel
+    # (32^3 only; cold-cache per launch, see the summary)
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "gs_sweep_fp32_elasticity_n32.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_sweep")
-        except Exception:
-            traffic = None
+    prof = os.path.join(ROOT, "profiles", "gs_colour_sweep_elasticity_n32.md")
+    if args.n == 32 and os.path.exists(prof):
+        for ln in open(prof):
+            if ln.startswith("dram_bytes_per_sweep:"):
+                traffic = int(ln.split(":")[1])
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -297,8 +298,8 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_block_rows<float,32,GS> (one level-0 sweep = "
-                               f"{sweep_launches} colour launches)",
+                     "kernel": "k_gs_pdl<float,G,U> multicolour Gauss-Seidel (unit: one "
+                               f"level-0 sweep = {sweep_launches} colour launches)",
                      "unit_bytes": gs_bytes, "ms_per_unit": sweep_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs"},
         "kernels": {"spmv_fp64_level0": {"ms": spmv_ms, "bytes": spmv_bytes,
@@ -338,6 +339,60 @@ def run_profile(args):
         h.free()
 
 
+def run_batched(args):
+    """64 uneven elasticity problems x 16 right-hand sides in one amg_solve_batched
+    launch (box meshes n ~ U{8..24}, side lengths ~ U[1,4], nu ~ U[0.2,0.45],
+    N(0,1) traction loads), FP32 V-cycle, flexible CG per right-hand side to 1e-8."""
+    import torch
+
+    from fem_inputs import configs, elasticity_problem
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1503_01287_gb300 import binding as B
+    specs = configs.batched_specs(args.batch, seed=4)
+    t0 = time.perf_counter()
+    probs = [elasticity_problem(sp["n"], seed=sp["seed"], nu=sp["nu"], lengths=sp["lengths"],
+                                n_rhs=args.rhs, traction="gaussian") for sp in specs]
+    gen_s = time.perf_counter() - t0
+    handles, Bs, Xs = [], [], []
+    t0 = time.perf_counter()
+    for p in probs:
+        h = B.setup_problem(p, B.default_options(precision=B.AMG_FP32))
+        handles.append(h)
+        Bs.append(torch.from_numpy(np.ascontiguousarray(p.f.reshape(args.rhs, -1))).cuda())
+        Xs.append(torch.zeros(args.rhs * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rc, stats = B.solve_batched(handles, Bs, Xs, args.rhs, TOL)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(stats[0].solve_ms)
+    ms = float(np.mean(times))
+    dof_rhs = sum(p.n_dof for p in probs) * args.rhs
+    worst = max(s.true_rel_residual for s in stats)
+    its = [s.iterations for s in stats]
+    line = {
+        "metric": "DOF x RHS/s solved to 1e-8 rel. residual, batched elasticity "
+                  f"({args.batch} uneven problems x {args.rhs} RHS, FP32 V-cycle, FCG)",
+        "value": dof_rhs / (ms * 1e-3), "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 cycle + f64 outer", "data": "synthetic",
+        "config": {"workload": f"batched_elast: {args.batch} problems, n in "
+                               f"{min(sp['n'] for sp in specs)}..{max(sp['n'] for sp in specs)}",
+                   "dof_total": sum(p.n_dof for p in probs), "rhs": args.rhs, "tol": TOL},
+        "iterations": {"min": min(its), "max": max(its)}, "true_rel_residual_max": worst,
+        "converged": rc == 0, "setup_s": setup_s, "generate_s": gen_s,
+        "graph_launches_per_step": 1,
+        "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+    }
+    print(json.dumps(line), flush=True)
+    for h in handles:
+        h.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +402,9 @@ def main():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--ref-n", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="elasticity", choices=["elasticity", "batched"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--profile", action="store_true",
                     help="setup, then exactly one FP32-cycle solve and one FP64 solve (for ncu)")
     args = ap.parse_args()
@@ -356,6 +414,8 @@ def main():
         return run_reference(args, rank, world)
     if args.profile:
         return run_profile(args)
+    if args.workload == "batched":
+        return run_batched(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
