@@ -64,9 +64,12 @@ def element_blocks(X: np.ndarray, kind: str, mu: float = 1.0, lam: float = 1.0):
     g, vol = barycentric_gradients(X)
     c = gradient_coefficients(g)
     M = lambda_mass(vol)
-    # G[t,i,j,al,be] = sum_pq c[t,i,p,al] M[t,p,q] c[t,j,q,be]
-    cM = np.einsum("tipa,tpq->tiqa", c, M)
-    G = np.einsum("tiqa,tjqb->tijab", cM, c)
+    # G[t,i,j,al,be] = sum_pq c[t,i,p,al] M[t,p,q] c[t,j,q,be], as batched products of
+    # the (30 x 4) coefficient matrix with M
+    T = len(X)
+    C30 = np.ascontiguousarray(np.transpose(c, (0, 1, 3, 2))).reshape(T, 30, 4)
+    G30 = C30 @ M @ np.transpose(C30, (0, 2, 1))
+    G = np.transpose(G30.reshape(T, 10, 3, 10, 3), (0, 1, 3, 2, 4))
     S = np.trace(G, axis1=3, axis2=4)
     I3 = np.eye(3)
     if kind == "laplace":

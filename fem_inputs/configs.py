@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .problems import (elasticity_problem, mixed_elasticity_problem, stokes_lid_problem,
+from .problems import (elasticity_problem, mixed_elasticity_family, stokes_lid_problem,
                        vector_laplace_problem)
 
 CONFIGS = {
@@ -55,8 +55,7 @@ def make_config(name: str, n: int | None = None, **over):
     if name.startswith("stokes"):
         return stokes_lid_problem(cfg["n"])
     if name.startswith("mixed"):
-        return [mixed_elasticity_problem(cfg["n"], nu=nu, seed=cfg["seed"])
-                for nu in cfg["nus"]]
+        return mixed_elasticity_family(cfg["n"], cfg["nus"], seed=cfg["seed"])
     if name.startswith("batched"):
         return [elasticity_problem(s["n"], seed=s["seed"], nu=s["nu"], lengths=s["lengths"],
                                    n_rhs=cfg["n_rhs"], traction="gaussian")

@@ -357,6 +357,30 @@ def stokes_lid_problem(n: int, mu: float = 1.0) -> Problem:
     return eliminate_dirichlet(prob)
 
 
+def mixed_elasticity_family(n: int, nus, seed: int = 0, E: float = 1.0, jitter: float = 0.2):
+    """mixed_elasticity_problem for several nu on one mesh: a(u,v) scales with mu and
+    c(p,q) with 1/lam, so the mesh, A (for mu = 1), B, the mass and the loads are
+    assembled once and scaled."""
+    rng = np.random.default_rng(seed)
+    mesh = box_mesh(n, jitter=jitter, rng=rng if jitter else None)
+    rp, c, v1 = assemble_velocity(mesh, "mixed", mu=1.0)
+    brp, bc, bv = assemble_divergence(mesh)
+    crp, cc, m1 = assemble_pressure_mass(mesh, 1.0)
+    top = boundary_faces(mesh, 2, 1)
+    t = rng.uniform(-1.0, 1.0, size=(len(top), 3))
+    f = face_load(mesh, top, face_edges(mesh, top), np.repeat(t[:, None, :], 3, axis=1))
+    tags = node_tags(mesh, np.unique(boundary_faces(mesh, 2, 0)))
+    out = []
+    for nu in nus:
+        lam, mu = lame(E, nu)
+        prob = Problem(f"mixed_elasticity_n{n}_nu{nu}_s{seed}", "mixed", mesh, rp, c, v1 * mu,
+                       tags.copy(), f.copy(), np.zeros((mesh.n_nodes, 3)), brp, bc, bv.copy(),
+                       crp, cc, m1 / lam, np.zeros(mesh.n_vertices),
+                       params={"n": n, "nu": nu, "seed": seed, "lam": lam, "mu": mu})
+        out.append(eliminate_dirichlet(prob))
+    return out
+
+
 def mixed_elasticity_problem(n: int, nu: float = 0.49, seed: int = 0, E: float = 1.0,
                              jitter: float = 0.2) -> Problem:
     """Mixed displacement-pressure elasticity, c = (1/lam) int p q: clamped z=0,

@@ -1,0 +1,69 @@
+"""The saddle-point workloads at full size, in the launch configuration of the
+library defaults: checked by properties that hold at any size (recomputed FP64
+residual of the full system, zero Dirichlet components, pressure normalisation)
+and by the bit-exact level-0 C/F splits against the oracle's greedy sets."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from fem_inputs import problems as fp
+from oracle import amg
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _full_K(p):
+    A = p.a_scipy().tocsr()
+    n3 = 3 * p.n_nodes
+    Bm = sp.bsr_matrix((p.b_val.reshape(-1, 1, 3), p.b_col, p.b_rowptr),
+                       shape=(p.n_pres, n3)).tocsr()
+    Cm = sp.csr_matrix((p.c_val, p.c_col, p.c_rowptr), shape=(p.n_pres, p.n_pres))
+    return sp.bmat([[A, Bm.T], [Bm, -Cm]]).tocsr()
+
+
+def _check(prob, precision=1):
+    from paper_1503_01287_gb300 import binding as B
+    h = B.setup_problem(prob, B.default_options(precision=precision))
+    # level-0 C/F splits equal the oracle's greedy independent sets
+    pat = amg.block_pattern(prob.a_rowptr, prob.a_col, prob.n_nodes)
+    g = amg.coarsening_graph(pat, np.asarray(prob.tags) & amg.TAG_TYPE_MASK, True)
+    st = amg.greedy_mis(g)
+    assert np.array_equal(h.level_array(0, "cf_state"), np.where(st == amg.STATE_C, 1, 2))
+    gp = amg.coarsening_graph(amg.block_pattern(prob.c_rowptr, prob.c_col, prob.n_pres),
+                              np.zeros(prob.n_pres, np.int32), True)
+    stp = amg.greedy_mis(gp)
+    assert np.array_equal(h.level_array(0, "pcf_state"), np.where(stp == amg.STATE_C, 1, 2))
+    b = prob.rhs()
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    st = h.solve(bt, x, 1e-8, device_ptrs=True)
+    assert st.converged, st.as_dict()
+    xv = x.cpu().numpy()
+    K = _full_K(prob)
+    assert np.linalg.norm(b - K @ xv) <= 1.5e-8 * np.linalg.norm(b)
+    d = (prob.tags & fp.TAG_DIRICHLET) != 0
+    assert np.all(xv[:3 * prob.n_nodes].reshape(-1, 3)[d] == 0.0)
+    return st, xv
+
+
+def test_stokes_lid_24_full_size():
+    """Lid-driven Taylor-Hood Stokes, 24^3 cubes (368,572 DOF), FP32 cycle in FGMRES."""
+    prob = fp.stokes_lid_problem(24)
+    st, x = _check(prob)
+    p = x[3 * prob.n_nodes:]
+    assert abs(prob.p_weights @ p) <= 1e-10 * np.abs(p).max() * prob.p_weights.sum()
+
+
+def test_mixed_elasticity_40_full_size():
+    """Mixed elasticity, nu = 0.4999, jittered 40^3 cubes (1,663,244 DOF), FP32 cycle."""
+    prob = fp.mixed_elasticity_family(40, [0.4999], seed=5)[0]
+    _check(prob)
