@@ -120,7 +120,7 @@ typedef struct amg_options {
   int32_t krylov;           /* amg_krylov (default AUTO)                        */
   int32_t max_levels;       /* levels 0..max_levels-1 (default 5)               */
   int32_t coarse_dofs;      /* stop coarsening at <= this many unknowns (300)   */
-  int32_t gmres_restart;    /* FGMRES(m) restart length (default 50)            */
+  int32_t gmres_restart;    /* FGMRES(m) restart length (default 50, at most 318) */
   int32_t separate;         /* 1: separate K_ll / K_qq graphs (Sec. 3.2.1);
                                0: graph of the whole matrix (Table 2, row 3)    */
   int32_t max_iterations;   /* Krylov iteration limit (default 1000)            */

@@ -88,6 +88,9 @@ struct Level {
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
   int group_gs = 0;     // the same for the colour-subset Gauss-Seidel kernel
   int group64 = 0;      // the FP64 operator kernel when the cycle runs in FP32
+  // learned weights of this level on the device: [0] relaxation multiplier,
+  // [1] coarse-correction scale, [2] pressure-step multiplier (all 1: plain)
+  double* wt = nullptr;
 
   // transfer to level+1 (absent on the coarsest level)
   DBuf<int> state, cid;
@@ -182,6 +185,9 @@ struct amg_handle {
   std::vector<amgp2::BatchLevel> B;
   amgp2::DBuf<double> mb, mx, mr, mz, mp, mq, mro, bred, bscal;
   amgp2::DBuf<int> bit;
+  amgp2::DBuf<double> wts;          // 4 learned weights per level (see Level::wt)
+  double plain_rho = 0.0;           // convergence factor of the plain method (fallback)
+  bool learned = false;
   ~amg_handle();
 };
 

@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict
                                                 const int* __restrict__ col,
                                                 const T* __restrict__ val, int64_t nnzb,
                                                 const T* x, const T* __restrict__ b, T* y,
-                                                const T* __restrict__ dinv, T omega) {
+                                                const T* __restrict__ dinv, T omega,
+                                                const double* __restrict__ wt) {
+  if (wt) omega = (T)((double)omega * wt[0]);   // learned relaxation multiplier
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / K;
   const int r = threadIdx.x % K;
   if (g >= nrows) return;
@@ -85,8 +87,7 @@ __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict
   const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
   T x0, x1, x2;
   ld3(x, o, x0, x1, x2);
-  if (MODE == mGS) st3(y, o, x0 + c0, x1 + c1, x2 + c2);
-  else st3(y, o, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
+  st3(y, o, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
 }
 
 // bc_(I,r) = sum_t w_t v_(i_t, r)
@@ -112,7 +113,9 @@ __global__ void k_restrict_m(int nc, const int* __restrict__ rrow, const int* __
 // x_(i,r) += sum_q P_iq xc_(q,r)
 template <typename T>
 __global__ void k_prolong_m(int n, const int* __restrict__ prow, const int* __restrict__ pcol,
-                            const T* __restrict__ pval, const T* __restrict__ xc, T* x) {
+                            const T* __restrict__ pval, const T* __restrict__ xc, T* x,
+                            const double* __restrict__ wt) {
+  const T wc = wt ? (T)wt[1] : T(1);   // coarse-correction scale
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / K, r = t % K;
   if (i >= n) return;
@@ -127,7 +130,7 @@ __global__ void k_prolong_m(int n, const int* __restrict__ prow, const int* __re
   }
   T x0, x1, x2;
   ld3(x, i * K + r, x0, x1, x2);
-  st3(x, i * K + r, x0 + s0, x1 + s1, x2 + s2);
+  st3(x, i * K + r, x0 + wc * s0, x1 + wc * s1, x2 + wc * s2);
 }
 
 // coarsest solve x = X b per right-hand side (X indexed 3 per node)
@@ -365,16 +368,16 @@ void rows_m(amg_handle* h, int mode, Level& lv, int first, int nrows, const T* v
   cudaStream_t s = h->stream;
   switch (mode) {
     case mApply:
-      k_rows_m<T, mApply><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      k_rows_m<T, mApply><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, nullptr);
       break;
     case mResid:
-      k_rows_m<T, mResid><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      k_rows_m<T, mResid><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, nullptr);
       break;
     case mGS:
-      k_rows_m<T, mGS><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      k_rows_m<T, mGS><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, lv.wt);
       break;
     default:
-      k_rows_m<T, mJacobi><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega);
+      k_rows_m<T, mJacobi><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, lv.wt);
       break;
   }
   h->launches++;
@@ -394,7 +397,7 @@ void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
-    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(0));
+    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1));
   }
 }
 
@@ -435,7 +438,8 @@ void cycle_m(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
   for (int k = 0; k < std::max(1, (l + 1 == L) ? 1 : h->opt.nu); ++k)
     cycle_m<T>(h, l + 1, MV<T>::x(bn), MV<T>::b(bn), k == 0);
   k_prolong_m<T><<<gridk((int64_t)lv.n * K), 256, 0, s>>>(lv.n, lv.p_rowptr, lv.p_col,
-                                                          MV<T>::pval(lv), MV<T>::x(bn), x);
+                                                          MV<T>::pval(lv), MV<T>::x(bn), x,
+                                                          lv.wt);
   h->launches++;
   for (int k = 0; k < h->opt.m_post; ++k) smooth_m<T>(h, l, x, b, true);
 }

@@ -76,8 +76,12 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
                                           const int* __restrict__ col,
                                           const T* __restrict__ val, int64_t nnzb, const T* x,
                                           const T* b, T* y, const T* __restrict__ dinv,
-                                          T omega, int warp, int nwarps) {
+                                          T omega, const double* __restrict__ wt, int warp,
+                                          int nwarps) {
   constexpr int RPW = 32 / G;
+  // relaxation: omega (Jacobi damping, 1 for Gauss-Seidel) times the level's
+  // learned multiplier (1 for the plain method)
+  if (MODE == kGS || MODE == kJacobi) omega = wt ? (T)((double)omega * wt[0]) : omega;
   const int lane = threadIdx.x & 31;
   const int sub = lane / G, gl = lane & (G - 1);
   for (int base = warp * RPW; base < nrows; base += nwarps * RPW) {
@@ -154,8 +158,7 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
     const T c1 = d0 * r0 + d1 * r1 + d2 * r2;
     ld3(d, 2, d0, d1, d2);
     const T c2 = d0 * r0 + d1 * r1 + d2 * r2;
-    if (MODE == kGS) st3(y, i, xi0 + c0, xi1 + c1, xi2 + c2);
-    else st3(y, i, xi0 + omega * c0, xi1 + omega * c1, xi2 + omega * c2);
+    st3(y, i, xi0 + omega * c0, xi1 + omega * c1, xi2 + omega * c2);
   }
 }
 
@@ -185,7 +188,9 @@ template <typename T, bool COH>
 __device__ __forceinline__ void prolong_body(int n, const int* __restrict__ prow,
                                              const int* __restrict__ pcol,
                                              const T* __restrict__ pval, const T* xc, T* x,
-                                             int tid, int nthr) {
+                                             const double* __restrict__ wt, int tid, int nthr) {
+  // coarse-grid correction x += w_c P x_c (w_c = 1 for the plain method)
+  const T wc = wt ? (T)wt[1] : T(1);
   for (int i = tid; i < n; i += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int q = prow[i]; q < prow[i + 1]; ++q) {
@@ -199,7 +204,7 @@ __device__ __forceinline__ void prolong_body(int n, const int* __restrict__ prow
     }
     T x0, x1, x2;
     VL<COH>::node(x, i, x0, x1, x2);
-    st3(x, i, x0 + s0, x1 + s1, x2 + s2);
+    st3(x, i, x0 + wc * s0, x1 + wc * s1, x2 + wc * s2);
   }
 }
 
@@ -220,11 +225,12 @@ template <typename T, bool COH>
 __device__ __forceinline__ void prolong1_body(int n, const int* __restrict__ prow,
                                               const int* __restrict__ pcol,
                                               const T* __restrict__ pval, const T* xc, T* x,
-                                              int tid, int nthr) {
+                                              const double* __restrict__ wt, int tid, int nthr) {
+  const T wc = wt ? (T)wt[1] : T(1);
   for (int i = tid; i < n; i += nthr) {
     T s = T(0);
     for (int q = prow[i]; q < prow[i + 1]; ++q) s = fma(pval[q], VL<COH>::one(xc + pcol[q]), s);
-    x[i] = VL<COH>::one(x + i) + s;
+    x[i] = VL<COH>::one(x + i) + wc * s;
   }
 }
 
@@ -288,7 +294,8 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
                                            const int* __restrict__ ccol,
                                            const T* __restrict__ cval, const T* u, const T* p,
                                            const T* g, T* yp, const T* __restrict__ sd, T omega,
-                                           int tid, int nthr) {
+                                           const double* __restrict__ wt, int tid, int nthr) {
+  if (MODE == 2 && wt) omega = (T)((double)omega * wt[2]);
   for (int k = tid; k < np; k += nthr) {
     T s = T(0);
     for (int q = brow[k]; q < brow[k + 1]; ++q) {
@@ -341,6 +348,7 @@ struct Phase {
   const double* X;
   int m, n3;
   double omega;
+  const double* wt;       // the level's learned weights (null: plain method)
 };
 
 template <typename T, bool COH>
@@ -352,8 +360,8 @@ __device__ void dispatch_rows(const Phase& P, int warp, int nwarps) {
   const T* d = (const T*)P.dinv;
   const T om = (T)P.omega;
 #define AMG_ROWS_MODE(GG, MM)                                                                \
-  rows_body<T, GG, MM, COH>(P.n, P.rows, P.rowptr, P.col, val, P.nnz, x, b, y, d, om, warp, \
-                            nwarps)
+  rows_body<T, GG, MM, COH>(P.n, P.rows, P.rowptr, P.col, val, P.nnz, x, b, y, d, om, P.wt, \
+                            warp, nwarps)
 #define AMG_ROWS_G(GG)                              \
   switch (P.mode) {                                 \
     case kApply: AMG_ROWS_MODE(GG, kApply); break;  \
@@ -383,16 +391,16 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
                             nthr);
       break;
     case PH_PROLONG:
-      prolong_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
-                           nthr);
+      prolong_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, P.wt,
+                           tid, nthr);
       break;
     case PH_RESTRICT1:
       restrict1_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
                              nthr);
       break;
     case PH_PROLONG1:
-      prolong1_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, tid,
-                            nthr);
+      prolong1_body<T, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x, (T*)P.y, P.wt,
+                            tid, nthr);
       break;
     case PH_COARSE:
       coarse_body<T, COH>(P.m, P.n3, P.X, (const T*)P.b, (T*)P.y, warp, nwarps);
@@ -408,7 +416,7 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
 #define AMG_PROWS(MM)                                                                        \
   prows_body<T, MM, COH>(P.n, P.rowptr, P.col, (const T*)P.val, P.nnz, P.crow, P.ccol,      \
                          (const T*)P.cval, u, p, (const T*)P.b, (T*)P.y, (const T*)P.sd, om, \
-                         tid, nthr)
+                         P.wt, tid, nthr)
       if (P.mode == 0) AMG_PROWS(0);
       else if (P.mode == 1) AMG_PROWS(1);
       else AMG_PROWS(2);
@@ -433,8 +441,10 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
                                                 const int* __restrict__ col,
                                                 const T* __restrict__ val, int64_t nnzb, T* x,
                                                 const T* __restrict__ b,
-                                                const T* __restrict__ dinv) {
+                                                const T* __restrict__ dinv,
+                                                const double* __restrict__ wt) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int gl = threadIdx.x & (G - 1);
   const bool active = g < nrows;
@@ -505,8 +515,8 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
   }
   if (!active || gl != 0) return;
   const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
-  st3(x, i, xi0 + d[0] * r0 + d[1] * r1 + d[2] * r2, xi1 + d[3] * r0 + d[4] * r1 + d[5] * r2,
-      xi2 + d[6] * r0 + d[7] * r1 + d[8] * r2);
+  st3(x, i, xi0 + om * (d[0] * r0 + d[1] * r1 + d[2] * r2),
+      xi1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2), xi2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
 }
 
 template <typename T, int G>
@@ -523,7 +533,7 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
   cfg.numAttrs = 1;
   AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U>, P.n, P.rows, P.rowptr, P.col,
                               (const T*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
-                              (const T*)P.dinv));
+                              (const T*)P.dinv, P.wt));
 }
 
 // one operation as its own kernel
@@ -538,7 +548,7 @@ __global__ void __launch_bounds__(256) k_rows(const Phase P) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   rows_body<T, G, MODE, false>(P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz,
                                (const T*)P.x, (const T*)P.b, (T*)P.y, (const T*)P.dinv,
-                               (T)P.omega, tid >> 5, (gridDim.x * blockDim.x) >> 5);
+                               (T)P.omega, P.wt, tid >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 
 template <typename T, int G>
@@ -708,6 +718,7 @@ struct Emit {
   void rows(int mode, const Level& lv, int G, int first, int nrows, const T* val, const T* x,
             const T* b, T* y, const T* dinv, T omega) {
     Phase P = blank(PH_ROWS);
+    P.wt = (mode == kGS || mode == kJacobi) ? lv.wt : nullptr;
     const int* order = lv.k_rows();
     P.mode = mode; P.G = G; P.n = nrows; P.rows = order ? order + first : nullptr;
     P.rowptr = lv.k_rowptr() + first; P.col = lv.k_col();
@@ -725,9 +736,9 @@ struct Emit {
     put(P, n);
   }
   void transfer(int type, int n, const int* row, const int* col, const T* val, const T* src,
-                T* dst) {
+                T* dst, const double* wt = nullptr) {
     Phase P = blank(type);
-    P.n = n; P.rowptr = row; P.col = col; P.val = val; P.x = src; P.y = dst;
+    P.n = n; P.rowptr = row; P.col = col; P.val = val; P.x = src; P.y = dst; P.wt = wt;
     put(P, n);
   }
   void coarse(const T* b, T* x) {
@@ -747,6 +758,7 @@ struct Emit {
     P.val = LvVec<T>::bval(lv); P.nnz = lv.b_nnz; P.crow = lv.c_rowptr; P.ccol = lv.c_col;
     P.cval = LvVec<T>::cval(lv); P.x = u; P.p = p; P.b = g; P.y = yp;
     P.sd = LvVec<T>::schur(lv); P.omega = (double)omega;
+    P.wt = mode == 2 ? lv.wt : nullptr;
     put(P, lv.np);
   }
 };
@@ -809,7 +821,7 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e2 = lv.colour_ptr[c + 1];
-    e.rows(kGS, lv, Ggs, a, e2 - a, val, x, b, x, dinv, T(0));
+    e.rows(kGS, lv, Ggs, a, e2 - a, val, x, b, x, dinv, T(1));
   }
 }
 
@@ -827,10 +839,10 @@ template <typename T>
 void e_prolong(Emit<T>& e, amg_handle* h, int l, const T* xc, T* x) {
   Level& lv = *h->L[l];
   Level& nx = *h->L[l + 1];
-  e.transfer(PH_PROLONG, lv.n, lv.p_rowptr, lv.p_col, LvVec<T>::pval(lv), xc, x);
+  e.transfer(PH_PROLONG, lv.n, lv.p_rowptr, lv.p_col, LvVec<T>::pval(lv), xc, x, lv.wt);
   if (h->saddle && lv.np > 0)
     e.transfer(PH_PROLONG1, lv.np, lv.h_rowptr, lv.h_col, LvVec<T>::hval(lv), xc + 4 * nx.n,
-               x + 4 * lv.n);
+               x + 4 * lv.n, lv.wt);
 }
 
 template <typename T>

@@ -16,7 +16,7 @@ namespace amgp2 {
 namespace {
 
 enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZN, S_ZRO, S_BB, S_BETA, S_T0, S_T1, S_TOL2, S_NSLOTS };
-constexpr int kMaxDots = 64;   // multi-dot width (FGMRES restart + 2)
+constexpr int kMaxDots = 320;  // multi-dot width (FGMRES restart + 2)
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

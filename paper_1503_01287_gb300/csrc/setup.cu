@@ -1235,6 +1235,10 @@ void build_hierarchy(amg_handle* h, const amg_matrix* m, const int32_t* tags) {
     h->L.push_back(std::move(nx));
   }
   for (size_t l = 0; l < h->L.size(); ++l) finish_level(h, *h->L[l], l + 1 == h->L.size());
+  // learned weights start at the plain method's (all 1)
+  h->wts.alloc(4 * h->L.size());
+  launch_fill(h->wts, 1.0, 4 * (int64_t)h->L.size(), s, h);
+  for (size_t l = 0; l < h->L.size(); ++l) h->L[l]->wt = h->wts.p + 4 * l;
   factor_coarsest(h);
   autotune_levels(h);
   AMG_CUDA(cudaStreamSynchronize(s));
