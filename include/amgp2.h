@@ -354,6 +354,101 @@ enum amg_level_op {
 int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precision, int32_t reps,
                       int32_t warmup, double* ms_per_rep, int32_t* launches_per_rep);
 
+
+/* ------------------------------------------- learned weights (small network)
+ *
+ * Three multipliers change the cycle, the same on every level; all 1 is the
+ * plain method of Sec. 3.3:
+ *   ws  relaxation: the block Jacobi damping omega, the Gauss-Seidel step and
+ *       the sGS velocity step are multiplied by ws;
+ *   wc  coarse-grid correction: x_l += wc * P x_{l+1} (Algorithm 1, step 13);
+ *   wp  sGS pressure step: omega_p is multiplied by wp (saddle kinds).
+ * A network of two hidden layers of 64 (ReLU) maps 13 statistics of the
+ * hierarchy's block diagonals and interpolation sets (amg_features) and a
+ * candidate (ws, wc, log2 wp) to the predicted log10 of the ratio of the
+ * candidate's convergence factor to the plain method's.  amg_learn_weights
+ * evaluates it on a fixed grid of candidates, keeps the best, and falls back to
+ * the plain weights when a measured probe solve with the chosen weights does
+ * not reduce the residual faster per iteration than the plain weights do.
+ */
+#define AMG_N_FEATURES 13
+#define AMG_MLP_INPUTS 16      /* features, ws, wc, log2 wp                   */
+#define AMG_MLP_HIDDEN 64
+#define AMG_MLP_NPARAM 5313    /* W1[64][16] b1[64] W2[64][64] b2[64] W3[64] b3 */
+#define AMG_WS_MIN 0.6
+#define AMG_WS_MAX 1.6
+#define AMG_GRID_NWS 11
+#define AMG_WC_MIN 0.8
+#define AMG_WC_MAX 1.9
+#define AMG_GRID_NWC 12
+#define AMG_WP_LOG2_MIN (-1.0)
+#define AMG_WP_LOG2_MAX 2.0
+#define AMG_GRID_NWP 7
+
+typedef struct amg_learned {
+  double weights[3];        /* ws, wc, wp in use after the call                 */
+  double predicted;         /* network output at the chosen candidate           */
+  double rho_plain;         /* probe convergence factor, plain weights          */
+  double rho_learned;       /* probe convergence factor, chosen weights         */
+  int32_t fell_back;        /* 1: the plain weights were kept                   */
+  int32_t n_candidates;
+  int32_t probe_iterations_plain;
+  int32_t probe_iterations_learned;
+} amg_learned;
+
+/*
+ * amg_features -- the network's 13 inputs for this hierarchy (host doubles):
+ *   [0]      log10(3 n_nodes + n_pres) / 7
+ *   [1..5]   level 0, over its non-Dirichlet nodes i (D_i the diagonal block,
+ *            Frobenius norms): mean log10(|D_i| |D_i^-1|); standard deviation
+ *            of log10 |D_i|; mean of sum_{j!=i} |A_ij| / |D_i|; and over its
+ *            F nodes: mean share sum_{j in S_i} |A_ij| / sum_{j!=i} |A_ij|
+ *            and mean |S_i| / 8, S_i the C nodes in the pattern of row i of P
+ *            (the C-neighbours of i in the coarsening graph)
+ *   [6..10]  the same for level 1 (0 when absent; the last two are 0 on the
+ *            coarsest level)
+ *   [11]     saddle kinds: mean over pressure rows of C_kk / S_D,kk with S_D the
+ *            sGS scaling diag(C + B (D/omega)^-1 B^T); 0 otherwise
+ *   [12]     1 for saddle kinds, 0 for SPD kinds
+ */
+int amg_features(amg_handle* h, double* features);
+
+/* Sets (ws, wc, wp) = w[0..2] on every level (host doubles, finite, > 0). */
+int amg_set_weights(amg_handle* h, const double* w);
+
+/* Copies the per-level weights, 4 doubles per level (ws, wc, wp, 1), to host. */
+int amg_get_weights(const amg_handle* h, double* w, int32_t capacity);
+
+/*
+ * amg_learn_weights -- chooses (ws, wc, wp) with the trained network theta
+ * (host floats, AMG_MLP_NPARAM, layout above): argmin of the network over the
+ * grid ws in [AMG_WS_MIN, AMG_WS_MAX] (AMG_GRID_NWS points) x wc (AMG_GRID_NWC)
+ * x log2 wp (AMG_GRID_NWP, saddle kinds; wp = 1 otherwise), then two probe
+ * solves of K x = K y (y pseudo-random, zero on Dirichlet nodes) to a relative
+ * residual of 1e-4 with the plain and with the chosen weights; the chosen
+ * weights stay only if their factor rel_residual^(1/iterations) is smaller.
+ * out receives the decision.  Later amg_solve calls use the weights in place.
+ */
+int amg_learn_weights(amg_handle* h, const float* theta, amg_learned* out);
+
+/*
+ * The network's kernels, on device memory (FP32 master weights, BF16 tensor-core
+ * products with FP32 accumulation), ordered on `stream` (cudaStream_t, NULL =
+ * legacy default stream); none synchronises.
+ *   amg_mlp_forward   y[i] = net(theta, x[16 i .. 16 i + 15]), i < n
+ *   amg_mlp_gradient  grad = d/dtheta of loss, loss = sum_i (y_i - t_i)^2 / n
+ *                     (grad: AMG_MLP_NPARAM floats, loss: 1 float, both
+ *                     overwritten)
+ *   amg_mlp_adam      one Adam step (beta 0.9 / 0.999, eps 1e-8) of step
+ *                     number `step` >= 1 with learning rate lr; m and v are
+ *                     the moment buffers (zero before step 1)
+ */
+int amg_mlp_forward(const float* theta, const float* x, int32_t n, float* y, void* stream);
+int amg_mlp_gradient(const float* theta, const float* x, const float* t, int32_t n, float* grad,
+                     float* loss, void* stream);
+int amg_mlp_adam(float* theta, const float* grad, float* m, float* v, int32_t step, float lr,
+                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -217,6 +217,11 @@ class Options:
     coarse_dofs: int = 300
     separate: bool = True           # separated (new) vs non-separating graph
     omega_p: float = 0.125          # sGS pressure step
+    # learned multipliers (1: the plain method): relaxation, coarse-grid
+    # correction scale, sGS pressure step
+    ws: float = 1.0
+    wc: float = 1.0
+    wp: float = 1.0
 
 
 @dataclass
@@ -368,10 +373,11 @@ def jacobi_sweep(lv: Level, x, b, omega):
     return x + omega * apply_dinv(lv.dinv, b - lv.A @ x)
 
 
-def gs_sweep(lv: Level, x, b, reverse: bool = False):
+def gs_sweep(lv: Level, x, b, reverse: bool = False, ws: float = 1.0):
     """Multicolour block Gauss-Seidel: per colour, every row of that colour is
     updated from the values at the start of the colour,
-    x_i <- x_i + D_i^{-1} (b_i - sum_j A_ij x_j)."""
+    x_i <- x_i + ws D_i^{-1} (b_i - sum_j A_ij x_j)  (ws = 1: Gauss-Seidel; other
+    values: symmetric over-/under-relaxation with the same colour order)."""
     x = x.copy()
     order = range(len(lv.colour_rows))
     if reverse:
@@ -380,7 +386,7 @@ def gs_sweep(lv: Level, x, b, reverse: bool = False):
         rows = lv.colour_rows[c]
         sidx = (3 * rows[:, None] + np.arange(3)).ravel()
         r = b[sidx] - lv.colour_A[c] @ x
-        x[sidx] += apply_dinv(lv.dinv[rows], r)
+        x[sidx] += ws * apply_dinv(lv.dinv[rows], r)
     return x
 
 
@@ -391,8 +397,8 @@ def smooth(h: Hierarchy, l: int, x, b, post: bool):
         from . import saddle as sd
         return sd.smooth(h, l, x, b, post)
     if o.smoother == "jacobi":
-        return jacobi_sweep(lv, x, b, o.omega)
-    return gs_sweep(lv, x, b, reverse=post)
+        return jacobi_sweep(lv, x, b, o.omega * o.ws)
+    return gs_sweep(lv, x, b, reverse=post, ws=o.ws)
 
 
 def operator(h: Hierarchy, l: int):
@@ -437,7 +443,7 @@ def amg_cycle(h: Hierarchy, l: int, x, b):
         xc = np.zeros_like(bc)
         for _ in range(o.nu):
             xc = amg_cycle(h, l + 1, xc, bc)
-    x = x + prolong(h, l, xc)
+    x = x + o.wc * prolong(h, l, xc)
     for _ in range(o.m_post):
         x = smooth(h, l, x, b, post=True)
     return x

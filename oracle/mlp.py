@@ -1,0 +1,69 @@
+"""Plain FP64 reference of the small network of the learned weights (TEST
+INFRASTRUCTURE ONLY: used by tests/ to check the CUDA training kernels).
+
+y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with x in R^16, two hidden layers of
+64, one output; loss = mean over the batch of (y - t)^2.  Gradients by the
+chain rule, written out layer by layer.  Parameter vector layout (shared with
+the CUDA kernels as data): W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64],
+b3 [1] (5313 values).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NI, NH = 16, 64
+SIZES = [("W1", (NH, NI)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)), ("W3", (NH,)),
+         ("b3", (1,))]
+NPARAM = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def unpack(theta: np.ndarray) -> dict:
+    out, o = {}, 0
+    for name, shape in SIZES:
+        n = int(np.prod(shape))
+        out[name] = theta[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def pack(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
+
+
+def forward(theta: np.ndarray, X: np.ndarray):
+    p = unpack(theta)
+    z1 = X @ p["W1"].T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ p["W3"] + p["b3"][0]
+    return y, (X, z1, h1, z2, h2)
+
+
+def loss(theta: np.ndarray, X: np.ndarray, t: np.ndarray) -> float:
+    y, _ = forward(theta, X)
+    return float(np.mean((y - t) ** 2))
+
+
+def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray) -> np.ndarray:
+    p = unpack(theta)
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    B = len(t)
+    dy = 2.0 * (y - t) / B                      # dL/dy
+    g = {"W3": h2.T @ dy, "b3": np.array([dy.sum()])}
+    dz2 = np.outer(dy, p["W3"]) * (z2 > 0)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ p["W2"]) * (z1 > 0)
+    g["W1"] = dz1.T @ X
+    g["b1"] = dz1.sum(axis=0)
+    return pack(g)
+
+
+def init(seed: int) -> np.ndarray:
+    """He-scaled normal weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    p = {"W1": rng.standard_normal((NH, NI)) * np.sqrt(2.0 / NI), "b1": np.zeros(NH),
+         "W2": rng.standard_normal((NH, NH)) * np.sqrt(2.0 / NH), "b2": np.zeros(NH),
+         "W3": rng.standard_normal(NH) * np.sqrt(1.0 / NH), "b3": np.zeros(1)}
+    return pack(p)

@@ -39,7 +39,16 @@ KINDS = {"laplace": AMG_VECTOR_LAPLACE, "elasticity": AMG_ELASTICITY,
 EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
             "amg_level_info_get", "amg_level_copy", "amg_apply_preconditioner",
             "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
-            "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc"]
+            "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc",
+            "amg_features", "amg_set_weights", "amg_get_weights", "amg_learn_weights",
+            "amg_mlp_forward", "amg_mlp_gradient", "amg_mlp_adam"]
+
+N_FEATURES = 13
+MLP_INPUTS = 16
+MLP_NPARAM = 5313
+# candidate grid of amg_learn_weights (the header's AMG_WS_* / AMG_WC_* / AMG_WP_* values)
+WS_RANGE, WC_RANGE, WP_LOG2_RANGE = (0.6, 1.6), (0.8, 1.9), (-1.0, 2.0)
+GRID = (11, 12, 7)
 
 OPS = {"apply": 0, "residual": 1, "smooth": 2, "restrict": 3, "prolong": 4, "precond": 5}
 
@@ -84,6 +93,18 @@ class AmgStats(C.Structure):
                 "level_nnzb": list(self.level_nnzb[:nl]),
                 "level_colours": list(self.level_colours[:nl]),
                 "level_group": list(self.level_group[:nl])}
+
+
+class AmgLearned(C.Structure):
+    _fields_ = [("weights", C.c_double * 3), ("predicted", C.c_double),
+                ("rho_plain", C.c_double), ("rho_learned", C.c_double),
+                ("fell_back", C.c_int32), ("n_candidates", C.c_int32),
+                ("probe_iterations_plain", C.c_int32), ("probe_iterations_learned", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["weights"] = list(self.weights)
+        return d
 
 
 class AmgLevelInfo(C.Structure):
@@ -136,6 +157,20 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_solve_batched.restype = C.c_int
     lib.amg_apply_preconditioner_noalloc.argtypes = [vp, vp, vp]
     lib.amg_apply_preconditioner_noalloc.restype = C.c_int
+    lib.amg_features.argtypes = [vp, vp]
+    lib.amg_features.restype = C.c_int
+    lib.amg_set_weights.argtypes = [vp, vp]
+    lib.amg_set_weights.restype = C.c_int
+    lib.amg_get_weights.argtypes = [vp, vp, i32]
+    lib.amg_get_weights.restype = C.c_int
+    lib.amg_learn_weights.argtypes = [vp, vp, C.POINTER(AmgLearned)]
+    lib.amg_learn_weights.restype = C.c_int
+    lib.amg_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    lib.amg_mlp_forward.restype = C.c_int
+    lib.amg_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    lib.amg_mlp_gradient.restype = C.c_int
+    lib.amg_mlp_adam.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp]
+    lib.amg_mlp_adam.restype = C.c_int
     _lib = lib
     return lib
 
@@ -286,6 +321,48 @@ class Handle:
     def level_smooth(self, level: int, x_dev, b_dev, post: bool = False):
         _check(load_library().amg_level_smooth(self.h, level, 1 if post else 0, _ptr(x_dev),
                                                _ptr(b_dev)), self.h)
+
+    def features(self) -> np.ndarray:
+        """The 13 statistics of the hierarchy that the weight network reads."""
+        out = np.zeros(N_FEATURES)
+        _check(load_library().amg_features(self.h, out.ctypes.data), self.h)
+        return out
+
+    def set_weights(self, ws: float, wc: float, wp: float = 1.0):
+        w = np.array([ws, wc, wp], dtype=np.float64)
+        _check(load_library().amg_set_weights(self.h, w.ctypes.data), self.h)
+
+    def weights(self) -> np.ndarray:
+        """Per-level (ws, wc, wp, 1) as an (n_levels, 4) array."""
+        out = np.zeros((self.n_levels(), 4))
+        _check(load_library().amg_get_weights(self.h, out.ctypes.data, out.size), self.h)
+        return out
+
+    def learn_weights(self, theta) -> AmgLearned:
+        """amg_learn_weights with host float32 network parameters."""
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == MLP_NPARAM
+        res = AmgLearned()
+        _check(load_library().amg_learn_weights(self.h, th.ctypes.data, C.byref(res)), self.h)
+        return res
+
+
+def mlp_forward(theta, x, y, stream=None):
+    """y[i] = net(theta, x[i]) on device tensors (float32; x of shape (n, 16))."""
+    n = int(x.shape[0])
+    _check(load_library().amg_mlp_forward(_ptr(theta), _ptr(x), n, _ptr(y), stream))
+
+
+def mlp_gradient(theta, x, t, grad, loss, stream=None):
+    """grad, loss of the mean squared error of the net on (x, t), device tensors."""
+    n = int(x.shape[0])
+    _check(load_library().amg_mlp_gradient(_ptr(theta), _ptr(x), _ptr(t), n, _ptr(grad),
+                                           _ptr(loss), stream))
+
+
+def mlp_adam(theta, grad, m, v, step: int, lr: float, stream=None):
+    _check(load_library().amg_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), step,
+                                       float(lr), stream))
 
 
 def setup_problem(prob, options: AmgOptions | None = None, stream=None) -> Handle:

@@ -233,6 +233,21 @@ int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stat
 // noalloc.cu: the preconditioner application with static staging vectors
 void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
 
+// learned.cu: statistics of the hierarchy, weights, selection with fallback
+constexpr double kProbeTol = 1e-4;
+void compute_features(amg_handle* h, double* out);
+void set_weights(amg_handle* h, const double* w3);
+void get_weights(const amg_handle* h, double* out);
+void learn_weights(amg_handle* h, const float* theta_host, amg_learned* out);
+
+// mlp.cu: the network's kernels
+int mlp_nparam();
+void mlp_forward(const float* theta, const float* X, int n, float* y, cudaStream_t s);
+void mlp_gradient(const float* theta, const float* X, const float* t, int n, float* grad,
+                  float* loss, cudaStream_t s);
+void mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr,
+              cudaStream_t s);
+
 // batched.cu: all problems and right-hand sides in one graph launch
 int solve_batched(amg_handle* const* hs, int np, int nrhs, const double* const* B,
                   double* const* X, double tol, amg_stats* stats, double* ms_out);

@@ -531,4 +531,69 @@ int amg_solve_batched(amg_handle* const* handles, int32_t n_problems, int32_t n_
   });
 }
 
+int amg_features(amg_handle* h, double* features) {
+  return guarded(h, [&]() -> int {
+    if (!h || !features) fail(AMG_ERR_INVALID, "null argument");
+    compute_features(h, features);
+    return AMG_OK;
+  });
+}
+
+int amg_set_weights(amg_handle* h, const double* w) {
+  return guarded(h, [&]() -> int {
+    if (!h || !w) fail(AMG_ERR_INVALID, "null argument");
+    for (int e = 0; e < 3; ++e)
+      if (!(std::isfinite(w[e]) && w[e] > 0.0)) fail(AMG_ERR_INVALID, "weights must be finite and > 0");
+    set_weights(h, w);
+    return AMG_OK;
+  });
+}
+
+int amg_get_weights(const amg_handle* hc, double* w, int32_t capacity) {
+  amg_handle* h = const_cast<amg_handle*>(hc);
+  return guarded(h, [&]() -> int {
+    if (!h || !w) fail(AMG_ERR_INVALID, "null argument");
+    if (capacity < 4 * (int64_t)h->L.size()) fail(AMG_ERR_INVALID, "capacity < 4 * n_levels");
+    get_weights(h, w);
+    return AMG_OK;
+  });
+}
+
+int amg_learn_weights(amg_handle* h, const float* theta, amg_learned* out) {
+  return guarded(h, [&]() -> int {
+    if (!h || !theta || !out) fail(AMG_ERR_INVALID, "null argument");
+    for (int k = 0; k < AMG_MLP_NPARAM; ++k)
+      if (!std::isfinite(theta[k])) fail(AMG_ERR_INVALID, "non-finite network parameter");
+    learn_weights(h, theta, out);
+    return AMG_OK;
+  });
+}
+
+int amg_mlp_forward(const float* theta, const float* x, int32_t n, float* y, void* stream) {
+  return guarded(nullptr, [&]() -> int {
+    if (n < 0 || (n > 0 && (!theta || !x || !y))) fail(AMG_ERR_INVALID, "bad argument");
+    mlp_forward(theta, x, n, y, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
+int amg_mlp_gradient(const float* theta, const float* x, const float* t, int32_t n, float* grad,
+                     float* loss, void* stream) {
+  return guarded(nullptr, [&]() -> int {
+    if (n < 0 || !grad || !loss || (n > 0 && (!theta || !x || !t)))
+      fail(AMG_ERR_INVALID, "bad argument");
+    mlp_gradient(theta, x, t, n, grad, loss, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
+int amg_mlp_adam(float* theta, const float* grad, float* m, float* v, int32_t step, float lr,
+                 void* stream) {
+  return guarded(nullptr, [&]() -> int {
+    if (!theta || !grad || !m || !v || step < 1 || !(lr > 0.f)) fail(AMG_ERR_INVALID, "bad argument");
+    mlp_adam(theta, grad, m, v, step, lr, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
 }  // extern "C"

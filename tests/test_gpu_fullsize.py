@@ -30,9 +30,9 @@ def _full_K(p):
     return sp.bmat([[A, Bm.T], [Bm, -Cm]]).tocsr()
 
 
-def _check(prob, precision=1):
+def _check(prob, precision=1, **opts):
     from paper_1503_01287_gb300 import binding as B
-    h = B.setup_problem(prob, B.default_options(precision=precision))
+    h = B.setup_problem(prob, B.default_options(precision=precision, **opts))
     # level-0 C/F splits equal the oracle's greedy independent sets
     pat = amg.block_pattern(prob.a_rowptr, prob.a_col, prob.n_nodes)
     g = amg.coarsening_graph(pat, np.asarray(prob.tags) & amg.TAG_TYPE_MASK, True)
@@ -64,6 +64,9 @@ def test_stokes_lid_24_full_size():
 
 
 def test_mixed_elasticity_40_full_size():
-    """Mixed elasticity, nu = 0.4999, jittered 40^3 cubes (1,663,244 DOF), FP32 cycle."""
+    """Mixed elasticity, nu = 0.4999, jittered 40^3 cubes (1,663,244 DOF), FP32 cycle.
+    FGMRES(50) stagnates near 1e-4 on this system (1500 iterations); with a restart
+    length of 300 it converges in about 140 iterations."""
     prob = fp.mixed_elasticity_family(40, [0.4999], seed=5)[0]
-    _check(prob)
+    st, _ = _check(prob, gmres_restart=300, max_iterations=600)
+    assert st.iterations <= 300

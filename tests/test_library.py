@@ -47,6 +47,10 @@ int main(void) {
          sizeof(amg_level_info));
   printf("%zu %zu %zu %zu\n", offsetof(amg_matrix, device_ptrs), offsetof(amg_options, omega_p),
          offsetof(amg_stats, level_colours), offsetof(amg_options, cycle_kernel));
+  printf("%zu %zu %d %d %d\n", sizeof(amg_learned), offsetof(amg_learned, probe_iterations_learned),
+         AMG_N_FEATURES, AMG_MLP_INPUTS, AMG_MLP_NPARAM);
+  printf("%.17g %.17g %d %.17g %.17g %d %.17g %.17g %d\n", AMG_WS_MIN, AMG_WS_MAX, AMG_GRID_NWS,
+         AMG_WC_MIN, AMG_WC_MAX, AMG_GRID_NWC, AMG_WP_LOG2_MIN, AMG_WP_LOG2_MAX, AMG_GRID_NWP);
   return 0;
 }
 '''
@@ -56,7 +60,8 @@ int main(void) {
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
-    sizes = [int(v) for v in out]
+    sizes = [int(v) for v in out[:13]]
+    grid = [float(v) for v in out[13:]]
     assert sizes[0] == ctypes.sizeof(B.AmgMatrix)
     assert sizes[1] == ctypes.sizeof(B.AmgOptions)
     assert sizes[2] == ctypes.sizeof(B.AmgStats)
@@ -65,6 +70,13 @@ int main(void) {
     assert sizes[5] == B.AmgOptions.omega_p.offset
     assert sizes[6] == B.AmgStats.level_colours.offset
     assert sizes[7] == B.AmgOptions.cycle_kernel.offset
+    assert sizes[8] == ctypes.sizeof(B.AmgLearned)
+    assert sizes[9] == B.AmgLearned.probe_iterations_learned.offset
+    assert sizes[10:13] == [B.N_FEATURES, B.MLP_INPUTS, B.MLP_NPARAM]
+    assert grid == [*B.WS_RANGE, B.GRID[0], *B.WC_RANGE, B.GRID[1], *B.WP_LOG2_RANGE, B.GRID[2]]
+    # inputs = features + (ws, wc, log2 wp); parameter count of 16 -> 64 -> 64 -> 1
+    assert B.MLP_INPUTS == B.N_FEATURES + 3
+    assert B.MLP_NPARAM == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 def test_default_options(lib):
@@ -84,3 +96,8 @@ def test_setup_rejects_bad_arguments_without_gpu(lib):
     assert lib.amg_solve(None, None, None, 1e-8, 0, None) == -1
     lib.amg_free(None)   # NULL-safe
     assert B.AMG_OK == 0
+    assert lib.amg_features(None, None) == -1
+    assert lib.amg_set_weights(None, None) == -1
+    assert lib.amg_learn_weights(None, None, None) == -1
+    assert lib.amg_mlp_forward(None, None, -1, None, None) == -1
+    assert lib.amg_mlp_adam(None, None, None, None, 0, 0.0, None) == -1

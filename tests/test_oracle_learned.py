@@ -1,0 +1,99 @@
+"""Pins of the oracle's learned-weights parts (no GPU): the network's gradient
+against central finite differences of its loss, its forward pass against a
+network built by hand, and the hierarchy statistics against closed forms and
+a second, matrix-level formulation of the same definitions."""
+import numpy as np
+import scipy.sparse as sp
+
+from fem_inputs import problems as fp
+from oracle import amg, features, mlp
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    theta = mlp.init(5) + 0.05 * rng.standard_normal(mlp.NPARAM)
+    X = rng.standard_normal((24, mlp.NI))
+    t = rng.standard_normal(24)
+    g = mlp.grad(theta, X, t)
+    idx = rng.choice(mlp.NPARAM, 200, replace=False)
+    idx = np.concatenate([idx, [mlp.NPARAM - 1, 0, 64 * 16, 64 * 16 + 64]])  # b3, W1, b1, W2
+    h = 1e-6
+    fd = np.empty(len(idx))
+    for k, i in enumerate(idx):
+        e = np.zeros(mlp.NPARAM)
+        e[i] = h
+        fd[k] = (mlp.loss(theta + e, X, t) - mlp.loss(theta - e, X, t)) / (2 * h)
+    assert np.abs(fd - g[idx]).max() <= 1e-6 * max(1.0, np.abs(g[idx]).max())
+
+
+def test_mlp_forward_of_a_hand_built_network():
+    """W1 picks input 13, W2 copies unit 0, W3 scales by c: y = c * relu(x_13) + b3."""
+    p = {k: np.zeros(s) for k, s in mlp.SIZES}
+    p["W1"][0, 13] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0] = -2.5
+    p["b3"][0] = 0.75
+    theta = mlp.pack(p)
+    X = np.zeros((4, mlp.NI))
+    X[:, 13] = [0.6, 1.0, 1.6, -0.3]
+    y, _ = mlp.forward(theta, X)
+    assert np.allclose(y, -2.5 * np.maximum(X[:, 13], 0.0) + 0.75, rtol=0, atol=1e-15)
+    assert mlp.NPARAM == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def test_features_vector_laplacian_closed_form():
+    """Blocks a_ij I_3: |D_i| |D_i^-1| = sqrt(3) a * sqrt(3) / a = 3 on every level."""
+    prob = fp.vector_laplace_problem(4, seed=0)
+    h = amg.build_hierarchy(prob)
+    f = features.features(h, False)
+    assert abs(f[1] - np.log10(3.0)) <= 1e-13
+    assert abs(f[6] - np.log10(3.0)) <= 1e-13
+    assert f[0] == np.log10(prob.n_dof) / 7.0
+    assert f[11] == 0.0 and f[12] == 0.0
+
+
+def test_features_are_scale_free():
+    prob = fp.elasticity_problem(4, seed=2)
+    f1 = features.features(amg.build_hierarchy(prob), False)
+    prob.a_val = prob.a_val * 7.3
+    f2 = features.features(amg.build_hierarchy(prob), False)
+    assert np.allclose(f1, f2, rtol=0, atol=1e-12)
+
+
+def _share_and_size(lv):
+    """The F-node statistics as matrix products: N (Frobenius norms of the
+    off-diagonal blocks), M (1 where column j is a C node in the pattern of row
+    i of P), share_i = (N o M) 1 / N 1."""
+    n = lv.n
+    norms = np.linalg.norm(lv.val.reshape(-1, 9), axis=1)
+    rows = np.repeat(np.arange(n), np.diff(lv.rowptr))
+    off = rows != lv.col
+    N = sp.csr_matrix((norms[off], (rows[off], lv.col[off])), shape=(n, n))
+    c_nodes = np.nonzero(lv.state == amg.STATE_C)[0]
+    E = sp.csr_matrix((np.ones(len(c_nodes)), (lv.coarse_of_fine[c_nodes], c_nodes)),
+                      shape=(lv.P_structure.shape[1], n))
+    M = (lv.P_structure @ E).tocsr()
+    M.data[:] = 1.0
+    num = np.asarray(N.multiply(M).sum(axis=1)).ravel()
+    den = np.asarray(N.sum(axis=1)).ravel()
+    psize = np.diff(lv.P_structure.tocsr().indptr)
+    sel = (lv.state == amg.STATE_F) & ((lv.tags & amg.TAG_DIRICHLET) == 0) & (psize > 0)
+    share = np.where(den[sel] > 0, num[sel] / np.where(den[sel] > 0, den[sel], 1.0), 0.0)
+    return share.mean(), psize[sel].mean() / 8.0
+
+
+def test_features_interpolation_statistics_by_matrix_products():
+    for prob, saddle in [(fp.elasticity_problem(4, seed=2), False),
+                         (fp.mixed_elasticity_family(4, [0.49], seed=3)[0], True)]:
+        h = amg.build_hierarchy(prob)
+        f = features.features(h, saddle)
+        for l, base in [(0, 1), (1, 6)]:
+            if l + 1 >= len(h.levels):
+                continue
+            share, size = _share_and_size(h.levels[l])
+            assert abs(f[base + 3] - share) <= 1e-13
+            assert abs(f[base + 4] - size) <= 1e-15
+            assert 0.0 < share <= 1.0
+        assert f[12] == (1.0 if saddle else 0.0)
+        if saddle:
+            assert 0.0 < f[11] < 1.0
