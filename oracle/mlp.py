@@ -6,6 +6,12 @@ y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with x in R^16, two hidden layers of
 chain rule, written out layer by layer.  Parameter vector layout (shared with
 the CUDA kernels as data): W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64],
 b3 [1] (5313 values).
+
+`rnd`, when given, is applied to both operands of every matrix product (the
+two hidden-layer products forward; the weight-gradient and back-propagation
+products of those layers backward), so that a test can evaluate the network
+with operands rounded to the precision a kernel multiplies in; everything else
+stays FP64.  Without it the whole computation is FP64.
 """
 from __future__ import annotations
 
@@ -30,11 +36,16 @@ def pack(p: dict) -> np.ndarray:
     return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
 
 
-def forward(theta: np.ndarray, X: np.ndarray):
+def _id(a):
+    return a
+
+
+def forward(theta: np.ndarray, X: np.ndarray, rnd=None):
+    r = rnd or _id
     p = unpack(theta)
-    z1 = X @ p["W1"].T + p["b1"]
+    z1 = r(X) @ r(p["W1"]).T + p["b1"]
     h1 = np.maximum(z1, 0.0)
-    z2 = h1 @ p["W2"].T + p["b2"]
+    z2 = r(h1) @ r(p["W2"]).T + p["b2"]
     h2 = np.maximum(z2, 0.0)
     y = h2 @ p["W3"] + p["b3"][0]
     return y, (X, z1, h1, z2, h2)
@@ -45,17 +56,18 @@ def loss(theta: np.ndarray, X: np.ndarray, t: np.ndarray) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray) -> np.ndarray:
+def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray, rnd=None) -> np.ndarray:
+    r = rnd or _id
     p = unpack(theta)
-    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    y, (X, z1, h1, z2, h2) = forward(theta, X, rnd)
     B = len(t)
     dy = 2.0 * (y - t) / B                      # dL/dy
     g = {"W3": h2.T @ dy, "b3": np.array([dy.sum()])}
     dz2 = np.outer(dy, p["W3"]) * (z2 > 0)
-    g["W2"] = dz2.T @ h1
+    g["W2"] = r(dz2).T @ r(h1)
     g["b2"] = dz2.sum(axis=0)
-    dz1 = (dz2 @ p["W2"]) * (z1 > 0)
-    g["W1"] = dz1.T @ X
+    dz1 = (r(dz2) @ r(p["W2"])) * (z1 > 0)
+    g["W1"] = r(dz1).T @ r(X)
     g["b1"] = dz1.sum(axis=0)
     return pack(g)
 

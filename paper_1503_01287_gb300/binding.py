@@ -199,11 +199,18 @@ def default_options(**over) -> AmgOptions:
 
 
 def _ptr(a):
-    """Address of a C-contiguous numpy array or torch tensor (None -> NULL)."""
+    """Address of a C-contiguous numpy array or torch tensor (None -> NULL).
+
+    For a CUDA tensor the caller's current stream is synchronised first: the
+    library works on its own stream, so work the caller queued on that tensor
+    (a fill, a copy) must be complete before the library reads or writes it."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
         assert a.is_contiguous()
+        if a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
         return a.data_ptr()
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data
@@ -334,7 +341,7 @@ class Handle:
 
     def weights(self) -> np.ndarray:
         """Per-level (ws, wc, wp, 1) as an (n_levels, 4) array."""
-        out = np.zeros((self.n_levels(), 4))
+        out = np.zeros((self.n_levels, 4))
         _check(load_library().amg_get_weights(self.h, out.ctypes.data, out.size), self.h)
         return out
 

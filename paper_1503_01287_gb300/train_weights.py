@@ -1,0 +1,214 @@
+"""Trains the learned-weights network on convergence factors measured by the
+AMG solver itself, on the GPU, with the library's own network kernels.
+
+    python -m paper_1503_01287_gb300.train_weights --problems 2000 \
+        --out paper_1503_01287_gb300/weights/mlp_theta.npy
+
+Data.  Seeded problems with n^3 cubes, n uniform in 8..16: even indices are
+mixed displacement-pressure elasticity (nu = 0.5 - 10^U[-4, -1.3], vertices
+jittered by U[0, 0.2] h), odd indices pure-displacement elasticity (nu in
+U[0.2, 0.45], side lengths U[1, 4] per axis, N(0, 1) traction).  Each problem
+is set up once (FP32 cycle; flexible CG or FGMRES(300)) and solved to 1e-8
+with the plain weights and with `--candidates` random (ws, wc, wp) from the
+box of the selection grid; a solve's convergence factor is
+rho = (||r_k|| / ||r_0||)^(1/k).  One training sample is
+  input  = the hierarchy's 13 statistics (amg_features), ws, wc, log2 wp
+  target = log10(rho_candidate / rho_plain), clipped to [-1, 1]
+(wp and its input are 1 and 0 for the SPD problems).  The plain weights give
+target 0 by definition, so the plain method is the yardstick of every sample.
+
+Training.  Adam on the mean squared error with the amg_mlp_* kernels (BF16
+products, FP32 accumulation), full batch, problems split 90 / 10 into
+training and validation sets.  The parameters (float32, AMG_MLP_NPARAM) are
+written to --out and a summary (data, losses, timings) next to it as .json.
+
+Problems are generated by a process pool started with `spawn` before the
+first CUDA call, a chunk ahead of the GPU measurements.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import time
+
+import numpy as np
+
+SEED0 = 20_000
+RESTART = 300
+MAXIT = 400
+
+
+def problem_spec(i: int, seed0: int = SEED0) -> dict:
+    rng = np.random.default_rng(seed0 + i)
+    n = int(rng.integers(8, 17))
+    if i % 2 == 0:
+        return {"kind": "mixed", "n": n, "nu": float(0.5 - 10.0 ** rng.uniform(-4.0, -1.3)),
+                "jitter": float(rng.uniform(0.0, 0.2)), "seed": seed0 + i}
+    return {"kind": "elasticity", "n": n, "nu": float(rng.uniform(0.2, 0.45)),
+            "lengths": tuple(float(v) for v in rng.uniform(1.0, 4.0, 3)), "seed": seed0 + i}
+
+
+def make_problem(spec: dict):
+    from fem_inputs import problems as fp
+    if spec["kind"] == "mixed":
+        return fp.mixed_elasticity_family(spec["n"], [spec["nu"]], seed=spec["seed"],
+                                          jitter=spec["jitter"])[0]
+    return fp.elasticity_problem(spec["n"], seed=spec["seed"], nu=spec["nu"],
+                                 lengths=spec["lengths"], traction="gaussian")
+
+
+def candidate_box(rng: np.random.Generator, saddle: bool):
+    from . import binding as B
+    ws = rng.uniform(*B.WS_RANGE)
+    wc = rng.uniform(*B.WC_RANGE)
+    lp = rng.uniform(*B.WP_LOG2_RANGE) if saddle else 0.0
+    return ws, wc, lp
+
+
+def _rho(st) -> float:
+    if st.iterations <= 0:
+        return 0.0
+    r = st.rel_residual
+    if not np.isfinite(r) or r <= 0.0:
+        return 10.0
+    return float(r ** (1.0 / st.iterations))
+
+
+def measure(prob, n_cand: int, rng: np.random.Generator, torch):
+    """(features, [(ws, wc, lp, target, iterations, ms)], plain (rho, iterations, ms))."""
+    from . import binding as B
+    saddle = prob.kind in ("mixed", "stokes")
+    h = B.setup_problem(prob, B.default_options(precision=1, gmres_restart=RESTART,
+                                                max_iterations=MAXIT))
+    feats = h.features()
+    b = torch.from_numpy(prob.rhs()).cuda()
+    x = torch.zeros_like(b)
+
+    def run(ws, wc, wp):
+        h.set_weights(ws, wc, wp)
+        x.zero_()
+        try:
+            st = h.solve(b, x, 1e-8, device_ptrs=True)
+        except B.AmgError:
+            return 10.0, MAXIT, float("nan")
+        return _rho(st), st.iterations, st.solve_ms
+
+    rho_p, it_p, ms_p = run(1.0, 1.0, 1.0)
+    rows = [(1.0, 1.0, 0.0, 0.0, it_p, ms_p)]
+    for _ in range(n_cand):
+        ws, wc, lp = candidate_box(rng, saddle)
+        rho, it, ms = run(ws, wc, 2.0 ** lp)
+        t = float(np.clip(np.log10(max(rho, 1e-12) / rho_p), -1.0, 1.0))
+        rows.append((ws, wc, lp, t, it, ms))
+    h.free()
+    return feats, rows, (rho_p, it_p, ms_p)
+
+
+def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: float, seed: int,
+          torch):
+    from . import binding as B
+    rng = np.random.default_rng(seed)
+    # He-scaled normal initialisation, zero biases (W1, b1, W2, b2, W3, b3)
+    th = np.concatenate([rng.standard_normal(64 * 16) * np.sqrt(2 / 16), np.zeros(64),
+                         rng.standard_normal(64 * 64) * np.sqrt(2 / 64), np.zeros(64),
+                         rng.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa
+    theta = dev(th)
+    g = torch.zeros(B.MLP_NPARAM, device="cuda")
+    m, v = torch.zeros_like(g), torch.zeros_like(g)
+    loss = torch.zeros(1, device="cuda")
+    Xt, Tt, Xv, Tv = dev(X[train_idx]), dev(T[train_idx]), dev(X[val_idx]), dev(T[val_idx])
+    hist = []
+    t0 = time.time()
+    for step in range(1, steps + 1):
+        B.mlp_gradient(theta, Xt, Tt, g, loss)
+        B.mlp_adam(theta, g, m, v, step, lr)
+        if step % 500 == 0 or step == steps:
+            tr = loss.item()
+            yv = torch.zeros(len(val_idx), device="cuda")
+            B.mlp_forward(theta, Xv, yv)
+            vl = float(((yv - Tv) ** 2).mean().item()) if len(val_idx) else float("nan")
+            hist.append({"step": step, "train_mse": tr, "val_mse": vl})
+    torch.cuda.synchronize()
+    return theta.cpu().numpy(), hist, time.time() - t0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--problems", type=int, default=2000)
+    ap.add_argument("--candidates", type=int, default=6)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights",
+                                                  "mlp_theta.npy"))
+    args = ap.parse_args(argv)
+
+    specs = [problem_spec(i) for i in range(args.problems)]
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(args.workers)          # before the first CUDA call
+    import torch
+    from . import binding as B
+    B.load_library()
+    rng = np.random.default_rng(7)
+    feats, rows, plain, owner = [], [], [], []
+    t0 = time.time()
+    chunks = [specs[k:k + args.chunk] for k in range(0, len(specs), args.chunk)]
+    pending = pool.map_async(make_problem, chunks[0]) if chunks else None
+    gen_wait = 0.0
+    for ci in range(len(chunks)):
+        tw = time.time()
+        probs = pending.get()
+        gen_wait += time.time() - tw
+        pending = pool.map_async(make_problem, chunks[ci + 1]) if ci + 1 < len(chunks) else None
+        for k, prob in enumerate(probs):
+            f, r, p = measure(prob, args.candidates, rng, torch)
+            pi = ci * args.chunk + k
+            for row in r:
+                feats.append(f)
+                rows.append(row)
+                owner.append(pi)
+            plain.append(p)
+        del probs
+        print(f"chunk {ci + 1}/{len(chunks)}: {len(plain)} problems, "
+              f"{time.time() - t0:.0f} s", flush=True)
+    pool.close()
+    pool.join()
+    measure_s = time.time() - t0
+
+    F = np.array(feats)
+    R = np.array(rows)
+    X = np.concatenate([F, R[:, 0:3]], axis=1).astype(np.float32)
+    T = R[:, 3].astype(np.float32)
+    owner = np.array(owner)
+    perm = np.random.default_rng(11).permutation(len(plain))
+    val_p = set(perm[:max(1, len(plain) // 10)].tolist())
+    val_idx = np.array([i for i in range(len(T)) if owner[i] in val_p], dtype=np.int64)
+    train_idx = np.array([i for i in range(len(T)) if owner[i] not in val_p], dtype=np.int64)
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch)
+
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.save(args.out, theta.astype(np.float32))
+    Pl = np.array(plain)
+    summary = {
+        "problems": args.problems, "candidates_per_problem": args.candidates,
+        "samples": int(len(T)), "train_samples": int(len(train_idx)),
+        "val_samples": int(len(val_idx)), "seed0": SEED0, "steps": args.steps, "lr": args.lr,
+        "target_mean": float(T.mean()), "target_std": float(T.std()),
+        "share_candidates_better_than_plain": float(np.mean(R[R[:, 3] != 0.0, 3] < 0.0))
+        if np.any(R[:, 3] != 0.0) else 0.0,
+        "plain_iterations_mean": float(Pl[:, 1].mean()),
+        "history": hist, "measure_s": measure_s, "generation_wait_s": gen_wait,
+        "train_s": train_s,
+    }
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
+        json.dump(summary, fh, indent=1)
+    print(json.dumps({k: v for k, v in summary.items() if k != "history"}), flush=True)
+    print(json.dumps(hist[-1]), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+"""The learned-weights path on the GPU, through the C ABI.
+
+Network kernels: the forward pass and the gradient against the FP64 oracle
+evaluated with the operands of its four matrix products rounded to BF16 the way
+the kernel rounds them (round to nearest even), so that both sides multiply the
+same numbers; what remains is FP32 accumulation (about 1e-7 relative per sum)
+and the rare BF16 rounding of a hidden value that lands on the other side of a
+rounding boundary in FP32 and FP64 (one BF16 ulp, 2^-8 relative, in one of
+~10^4 values).  Bounds: 1e-3 of the output scale and 2e-3 per gradient block.
+Inputs are drawn so that no pre-activation is within 1e-4 of 0, where the two
+precisions could take different ReLU branches.
+
+Statistics: the 13 inputs against oracle/features.py on hierarchies that are
+bit-exact between the two sides (1e-10 absolute; the sums are FP64 in a
+different order).  Weights: one preconditioner application with (ws, wc, wp)
+against the oracle's multipliers (1e-10 relative, the preconditioner bound).
+"""
+import numpy as np
+import pytest
+
+from fem_inputs import problems as fp
+from oracle import amg, features, mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def B():
+    from paper_1503_01287_gb300 import binding
+    return binding
+
+
+def bf16(a):
+    """Round to the nearest BF16 value, ties to even (IEEE round-to-nearest on the
+    upper 16 bits of the binary32 pattern), returned as float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _draw(n, seed):
+    """theta, X, t with every pre-activation at least 1e-4 away from 0."""
+    for s in range(seed, seed + 50):
+        rng = np.random.default_rng(s)
+        theta = f32(mlp.init(s) + 0.02 * rng.standard_normal(mlp.NPARAM))
+        X = f32(rng.standard_normal((n, mlp.NI)))
+        t = f32(rng.standard_normal(n))
+        _, (_, z1, _, z2, _) = mlp.forward(theta, X, bf16)
+        if np.abs(z1).min() > 1e-4 and np.abs(z2).min() > 1e-4:
+            return theta, X, t
+    raise AssertionError("no draw with a margin")
+
+
+@pytest.mark.parametrize("n", [1, 64, 200])
+def test_mlp_forward_matches_oracle(n):
+    theta, X, _ = _draw(n, 10 + n)
+    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    B().mlp_forward(dev(theta), dev(X), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    want, _ = mlp.forward(theta, X, bf16)
+    assert np.abs(got - want).max() <= 1e-3 * max(1.0, np.abs(want).max())
+    exact, _ = mlp.forward(theta, X)           # all-FP64 network: BF16-level agreement
+    assert np.abs(got - exact).max() <= 3e-2 * max(1.0, np.abs(exact).max())
+
+
+@pytest.mark.parametrize("n", [37, 256])
+def test_mlp_gradient_matches_oracle(n):
+    theta, X, t = _draw(n, 100 + n)
+    g = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    B().mlp_gradient(dev(theta), dev(X), dev(t), g, loss)
+    torch.cuda.synchronize()
+    got = g.cpu().numpy().astype(np.float64)
+    want = mlp.grad(theta, X, t, bf16)
+    y, _ = mlp.forward(theta, X, bf16)
+    assert abs(loss.item() - np.mean((y - t) ** 2)) <= 1e-4 * np.mean((y - t) ** 2)
+    off = 0
+    for name, shape in mlp.SIZES:
+        k = int(np.prod(shape))
+        a, b = got[off:off + k], want[off:off + k]
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-7, name
+        off += k
+    exact = mlp.grad(theta, X, t)
+    assert np.dot(got, exact) >= 0.999 * np.linalg.norm(got) * np.linalg.norm(exact)
+
+
+def test_mlp_adam_steps():
+    """Step 1 from zero moments is theta - lr g / (|g| + eps); step 2 by the update rule."""
+    rng = np.random.default_rng(4)
+    theta = f32(rng.standard_normal(mlp.NPARAM))
+    g1 = f32(rng.standard_normal(mlp.NPARAM))
+    g2 = f32(rng.standard_normal(mlp.NPARAM))
+    th, m, v = dev(theta), torch.zeros(mlp.NPARAM, device="cuda"), torch.zeros(
+        mlp.NPARAM, device="cuda")
+    lr = 1e-2
+    B().mlp_adam(th, dev(g1), m, v, 1, lr)
+    torch.cuda.synchronize()
+    want1 = theta - lr * g1 / (np.abs(g1) + 1e-8)
+    assert np.abs(th.cpu().numpy() - want1).max() <= 1e-6 * (1 + np.abs(want1).max())
+    B().mlp_adam(th, dev(g2), m, v, 2, lr)
+    torch.cuda.synchronize()
+    m2 = 0.9 * 0.1 * g1 + 0.1 * g2
+    v2 = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2
+    want2 = want1 - lr * (m2 / (1 - 0.9 ** 2)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-8)
+    assert np.abs(th.cpu().numpy() - want2).max() <= 1e-5 * (1 + np.abs(want2).max())
+
+
+def test_mlp_training_reduces_the_loss():
+    rng = np.random.default_rng(8)
+    X = f32(rng.standard_normal((640, mlp.NI)))
+    t = f32(np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2])
+    th = dev(mlp.init(2))
+    g = torch.zeros(mlp.NPARAM, device="cuda")
+    m, v = torch.zeros_like(g), torch.zeros_like(g)
+    loss = torch.zeros(1, device="cuda")
+    Xd, td = dev(X), dev(t)
+    B().mlp_gradient(th, Xd, td, g, loss)
+    first = loss.item()
+    for step in range(1, 301):
+        B().mlp_gradient(th, Xd, td, g, loss)
+        B().mlp_adam(th, g, m, v, step, 3e-3)
+    B().mlp_gradient(th, Xd, td, g, loss)
+    torch.cuda.synchronize()
+    assert loss.item() < first / 5
+    # the trained parameters evaluate the same in the oracle (rounded operands)
+    y = torch.zeros(len(t), device="cuda")
+    B().mlp_forward(th, Xd, y)
+    ref, _ = mlp.forward(th.cpu().numpy().astype(np.float64), X, bf16)
+    assert abs(np.mean((ref - t) ** 2) - loss.item()) <= 0.05 * loss.item()
+
+
+PROBLEMS = {
+    "laplace": lambda: (fp.vector_laplace_problem(4, seed=0), False),
+    "elasticity": lambda: (fp.elasticity_problem(6, seed=2), False),
+    "mixed": lambda: (fp.mixed_elasticity_family(4, [0.499], seed=3)[0], True),
+    "stokes": lambda: (fp.stokes_lid_problem(4), True),
+}
+
+
+@pytest.mark.parametrize("kind", sorted(PROBLEMS))
+def test_features_match_oracle(kind):
+    prob, saddle = PROBLEMS[kind]()
+    h = B().setup_problem(prob, B().default_options())
+    got = h.features()
+    want = features.features(amg.build_hierarchy(prob), saddle)
+    assert np.abs(got - want).max() <= 1e-10, (got, want)
+    h.free()
+
+
+@pytest.mark.parametrize("kind,w", [("elasticity", (1.2, 1.4, 1.0)),
+                                    ("laplace", (0.7, 1.8, 1.0)),
+                                    ("mixed", (0.8, 1.3, 2.0))])
+def test_weighted_preconditioner_matches_oracle(kind, w):
+    prob, saddle = PROBLEMS[kind]()
+    h = B().setup_problem(prob, B().default_options())
+    h.set_weights(*w)
+    wl = h.weights()
+    assert np.array_equal(wl, np.tile([w[0], w[1], w[2], 1.0], (h.n_levels, 1)))
+    o = amg.Options(smoother="sgs" if saddle else "gs", ws=w[0], wc=w[1], wp=w[2])
+    oh = amg.build_hierarchy(prob, o)
+    r = np.random.default_rng(3).standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(torch.from_numpy(r).cuda(), z)
+    want = amg.precondition(oh, r)
+    assert np.linalg.norm(z.cpu().numpy() - want) <= 1e-10 * np.linalg.norm(want)
+    h.free()
+
+
+def _linear_in_ws(c):
+    """A network whose output is c * ws (input 13): argmin at the grid's smallest
+    ws for c > 0, first wc and wp on ties."""
+    p = {k: np.zeros(s) for k, s in mlp.SIZES}
+    p["W1"][0, 13] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0] = c
+    return mlp.pack(p).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["elasticity", "mixed"])
+def test_learn_weights_decision_and_fallback(kind):
+    prob, saddle = PROBLEMS[kind]()
+    h = B().setup_problem(prob, B().default_options(precision=1))
+    res = h.learn_weights(_linear_in_ws(1.0))
+    Bm = B()
+    assert res.n_candidates == Bm.GRID[0] * Bm.GRID[1] * (Bm.GRID[2] if saddle else 1)
+    assert abs(res.predicted - bf16(Bm.WS_RANGE[0])) <= 1e-6    # the input is multiplied in BF16
+    chosen = [Bm.WS_RANGE[0], Bm.WC_RANGE[0], 2.0 ** Bm.WP_LOG2_RANGE[0] if saddle else 1.0]
+    assert 0.0 < res.rho_plain < 1.0 and res.rho_learned > 0.0
+    fell = res.rho_learned >= res.rho_plain
+    assert res.fell_back == int(fell)
+    want = [1.0, 1.0, 1.0] if fell else chosen
+    assert np.allclose(list(res.weights), want, rtol=0, atol=1e-12)
+    assert np.allclose(h.weights()[:, :3], np.tile(want, (h.n_levels, 1)), rtol=0, atol=1e-12)
+    # solves use the weights in place; plain weights give the plain iteration count
+    b = torch.from_numpy(prob.rhs()).cuda()
+    x = torch.zeros_like(b)
+    st = h.solve(b, x, 1e-8, device_ptrs=True)
+    assert st.converged
+    h.free()
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "..",
+                                     "paper_1503_01287_gb300", "weights", "mlp_theta.npy")
+
+
+def test_trained_network_gain_over_plain():
+    """Held-out problems of the training distribution (seeds outside the training
+    range): the plain solve and the solve with the weights amg_learn_weights picks
+    with the trained network.  The measured fallback may cost at most a couple of
+    iterations against plain on any problem; the gain is what remains."""
+    import os
+    if not os.path.exists(WEIGHTS):
+        pytest.skip("no trained network in the package")
+    from paper_1503_01287_gb300 import train_weights as tw
+    theta = np.load(WEIGHTS)
+    rows = []
+    for i in range(8):
+        spec = tw.problem_spec(i, seed0=900_000)
+        spec["n"] = min(spec["n"], 12)
+        prob = tw.make_problem(spec)
+        h = B().setup_problem(prob, B().default_options(precision=1, gmres_restart=tw.RESTART,
+                                                        max_iterations=tw.MAXIT))
+        b = torch.from_numpy(prob.rhs()).cuda()
+        x = torch.zeros_like(b)
+        plain = h.solve(b, x, 1e-8, device_ptrs=True)
+        res = h.learn_weights(theta)
+        learned = h.solve(b, x, 1e-8, device_ptrs=True)
+        assert plain.converged and learned.converged
+        rows.append((spec["kind"], plain.iterations, learned.iterations, res.fell_back,
+                     tuple(round(w, 3) for w in res.weights)))
+        h.free()
+    print("\nkind, plain iterations, learned iterations, fell back, weights")
+    for r in rows:
+        print(*r)
+    for kind, ip, il, _, _ in rows:
+        assert il <= ip + 2, (kind, ip, il)
+    assert sum(r[2] for r in rows) <= sum(r[1] for r in rows)
