@@ -300,6 +300,8 @@ def build_hierarchy(prob, opts: Options | None = None) -> Hierarchy:
             sd.finish_saddle_level(lv, h, last)
     if saddle:
         h.coarse_factor = sd.factor_coarsest(h)
+        if opts.smoother == "bs":
+            sd.bs_setup(h)
     else:
         h.coarse_factor = ("cplu", complete_pivot_lu(levels[-1].A.toarray()))
     return h

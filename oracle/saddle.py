@@ -12,6 +12,16 @@ System of Eq. (mixedeqn): K = [A B^T; B -C], unknowns [u; p].
                The identity of Eq. (uzsm) is read as S_D = diag(C + B M_A^{-1} B^T)
                (M_A = 2 D, D the 3x3-block diagonal of A) so that omega is
                independent of the scaling of the equations.
+  smoother     Braess-Sarazin type, Eqs. (bssm) / (bssmpre) (Options.smoother = "bs"):
+               one step is x += K^{-1} (b - K x) with
+                   K^ = [A^  B^T; B  B A^{-1} B^T - S^],  A^ = 2 diag(A) (scalar diagonal)
+               and S^{-1} one V(1,1)-cycle of the graph AMG on the scalar matrix
+               S = C + B A^{-1} B^T (the "C + B A^{-1} B" of Sec. 3.3.2 read with the
+               transpose): coarsened on the P1 graph, i.e. through the same pressure
+               prolongations H as the saddle hierarchy, S_{k+1} = H^T S_k H, damped
+               scalar Jacobi (0.5) as its smoother and a direct solve on the coarsest
+               pressure level.  Solving K^ [du; dp] = [r_u; r_p] gives
+                   w = A^{-1} r_u,  dp = S^{-1} (B w - r_p),  du = w - A^{-1} B^T dp.
   coarsest     the same rank-revealing complete-pivoting LU as the SPD case
                (see amg.complete_pivot_lu); it also covers the singular Galerkin
                Stokes matrices (constant pressure and other coarse null modes).
@@ -84,6 +94,59 @@ def finish_saddle_level(lv, h, last):
         lv.extra["schur_diag"] = schur_diagonal(lv, h.opts.omega)
 
 
+BS_JACOBI = 0.5     # damping of the scalar Jacobi smoother of the S-cycle
+
+
+def bs_setup(h):
+    """Per non-coarsest level l: A^{-1} = 1 / (2 diag A) and the S hierarchy
+    S_l, H_l^T S_l H_l, ... down to the coarsest pressure level (its last matrix
+    factorised by the complete-pivoting LU)."""
+    L = len(h.levels) - 1
+    for l in range(L):
+        lv = h.levels[l]
+        ahat_inv = 0.5 / lv.A.diagonal()
+        S = (lv.C + lv.B @ sp.diags(ahat_inv) @ lv.B.T).tocsr()
+        mats = [S]
+        for k in range(l, L):
+            Hk = h.levels[k].H
+            mats.append((Hk.T @ mats[-1] @ Hk).tocsr())
+        lv.extra["bs"] = {"ahat_inv": ahat_inv, "S": mats,
+                          "S_dinv": [np.divide(1.0, m.diagonal(),
+                                               out=np.zeros(m.shape[0]),
+                                               where=m.diagonal() != 0.0) for m in mats],
+                          "coarse": amg.complete_pivot_lu(mats[-1].toarray())}
+
+
+def s_cycle(h, l, rhs):
+    """One V(1,1)-cycle of the S hierarchy of level l from a zero initial guess."""
+    bs = h.levels[l].extra["bs"]
+    mats, dinv = bs["S"], bs["S_dinv"]
+
+    def rec(k, b):
+        if k == len(mats) - 1:
+            return amg.complete_pivot_solve(bs["coarse"], b)
+        S = mats[k]
+        x = BS_JACOBI * dinv[k] * b
+        Hk = h.levels[l + k].H
+        xc = rec(k + 1, Hk.T @ (b - S @ x))
+        x = x + Hk @ xc
+        return x + BS_JACOBI * dinv[k] * (b - S @ x)
+    return rec(0, rhs)
+
+
+def smooth_bs(h, l, x, b):
+    """One Braess-Sarazin step, Eq. (bssm) with K^ of Eq. (bssmpre)."""
+    lv = h.levels[l]
+    bs = lv.extra["bs"]
+    nu = 3 * lv.n
+    r = b - apply_K(lv, x)
+    ru, rp = r[:nu], r[nu:]
+    w = bs["ahat_inv"] * ru
+    dp = s_cycle(h, l, lv.B @ w - rp)
+    du = w - bs["ahat_inv"] * (lv.B.T @ dp)
+    return x + np.concatenate([du, dp])
+
+
 def apply_K(lv, v):
     nu = 3 * lv.n
     u, p = v[:nu], v[nu:]
@@ -101,9 +164,12 @@ def prolong(lv, xc):
 
 
 def smooth(h, l, x, b, post):
-    """Segregated Gauss-Seidel, Eq. (uzsm) with M_A = damped block Jacobi."""
+    """Segregated Gauss-Seidel, Eq. (uzsm) with M_A = damped block Jacobi, or the
+    Braess-Sarazin step (Options.smoother = "bs")."""
     lv = h.levels[l]
     o = h.opts
+    if o.smoother == "bs":
+        return smooth_bs(h, l, x, b)
     nu = 3 * lv.n
     u, p = x[:nu].copy(), x[nu:].copy()
     f, g = b[:nu], b[nu:]
