@@ -62,7 +62,14 @@ enum amg_node_tag {
 enum amg_smoother {
   AMG_SMOOTHER_GS = 0,      /* symmetric multicolour 3x3-block Gauss-Seidel     */
   AMG_SMOOTHER_JACOBI = 1,  /* damped 3x3-block Jacobi (omega, default 0.5)     */
-  AMG_SMOOTHER_SGS = 2      /* segregated Gauss-Seidel for saddle systems       */
+  AMG_SMOOTHER_SGS = 2,     /* segregated Gauss-Seidel for saddle systems       */
+  AMG_SMOOTHER_BS = 3       /* Braess-Sarazin type for saddle systems, Eqs.
+                               (bssm) / (bssmpre): x += K^{-1} (b - K x) with
+                               K^ = [A^ B^T; B B A^{-1} B^T - S^], A^ = 2 diag(A),
+                               S^{-1} one V(1,1)-cycle (damped scalar Jacobi 0.5)
+                               of the graph AMG on S = C + B A^{-1} B^T through
+                               the pressure prolongations H, direct solve on the
+                               coarsest pressure level                          */
 };
 
 enum amg_precision {
@@ -189,8 +196,13 @@ enum amg_level_item {
   AMG_Q_H_ROWPTR = 17,
   AMG_Q_H_COL = 18,
   AMG_Q_H_VAL = 19,
-  AMG_Q_COARSE_INV = 20 /* double [m*m] generalised inverse of the coarsest K,
+  AMG_Q_COARSE_INV = 20, /* double [m*m] generalised inverse of the coarsest K,
                            m = 3*n_nodes + n_pres (coarsest level only)         */
+  AMG_Q_S_ROWPTR = 21,  /* int32 [n_pres+1] Braess-Sarazin S = C + B A^{-1} B^T
+                           of the level (non-coarsest saddle levels, smoother
+                           AMG_SMOOTHER_BS); its nnz is S_ROWPTR[n_pres]        */
+  AMG_Q_S_COL = 22,
+  AMG_Q_S_VAL = 23      /* double [nnz]                                         */
 };
 
 typedef struct amg_handle amg_handle;

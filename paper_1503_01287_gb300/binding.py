@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libamgp2.so")
 
 # enums (include/amgp2.h)
 AMG_VECTOR_LAPLACE, AMG_ELASTICITY, AMG_MIXED_ELASTICITY, AMG_STOKES = 0, 1, 2, 3
-AMG_SMOOTHER_GS, AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SGS = 0, 1, 2
+AMG_SMOOTHER_GS, AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SGS, AMG_SMOOTHER_BS = 0, 1, 2, 3
 AMG_FP64, AMG_FP32 = 0, 1
 AMG_KRYLOV_AUTO, AMG_KRYLOV_PCG, AMG_KRYLOV_FCG, AMG_KRYLOV_FGMRES, AMG_KRYLOV_NONE = 0, 1, 2, 3, 4
 AMG_OK, AMG_NOT_CONVERGED = 0, 1
@@ -31,6 +31,7 @@ ITEMS = {
     "b_val": (12, np.float64), "c_rowptr": (13, np.int32), "c_col": (14, np.int32),
     "c_val": (15, np.float64), "pcf_state": (16, np.int32), "h_rowptr": (17, np.int32),
     "h_col": (18, np.int32), "h_val": (19, np.float64), "coarse_inv": (20, np.float64),
+    "s_rowptr": (21, np.int32), "s_col": (22, np.int32), "s_val": (23, np.float64),
 }
 
 KINDS = {"laplace": AMG_VECTOR_LAPLACE, "elasticity": AMG_ELASTICITY,
@@ -298,7 +299,10 @@ class Handle:
             "c_val": info.c_nnz, "pcf_state": info.n_pres, "h_rowptr": info.n_pres + 1,
             "h_col": info.h_nnz, "h_val": info.h_nnz,
             "coarse_inv": (3 * info.n_nodes + info.n_pres) ** 2,
+            "s_rowptr": info.n_pres + 1,
         }
+        if item in ("s_col", "s_val"):
+            sizes[item] = int(self.level_array(level, "s_rowptr")[-1])
         out = np.empty(int(sizes[item]), dtype=dt)
         _check(load_library().amg_level_copy(self.h, level, code, out.ctypes.data, out.nbytes),
                self.h)

@@ -57,6 +57,19 @@ struct DBuf {
 
 // ------------------------------------------------------------------------ hierarchy
 
+// One level of the scalar hierarchy of S = C + B A^{-1} B^T that the Braess-Sarazin
+// smoother of a saddle level cycles on (S_0 on the saddle level's pressure
+// unknowns, S_{k+1} = H^T S_k H through the pressure prolongations below it).
+struct SLevel {
+  int n = 0;            // pressure unknowns
+  int64_t nnz = 0;
+  DBuf<int> rowptr, col;
+  DBuf<double> val, dinv;   // dinv: 1 / S_kk (0 where S_kk = 0)
+  DBuf<float> val32, dinv32;
+  DBuf<double> x64, b64, r64;
+  DBuf<float> x32, b32, r32;
+};
+
 // One level of the hierarchy.  A is kept as 9 value planes (plane e holds entry
 // (e/3, e%3) of every block), so that consecutive threads reading consecutive
 // blocks read consecutive addresses; the column indices are shared by both
@@ -116,6 +129,13 @@ struct Level {
   DBuf<double> schur;          // sGS scaling S_D (np)
   DBuf<float> schur32;
   DBuf<int> pstate, pcid;
+  // Braess-Sarazin smoother: 1 / (2 diag A) in the padded layout, and the S
+  // hierarchy with the generalised inverse of its coarsest matrix
+  DBuf<double> ahinv;
+  DBuf<float> ahinv32;
+  std::vector<std::unique_ptr<SLevel>> S;
+  DBuf<double> s_coarse_inv;
+  int s_coarse_m = 0;
   int64_t h_nnz = 0;
   DBuf<int> h_rowptr, h_col, ht_rowptr, ht_col;
   DBuf<double> h_val, ht_val;

@@ -101,10 +101,11 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
     if (opt) h->opt = *opt;
     else amg_default_options(&h->opt);
     if (h->opt.smoother < 0) h->opt.smoother = saddle ? AMG_SMOOTHER_SGS : AMG_SMOOTHER_GS;
-    if (saddle && h->opt.smoother != AMG_SMOOTHER_SGS)
-      fail(AMG_ERR_UNSUPPORTED, "saddle kinds use the segregated Gauss-Seidel smoother");
-    if (!saddle && h->opt.smoother == AMG_SMOOTHER_SGS)
-      fail(AMG_ERR_INVALID, "the segregated smoother needs a saddle kind");
+    if (saddle && h->opt.smoother != AMG_SMOOTHER_SGS && h->opt.smoother != AMG_SMOOTHER_BS)
+      fail(AMG_ERR_UNSUPPORTED,
+           "saddle kinds use the segregated Gauss-Seidel or the Braess-Sarazin smoother");
+    if (!saddle && (h->opt.smoother == AMG_SMOOTHER_SGS || h->opt.smoother == AMG_SMOOTHER_BS))
+      fail(AMG_ERR_INVALID, "the segregated and Braess-Sarazin smoothers need a saddle kind");
     if (h->opt.precision != AMG_FP64 && h->opt.precision != AMG_FP32)
       fail(AMG_ERR_INVALID, "unknown precision");
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
@@ -372,6 +373,16 @@ int amg_level_copy(const amg_handle* hc, int32_t level, int32_t item, void* dst,
       case AMG_Q_H_VAL:
         if (!h->saddle || last) fail(AMG_ERR_INVALID, "no H");
         copy_out(h, lv.h_val, lv.h_nnz * D, dst, cap); break;
+      case AMG_Q_S_ROWPTR:
+      case AMG_Q_S_COL:
+      case AMG_Q_S_VAL: {
+        if (lv.S.empty()) fail(AMG_ERR_INVALID, "level has no Braess-Sarazin S matrix");
+        const SLevel& q = *lv.S[0];
+        if (item == AMG_Q_S_ROWPTR) copy_out(h, q.rowptr, (q.n + 1) * I, dst, cap);
+        else if (item == AMG_Q_S_COL) copy_out(h, q.col, q.nnz * I, dst, cap);
+        else copy_out(h, q.val, q.nnz * D, dst, cap);
+        break;
+      }
       case AMG_Q_COARSE_INV:
         if (!last) fail(AMG_ERR_INVALID, "only the coarsest level has a factorisation");
         copy_out(h, h->coarse_inv, (size_t)h->coarse_m * h->coarse_m * D, dst, cap); break;

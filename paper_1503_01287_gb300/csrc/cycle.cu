@@ -285,7 +285,8 @@ __device__ __forceinline__ void bt_add_body(int n, const int* __restrict__ row,
 }
 
 // MODE 0: yp = B u - C p;  MODE 1: yp = g - B u + C p (residual);
-// MODE 2: yp = p + omega (B u - C p - g) / S_D (sGS pressure step)
+// MODE 2: yp = p + omega (B u - C p - g) / S_D (sGS pressure step);
+// MODE 3: yp = B u - g (Braess-Sarazin: g holds the pressure residual)
 template <typename T, int MODE, bool COH>
 __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
                                            const int* __restrict__ bcol,
@@ -306,6 +307,10 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
       s = fma(bval[bnnz + q], u1, s);
       s = fma(bval[2 * bnnz + q], u2, s);
     }
+    if (MODE == 3) {               // Braess-Sarazin right-hand side B w - r_p
+      yp[k] = s - VL<COH>::one(g + k);
+      continue;
+    }
     T cp = T(0);
     for (int q = crow[k]; q < crow[k + 1]; ++q) cp = fma(cval[q], VL<COH>::one(p + ccol[q]), cp);
     if (MODE == 0) {
@@ -320,11 +325,40 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
   }
 }
 
+// Scalar CSR rows of an S-hierarchy matrix (Braess-Sarazin smoother):
+// MODE 0: y = b - S x;  MODE 1: y = x + omega d (b - S x) (damped Jacobi, d = 1/S_kk)
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void srows_body(int n, const int* __restrict__ rowptr,
+                                           const int* __restrict__ col,
+                                           const T* __restrict__ val, const T* x, const T* b,
+                                           const T* __restrict__ d, T omega, T* y, int tid,
+                                           int nthr) {
+  for (int k = tid; k < n; k += nthr) {
+    T acc = T(0);
+    for (int q = rowptr[k]; q < rowptr[k + 1]; ++q)
+      acc = fma(val[q], VL<COH>::one(x + col[q]), acc);
+    const T r = VL<COH>::one(b + k) - acc;
+    y[k] = MODE == 0 ? r : VL<COH>::one(x + k) + omega * d[k] * r;
+  }
+}
+
+// Element-wise: MODE 0: y = omega d x;  MODE 1: y += x;  MODE 2: y += x - d b
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void vec_body(int64_t n, const T* __restrict__ d, const T* x,
+                                         const T* b, T omega, T* y, int tid, int nthr) {
+  for (int64_t k = tid; k < n; k += nthr) {
+    const T xv = VL<COH>::one(x + k);
+    if (MODE == 0) y[k] = omega * d[k] * xv;
+    else if (MODE == 1) y[k] = VL<COH>::one(y + k) + xv;
+    else y[k] = VL<COH>::one(y + k) + xv - d[k] * VL<COH>::one(b + k);
+  }
+}
+
 // ------------------------------------------------------------------- phases
 
 enum PhaseType : int {
   PH_ZERO = 0, PH_COPY, PH_ROWS, PH_RESTRICT, PH_PROLONG, PH_RESTRICT1, PH_PROLONG1,
-  PH_COARSE, PH_BT_ADD, PH_PROWS
+  PH_COARSE, PH_BT_ADD, PH_PROWS, PH_SROWS, PH_VEC
 };
 
 // One operation of the cycle with its operands (a plain record, copied to the
@@ -419,10 +453,30 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
                          P.wt, tid, nthr)
       if (P.mode == 0) AMG_PROWS(0);
       else if (P.mode == 1) AMG_PROWS(1);
-      else AMG_PROWS(2);
+      else if (P.mode == 2) AMG_PROWS(2);
+      else AMG_PROWS(3);
 #undef AMG_PROWS
       break;
     }
+    case PH_SROWS:
+      if (P.mode == 0)
+        srows_body<T, 0, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x,
+                              (const T*)P.b, (const T*)P.dinv, (T)P.omega, (T*)P.y, tid, nthr);
+      else
+        srows_body<T, 1, COH>(P.n, P.rowptr, P.col, (const T*)P.val, (const T*)P.x,
+                              (const T*)P.b, (const T*)P.dinv, (T)P.omega, (T*)P.y, tid, nthr);
+      break;
+    case PH_VEC:
+      if (P.mode == 0)
+        vec_body<T, 0, COH>(P.n, (const T*)P.dinv, (const T*)P.x, (const T*)P.b, (T)P.omega,
+                            (T*)P.y, tid, nthr);
+      else if (P.mode == 1)
+        vec_body<T, 1, COH>(P.n, (const T*)P.dinv, (const T*)P.x, (const T*)P.b, (T)P.omega,
+                            (T*)P.y, tid, nthr);
+      else
+        vec_body<T, 2, COH>(P.n, (const T*)P.dinv, (const T*)P.x, (const T*)P.b, (T)P.omega,
+                            (T*)P.y, tid, nthr);
+      break;
     default:
       break;
   }
@@ -683,6 +737,27 @@ template <> struct LvVec<float> {
   static const float* schur(Level& l) { return l.schur32; }
 };
 
+template <typename T> struct SVec;
+template <> struct SVec<double> {
+  static double* x(SLevel& q) { return q.x64; }
+  static double* b(SLevel& q) { return q.b64; }
+  static double* r(SLevel& q) { return q.r64; }
+  static const double* val(SLevel& q) { return q.val; }
+  static const double* dinv(SLevel& q) { return q.dinv; }
+  static const double* ahinv(Level& l) { return l.ahinv; }
+};
+template <> struct SVec<float> {
+  static float* x(SLevel& q) { return q.x32; }
+  static float* b(SLevel& q) { return q.b32; }
+  static float* r(SLevel& q) { return q.r32; }
+  static const float* val(SLevel& q) { return q.val32; }
+  static const float* dinv(SLevel& q) { return q.dinv32; }
+  static const float* ahinv(Level& l) { return l.ahinv32; }
+};
+
+// damping of the scalar Jacobi smoother of the S-cycle (Braess-Sarazin)
+constexpr double kBsJacobi = 0.5;
+
 // lanes per block row: the autotuned value, else from the average row length
 inline int group_for(const Level& lv) {
   if (lv.group) return lv.group;
@@ -752,6 +827,22 @@ struct Emit {
     P.nnz = lv.b_nnz; P.x = p; P.omega = (double)sign; P.y = y;
     put(P, lv.n);
   }
+  void srows(int mode, SLevel& q, const T* x, const T* b, T* y, T omega) {
+    Phase P = blank(PH_SROWS);
+    P.mode = mode; P.n = q.n; P.rowptr = q.rowptr; P.col = q.col; P.val = SVec<T>::val(q);
+    P.nnz = q.nnz; P.x = x; P.b = b; P.y = y; P.dinv = SVec<T>::dinv(q); P.omega = (double)omega;
+    put(P, q.n);
+  }
+  void vec(int mode, int64_t n, const T* d, const T* x, const T* b, T omega, T* y) {
+    Phase P = blank(PH_VEC);
+    P.mode = mode; P.n = (int)n; P.dinv = d; P.x = x; P.b = b; P.omega = (double)omega; P.y = y;
+    put(P, n);
+  }
+  void coarse_s(Level& lv, const T* b, T* x) {
+    Phase P = blank(PH_COARSE);
+    P.m = lv.s_coarse_m; P.n3 = 0; P.X = lv.s_coarse_inv; P.b = b; P.y = x;
+    put(P, P.m, 32);
+  }
   void prows(int mode, Level& lv, const T* u, const T* p, const T* g, T* yp, T omega) {
     Phase P = blank(PH_PROWS);
     P.mode = mode; P.n = lv.np; P.rowptr = lv.b_rowptr; P.col = lv.b_col;
@@ -786,6 +877,49 @@ void e_residual(Emit<T>& e, Level& lv, const T* x, const T* b, T* r, bool saddle
   }
 }
 
+// One V(1,1)-cycle on the S hierarchy of level l from a zero initial guess
+// (Braess-Sarazin: S^{-1} of Eq. (bssmpre)); the result is left in S_k.x.
+template <typename T>
+void e_scycle(Emit<T>& e, amg_handle* h, int l, int k, const T* rhs) {
+  Level& lv = *h->L[l];
+  SLevel& q = *lv.S[k];
+  T* x = SVec<T>::x(q);
+  if (k + 1 == (int)lv.S.size()) {
+    e.coarse_s(lv, rhs, x);
+    return;
+  }
+  T* r = SVec<T>::r(q);
+  SLevel& nx = *lv.S[k + 1];
+  Level& pk = *h->L[l + k];
+  e.vec(0, q.n, SVec<T>::dinv(q), rhs, nullptr, T(kBsJacobi), x);   // x = w D^{-1} rhs
+  e.srows(0, q, x, rhs, r, T(0));                                    // r = rhs - S x
+  e.transfer(PH_RESTRICT1, nx.n, pk.ht_rowptr, pk.ht_col, LvVec<T>::htval(pk), r, SVec<T>::b(nx));
+  e_scycle<T>(e, h, l, k + 1, SVec<T>::b(nx));
+  e.transfer(PH_PROLONG1, q.n, pk.h_rowptr, pk.h_col, LvVec<T>::hval(pk), SVec<T>::x(nx), x);
+  e.srows(1, q, x, rhs, r, T(kBsJacobi));                            // Jacobi into r
+  e.copy(r, x, q.n);
+}
+
+// One Braess-Sarazin step, Eq. (bssm) with K^ of Eq. (bssmpre):
+// r = b - K x; w = A^{-1} r_u; dp = S^{-1}(B w - r_p); x_u += w - A^{-1} B^T dp; p += dp.
+template <typename T>
+void e_smooth_bs(Emit<T>& e, amg_handle* h, int l, T* x, const T* b) {
+  Level& lv = *h->L[l];
+  const int64_t n4 = 4 * (int64_t)lv.n;
+  T* r = LvVec<T>::r(lv);
+  T* t = LvVec<T>::t(lv);
+  const T* ah = SVec<T>::ahinv(lv);
+  e_residual<T>(e, lv, x, b, r, true);
+  e.vec(0, n4, ah, r, nullptr, T(1), t);                   // t_u = w
+  e.prows(3, lv, t, nullptr, r + n4, t + n4, T(0));         // t_p = B w - r_p
+  e_scycle<T>(e, h, l, 0, t + n4);
+  const T* dp = SVec<T>::x(*lv.S[0]);
+  e.zero(r, n4);
+  e.bt_add(lv, dp, T(1), r);                                // r_u = B^T dp
+  e.vec(2, n4, ah, t, r, T(1), x);                          // x_u += w - A^{-1} B^T dp
+  e.vec(1, lv.np, nullptr, dp, nullptr, T(1), x + n4);      // p += dp
+}
+
 // One smoothing sweep (Sec. 3.3).  SPD: symmetric multicolour block GS (colours
 // ascending before the coarse correction, descending after it) or damped block
 // Jacobi.  Saddle: segregated Gauss-Seidel, Eq. (uzsm).
@@ -797,6 +931,12 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
   const int G = group_for(lv);
   const T* val = LvVec<T>::val(lv);
   const T* dinv = LvVec<T>::dinv(lv);
+  if (h->saddle && h->opt.smoother == AMG_SMOOTHER_BS) {
+    int l = 0;
+    while (h->L[l].get() != &lv) ++l;
+    e_smooth_bs<T>(e, h, l, x, b);
+    return;
+  }
   if (h->saddle) {
     T* t = LvVec<T>::t(lv);
     T* r = LvVec<T>::r(lv);

@@ -1164,6 +1164,188 @@ std::unique_ptr<Level> coarsen(amg_handle* h, Level& lv) {
   return nx;
 }
 
+// ============================================================================ Braess-Sarazin setup
+//
+// S = C + B A^{-1} B^T with A^ = 2 diag(A) (scalar diagonal), formed as one
+// triple product R M R^T with R = [B | I] (pressure rows; columns: the 3n
+// velocity unknowns, then the pressure unknowns) and M = diag(A^{-1}) (+) C.
+
+// 1 / (2 A_ii,cc) in the padded layout (pad entries 0)
+__global__ void k_bs_ahinv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, int64_t nnzb,
+                           double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double d[3] = {0.0, 0.0, 0.0};
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] == i)
+        for (int c = 0; c < 3; ++c) d[c] = val[(4 * c) * nnzb + k];
+    for (int c = 0; c < 3; ++c) out[4 * (int64_t)i + c] = d[c] != 0.0 ? 0.5 / d[c] : 0.0;
+    out[4 * (int64_t)i + 3] = 0.0;
+  }
+}
+
+// rows of R = [B | I]: row k holds 3 entries per block of B row k, then (n3 + k, 1)
+__global__ void k_bs_rrow(int np, const int* __restrict__ brow, int* __restrict__ cnt) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x)
+    cnt[k] = 3 * (brow[k + 1] - brow[k]) + 1;
+}
+
+__global__ void k_bs_rfill(int np, int n3, const int* __restrict__ brow,
+                           const int* __restrict__ bcol, const double* __restrict__ bval,
+                           int64_t bnnz, const int* __restrict__ rrow, int* __restrict__ rcol,
+                           double* __restrict__ rval) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+    int o = rrow[k];
+    for (int q = brow[k]; q < brow[k + 1]; ++q)
+      for (int c = 0; c < 3; ++c) {
+        rcol[o] = 3 * bcol[q] + c;
+        rval[o] = bval[c * bnnz + q];
+        ++o;
+      }
+    rcol[o] = n3 + k;
+    rval[o] = 1.0;
+  }
+}
+
+// rows of M = diag(A^{-1}) (+) C: rows i < n3 hold (i, A^{-1}_i); row n3 + k holds
+// C row k shifted by n3
+__global__ void k_bs_mrow(int n3, int np, const int* __restrict__ crow, int* __restrict__ cnt) {
+  const int m = n3 + np;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    cnt[i] = i < n3 ? 1 : crow[i - n3 + 1] - crow[i - n3];
+}
+
+__global__ void k_bs_mfill(int n3, int np, const double* __restrict__ ahinv,
+                           const int* __restrict__ crow, const int* __restrict__ ccol,
+                           const double* __restrict__ cval, const int* __restrict__ mrow,
+                           int* __restrict__ mcol, double* __restrict__ mval) {
+  const int m = n3 + np;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    int o = mrow[i];
+    if (i < n3) {
+      mcol[o] = i;
+      mval[o] = ahinv[4 * (i / 3) + i % 3];
+    } else {
+      const int k = i - n3;
+      for (int q = crow[k]; q < crow[k + 1]; ++q, ++o) {
+        mcol[o] = n3 + ccol[q];
+        mval[o] = cval[q];
+      }
+    }
+  }
+}
+
+__global__ void k_s_dinv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                         const double* __restrict__ val, double* __restrict__ dinv) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int q = rowptr[k]; q < rowptr[k + 1]; ++q)
+      if (col[q] == k) d = val[q];
+    dinv[k] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+}
+
+__global__ void k_dense_csr(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, double* __restrict__ K) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    for (int q = rowptr[k]; q < rowptr[k + 1]; ++q) K[(int64_t)k * n + col[q]] = val[q];
+}
+
+// The S hierarchy of every non-coarsest saddle level (Braess-Sarazin smoother).
+void bs_setup(amg_handle* h) {
+  cudaStream_t s = h->stream;
+  const bool fp32 = h->opt.precision == AMG_FP32;
+  const int L = (int)h->L.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    Level& lv = *h->L[l];
+    const int n3 = 3 * lv.n, np = lv.np;
+    lv.ahinv.alloc(4 * (size_t)std::max(lv.n, 1));
+    k_bs_ahinv<<<grid_for(lv.n), 256, 0, s>>>(lv.n, lv.rowptr, lv.col, lv.val, lv.nnzb, lv.ahinv);
+    AMG_LAUNCH_CHECK();
+    h->launches++;
+    if (fp32) {
+      lv.ahinv32.alloc(4 * (size_t)std::max(lv.n, 1));
+      launch_to_float(lv.ahinv, lv.ahinv32, 4 * (int64_t)lv.n, s, h);
+    }
+    // R = [B | I], M = diag(A^{-1}) (+) C, R^T
+    DBuf<int> cnt, rrow, rcol, mrow, mcol, trow, tcol;
+    DBuf<double> rval, mval, tval;
+    cnt.alloc(std::max(n3 + np, 1) + 1);
+    k_bs_rrow<<<grid_for(np), 256, 0, s>>>(np, lv.b_rowptr, cnt);
+    rrow.alloc(np + 1);
+    const int64_t rnnz = exclusive_scan(cnt, rrow, np, s, h);
+    rcol.alloc(std::max<int64_t>(rnnz, 1));
+    rval.alloc(std::max<int64_t>(rnnz, 1));
+    k_bs_rfill<<<grid_for(np), 256, 0, s>>>(np, n3, lv.b_rowptr, lv.b_col, lv.b_val, lv.b_nnz,
+                                            rrow, rcol, rval);
+    k_bs_mrow<<<grid_for(n3 + np), 256, 0, s>>>(n3, np, lv.c_rowptr, cnt);
+    mrow.alloc(n3 + np + 1);
+    const int64_t mnnz = exclusive_scan(cnt, mrow, n3 + np, s, h);
+    mcol.alloc(std::max<int64_t>(mnnz, 1));
+    mval.alloc(std::max<int64_t>(mnnz, 1));
+    k_bs_mfill<<<grid_for(n3 + np), 256, 0, s>>>(n3, np, lv.ahinv, lv.c_rowptr, lv.c_col,
+                                                lv.c_val, mrow, mcol, mval);
+    AMG_LAUNCH_CHECK();
+    h->launches += 4;
+    transpose(h, np, n3 + np, rrow, rcol, rval, 1, rnnz, trow, tcol, tval);
+    lv.S.clear();
+    auto s0 = std::make_unique<SLevel>();
+    s0->n = np;
+    s0->nnz = galerkin<1>(h, np, np, rrow, rcol, rval, mrow, mcol, mval, mnnz, trow, tcol, tval,
+                          s0->rowptr, s0->col, s0->val);
+    lv.S.push_back(std::move(s0));
+    for (int k = l; k < L; ++k) {
+      Level& pk = *h->L[k];
+      SLevel& cur = *lv.S.back();
+      auto nx = std::make_unique<SLevel>();
+      nx->n = h->L[k + 1]->np;
+      nx->nnz = galerkin<1>(h, nx->n, nx->n, pk.ht_rowptr, pk.ht_col, pk.ht_val, cur.rowptr,
+                            cur.col, cur.val, cur.nnz, pk.h_rowptr, pk.h_col, pk.h_val,
+                            nx->rowptr, nx->col, nx->val);
+      lv.S.push_back(std::move(nx));
+    }
+    for (auto& sp : lv.S) {
+      SLevel& q = *sp;
+      const int n = std::max(q.n, 1);
+      q.dinv.alloc(n);
+      k_s_dinv<<<grid_for(q.n), 256, 0, s>>>(q.n, q.rowptr, q.col, q.val, q.dinv);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+      q.x64.alloc(n); q.b64.alloc(n); q.r64.alloc(n);
+      AMG_CUDA(cudaMemsetAsync(q.x64.p, 0, q.x64.bytes(), s));
+      if (fp32) {
+        q.val32.alloc(std::max<int64_t>(q.nnz, 1));
+        launch_to_float(q.val, q.val32, q.nnz, s, h);
+        q.dinv32.alloc(n);
+        launch_to_float(q.dinv, q.dinv32, q.n, s, h);
+        q.x32.alloc(n); q.b32.alloc(n); q.r32.alloc(n);
+        AMG_CUDA(cudaMemsetAsync(q.x32.p, 0, q.x32.bytes(), s));
+      }
+    }
+    // generalised inverse of the coarsest S (complete-pivoting LU, as the coarsest K)
+    SLevel& last = *lv.S.back();
+    const int m = last.n;
+    if (m > 2048) fail(AMG_ERR_UNSUPPORTED, "coarsest S larger than 2048 unknowns");
+    lv.s_coarse_m = m;
+    if (m > 0) {
+      DBuf<double> K, work;
+      K.alloc((size_t)m * m);
+      AMG_CUDA(cudaMemsetAsync(K.p, 0, K.bytes(), s));
+      k_dense_csr<<<grid_for(m), 256, 0, s>>>(m, last.rowptr, last.col, last.val, K);
+      DBuf<int> rp, cp, rank;
+      rp.alloc(m); cp.alloc(m); rank.alloc(1);
+      k_cplu<<<1, 1024, 0, s>>>(m, K, rp, cp, 1e-13, rank);
+      lv.s_coarse_inv.alloc((size_t)m * m);
+      work.alloc((size_t)m * m);
+      k_cplu_inverse<<<m, 256, 0, s>>>(m, K, rp, cp, rank, work, lv.s_coarse_inv);
+      AMG_LAUNCH_CHECK();
+      h->launches += 3;
+      AMG_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  AMG_CUDA(cudaStreamSynchronize(s));
+}
+
 void factor_coarsest(amg_handle* h) {
   Level& lv = *h->L.back();
   cudaStream_t s = h->stream;
@@ -1240,6 +1422,7 @@ void build_hierarchy(amg_handle* h, const amg_matrix* m, const int32_t* tags) {
   launch_fill(h->wts, 1.0, 4 * (int64_t)h->L.size(), s, h);
   for (size_t l = 0; l < h->L.size(); ++l) h->L[l]->wt = h->wts.p + 4 * l;
   factor_coarsest(h);
+  if (h->saddle && h->opt.smoother == AMG_SMOOTHER_BS) bs_setup(h);
   autotune_levels(h);
   AMG_CUDA(cudaStreamSynchronize(s));
 }
