@@ -290,7 +290,9 @@ def run_gpu(args, rank, world):
         "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
                    "colours": stats[-1]["level_colours"],
-                   "lanes_per_row": stats[-1]["level_group"]},
+                   "lanes_per_row": stats[-1]["level_group"],
+                   "cluster_from": stats[-1]["cluster_from"],
+                   "cycle_kernel": stats[-1]["cycle_kernel"]},
         "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                        "iterations": stats_plain[-1]["iterations"]},
         "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": "DOF/s",

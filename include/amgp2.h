@@ -160,6 +160,9 @@ typedef struct amg_stats {
   int64_t level_nnzb[AMG_MAX_LEVELS];
   int32_t level_colours[AMG_MAX_LEVELS];
   int32_t level_group[AMG_MAX_LEVELS];  /* lanes per block row chosen at setup       */
+  int32_t cluster_from;     /* cycle variant in use: first level of the cluster
+                               sub-cycle (0: none)                              */
+  int32_t cycle_kernel;     /* 1: one launch per operation, 2: persistent cycle */
 } amg_stats;
 
 typedef struct amg_level_info {

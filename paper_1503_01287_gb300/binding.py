@@ -81,7 +81,8 @@ class AmgStats(C.Structure):
                 ("level_pres", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_nnzb", C.c_int64 * AMG_MAX_LEVELS),
                 ("level_colours", C.c_int32 * AMG_MAX_LEVELS),
-                ("level_group", C.c_int32 * AMG_MAX_LEVELS)]
+                ("level_group", C.c_int32 * AMG_MAX_LEVELS),
+                ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -93,7 +94,8 @@ class AmgStats(C.Structure):
                 "level_pres": list(self.level_pres[:nl]),
                 "level_nnzb": list(self.level_nnzb[:nl]),
                 "level_colours": list(self.level_colours[:nl]),
-                "level_group": list(self.level_group[:nl])}
+                "level_group": list(self.level_group[:nl]),
+                "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel}
 
 
 class AmgLearned(C.Structure):

@@ -175,6 +175,8 @@ int amg_set_pressure_weights(amg_handle* h, const double* w, int32_t device_ptrs
 static void fill_stats(amg_handle* h, amg_stats* st) {
   st->n_levels = (int)h->L.size();
   st->setup_ms = h->setup_ms;
+  st->cluster_from = h->sub_from;
+  st->cycle_kernel = h->use_full ? 2 : 1;
   for (int l = 0; l < AMG_MAX_LEVELS; ++l) {
     if (l < (int)h->L.size()) {
       st->level_nodes[l] = h->L[l]->n;
