@@ -252,6 +252,34 @@ def run_gpu(args, rank, world):
         breakdown.append(row)
     precond_ms, precond_launches = chosen.time_level_op("precond", 0, B.AMG_FP32, reps=10,
                                                         warmup=2)
+    # iteration counts versus mesh size (the paper's mesh-independence study), after the
+    # timed region: the same workload family at 4^3, 8^3, 16^3 and the timed size
+    mesh = None
+    if rank == 0 and not args.no_mesh:
+        mesh = {"n": [], "dofs": [], "chosen_iterations": [], "chosen_ms": [],
+                "plain_fp64_iterations": [], "plain_fp64_ms": [],
+                "paper_pcg_gs11_iterations_L1_L4": [40, 43, 43, 42],
+                "paper_note": "AMG-PCG, V-cycle, sequential GS-1-1, elasticity at 4^3..32^3 "
+                              "(Sec. 4.3 table); the paper's boundary data differ"}
+        for n in [m for m in (4, 8, 16) if m < args.n]:
+            p = elasticity_problem(n, seed=1)
+            bb = torch.from_numpy(p.rhs()).cuda()
+            xx = torch.zeros_like(bb)
+            mesh["n"].append(n)
+            mesh["dofs"].append(p.n_dof)
+            for key, prec in (("chosen", B.AMG_FP32), ("plain_fp64", B.AMG_FP64)):
+                hh = B.setup_problem(p, B.default_options(precision=prec), stream=sptr)
+                hh.solve(bb, xx, TOL, device_ptrs=True)
+                st = hh.solve(bb, xx, TOL, device_ptrs=True)
+                mesh[key + "_iterations"].append(st.iterations)
+                mesh[key + "_ms"].append(st.solve_ms)
+                hh.free()
+        mesh["n"].append(args.n)
+        mesh["dofs"].append(ndof)
+        mesh["chosen_iterations"].append(stats[-1]["iterations"])
+        mesh["chosen_ms"].append(ms)
+        mesh["plain_fp64_iterations"].append(stats_plain[-1]["iterations"])
+        mesh["plain_fp64_ms"].append(ms_plain)
     peak, peak_kind = peaks()
     achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
     # DRAM bytes of one level-0 sweep from the committed ncu summary of this kernel
@@ -288,6 +316,7 @@ def run_gpu(args, rank, world):
         "iterations": stats[-1]["iterations"],
         "true_rel_residual": true_rel,
         "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
+        "iterations_vs_mesh": mesh,
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
                    "colours": stats[-1]["level_colours"],
                    "lanes_per_row": stats[-1]["level_group"],
@@ -404,6 +433,8 @@ def main():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--ref-n", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mesh", action="store_true",
+                    help="skip the iteration-count-versus-mesh-size study")
     ap.add_argument("--workload", default="elasticity", choices=["elasticity", "batched"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rhs", type=int, default=16)
