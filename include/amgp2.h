@@ -74,7 +74,12 @@ enum amg_smoother {
 
 enum amg_precision {
   AMG_FP64 = 0,             /* cycle in FP64                                    */
-  AMG_FP32 = 1              /* cycle in FP32, outer Krylov and coarsest in FP64 */
+  AMG_FP32 = 1,             /* cycle in FP32, outer Krylov and coarsest in FP64 */
+  AMG_FP32_BF16 = 2         /* AMG_FP32 with the operator values of levels >= 1
+                               stored in BF16 (rounded to nearest even from the
+                               FP64 Galerkin values, converted to FP32 in the
+                               kernels); level 0, D^{-1}, P and the pressure
+                               parts stay FP32                                  */
 };
 
 enum amg_krylov {

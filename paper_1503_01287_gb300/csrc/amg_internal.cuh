@@ -81,6 +81,8 @@ struct Level {
   DBuf<int> rowptr, col, tags;
   DBuf<double> val;     // 9 * nnzb, plane-major
   DBuf<float> val32;     // FP32 copy of the kernel layout (k_val)
+  DBuf<unsigned short> val16;   // BF16 bit patterns of the kernel layout (levels >= 1,
+                                // AMG_FP32_BF16 only)
   DBuf<double> dinv;    // 12 * n: per node 3 padded rows (4 values) of the inverse
   DBuf<float> dinv32;
   int ncolours = 0;
@@ -208,6 +210,7 @@ struct amg_handle {
   amgp2::DBuf<double> wts;          // 4 learned weights per level (see Level::wt)
   double plain_rho = 0.0;           // convergence factor of the plain method (fallback)
   bool learned = false;
+  bool bf16_coarse = false;         // AMG_FP32_BF16: levels >= 1 keep BF16 values
   ~amg_handle();
 };
 

@@ -106,8 +106,13 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
            "saddle kinds use the segregated Gauss-Seidel or the Braess-Sarazin smoother");
     if (!saddle && (h->opt.smoother == AMG_SMOOTHER_SGS || h->opt.smoother == AMG_SMOOTHER_BS))
       fail(AMG_ERR_INVALID, "the segregated and Braess-Sarazin smoothers need a saddle kind");
-    if (h->opt.precision != AMG_FP64 && h->opt.precision != AMG_FP32)
+    if (h->opt.precision != AMG_FP64 && h->opt.precision != AMG_FP32 &&
+        h->opt.precision != AMG_FP32_BF16)
       fail(AMG_ERR_INVALID, "unknown precision");
+    if (h->opt.precision == AMG_FP32_BF16) {   // an FP32 cycle with BF16 coarse values
+      h->bf16_coarse = true;
+      h->opt.precision = AMG_FP32;
+    }
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
         h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1)
       fail(AMG_ERR_INVALID, "option out of range");

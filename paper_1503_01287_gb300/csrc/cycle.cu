@@ -9,8 +9,10 @@
 // thread-block cluster, separated by cluster barriers, so both paths perform the
 // same operations in the same order.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -27,6 +29,19 @@ enum RowMode { kApply = 0, kResid = 1, kGS = 2, kJacobi = 3 };
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Operator values stored as V (T itself, or BF16 for the coarse levels of
+// AMG_FP32_BF16), returned in the arithmetic type T.
+template <typename T, typename V>
+__device__ __forceinline__ T ldcs_v(const V* p) {
+  if constexpr (std::is_same<T, V>::value) return __ldcs(p);
+  else return __bfloat162float(__ldcs(p));
+}
+template <typename T, typename V>
+__device__ __forceinline__ T ldg_v(const V* p) {
+  if constexpr (std::is_same<T, V>::value) return __ldg(p);
+  else return __bfloat162float(__ldg(p));
+}
 
 // Vector loads.  COH = false: read-only path (vectors written by earlier
 // kernels).  COH = true: through L2 only, for vectors written earlier in the
@@ -70,11 +85,11 @@ struct VL<true> {
 //   kJacobi: y_i = x_i + omega D_i^{-1} (b_i - (A x)_i)
 // Stored row g holds the blocks rowptr[g]..rowptr[g+1] of node i = rows[g]
 // (i = g when rows is null).  D^{-1} is stored as 3 padded rows per node.
-template <typename T, int G, int MODE, bool COH>
+template <typename T, int G, int MODE, bool COH, typename V = T>
 __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ rows,
                                           const int* __restrict__ rowptr,
                                           const int* __restrict__ col,
-                                          const T* __restrict__ val, int64_t nnzb, const T* x,
+                                          const V* __restrict__ val, int64_t nnzb, const T* x,
                                           const T* b, T* y, const T* __restrict__ dinv,
                                           T omega, const double* __restrict__ wt, int warp,
                                           int nwarps) {
@@ -102,7 +117,11 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
       // U blocks per lane per step: all column indices of the step are loaded
       // before the gathers that depend on them
       // FP64 keeps fewer blocks in flight per lane (register budget)
-      constexpr int U = sizeof(T) == 8 ? (G >= 16 ? 1 : 2) : (G >= 32 ? 3 : (G >= 16 ? 2 : 4));
+      // (one block per step inside the cluster and persistent kernels, whose one
+      // body holds every row variant within the 128 registers of a 512-thread CTA)
+      constexpr int U = COH ? 1
+                            : (sizeof(T) == 8 ? (G >= 16 ? 1 : 2)
+                                              : (G >= 32 ? 3 : (G >= 16 ? 2 : 4)));
       for (int k0 = a + gl; k0 < e; k0 += U * G) {
         // the matrix is streamed once per pass: evict-first loads keep the
         // gathered vector resident in L2; values do not wait for the columns
@@ -114,7 +133,7 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
           if (k < e) {
             j[u] = __ldcs(col + k);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) v[u][q] = __ldcs(val + q * nnzb + k);
+            for (int q = 0; q < 9; ++q) v[u][q] = ldcs_v<T>(val + q * nnzb + k);
           }
         }
 #pragma unroll
@@ -383,19 +402,20 @@ struct Phase {
   int m, n3;
   double omega;
   const double* wt;       // the level's learned weights (null: plain method)
+  int vbf;                // PH_ROWS: values stored as BF16 (FP32 arithmetic)
 };
 
-template <typename T, bool COH>
-__device__ void dispatch_rows(const Phase& P, int warp, int nwarps) {
-  const T* val = (const T*)P.val;
+template <typename T, bool COH, typename V = T>
+__device__ void dispatch_rows_v(const Phase& P, int warp, int nwarps) {
+  const V* val = (const V*)P.val;
   const T* x = (const T*)P.x;
   const T* b = (const T*)P.b;
   T* y = (T*)P.y;
   const T* d = (const T*)P.dinv;
   const T om = (T)P.omega;
-#define AMG_ROWS_MODE(GG, MM)                                                                \
-  rows_body<T, GG, MM, COH>(P.n, P.rows, P.rowptr, P.col, val, P.nnz, x, b, y, d, om, P.wt, \
-                            warp, nwarps)
+#define AMG_ROWS_MODE(GG, MM)                                                                   \
+  rows_body<T, GG, MM, COH, V>(P.n, P.rows, P.rowptr, P.col, val, P.nnz, x, b, y, d, om, P.wt, \
+                               warp, nwarps)
 #define AMG_ROWS_G(GG)                              \
   switch (P.mode) {                                 \
     case kApply: AMG_ROWS_MODE(GG, kApply); break;  \
@@ -411,6 +431,17 @@ __device__ void dispatch_rows(const Phase& P, int warp, int nwarps) {
   }
 #undef AMG_ROWS_G
 #undef AMG_ROWS_MODE
+}
+
+template <typename T, bool COH>
+__device__ void dispatch_rows(const Phase& P, int warp, int nwarps) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (P.vbf) {
+      dispatch_rows_v<float, COH, __nv_bfloat16>(P, warp, nwarps);
+      return;
+    }
+  }
+  dispatch_rows_v<T, COH, T>(P, warp, nwarps);
 }
 
 template <typename T, bool COH>
@@ -489,11 +520,11 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
 // the update remain.  Neither the previous colour's kernel nor any operation
 // it overlaps writes those operands (it writes x of its own rows only).
 // One group of G lanes per stored row; each lane prefetches up to U blocks.
-template <typename T, int G, int U>
+template <typename T, int G, int U, typename V = T>
 __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict__ rows,
                                                 const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
-                                                const T* __restrict__ val, int64_t nnzb, T* x,
+                                                const V* __restrict__ val, int64_t nnzb, T* x,
                                                 const T* __restrict__ b,
                                                 const T* __restrict__ dinv,
                                                 const double* __restrict__ wt) {
@@ -519,7 +550,7 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
       if (k < e) {
         j[u] = __ldcs(col + k);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) v[u][q] = __ldcs(val + q * nnzb + k);
+        for (int q = 0; q < 9; ++q) v[u][q] = ldcs_v<T>(val + q * nnzb + k);
       }
     }
     if (gl == 0) {
@@ -549,16 +580,16 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
       const int jj = ldg(col + k);
       T x0, x1, x2;
       VL<true>::node(x, jj, x0, x1, x2);
-      const T* vv = val + k;
-      s0 = fma(ldg(vv), x0, s0);
-      s0 = fma(ldg(vv + nnzb), x1, s0);
-      s0 = fma(ldg(vv + 2 * nnzb), x2, s0);
-      s1 = fma(ldg(vv + 3 * nnzb), x0, s1);
-      s1 = fma(ldg(vv + 4 * nnzb), x1, s1);
-      s1 = fma(ldg(vv + 5 * nnzb), x2, s1);
-      s2 = fma(ldg(vv + 6 * nnzb), x0, s2);
-      s2 = fma(ldg(vv + 7 * nnzb), x1, s2);
-      s2 = fma(ldg(vv + 8 * nnzb), x2, s2);
+      const V* vv = val + k;
+      s0 = fma(ldg_v<T>(vv), x0, s0);
+      s0 = fma(ldg_v<T>(vv + nnzb), x1, s0);
+      s0 = fma(ldg_v<T>(vv + 2 * nnzb), x2, s0);
+      s1 = fma(ldg_v<T>(vv + 3 * nnzb), x0, s1);
+      s1 = fma(ldg_v<T>(vv + 4 * nnzb), x1, s1);
+      s1 = fma(ldg_v<T>(vv + 5 * nnzb), x2, s1);
+      s2 = fma(ldg_v<T>(vv + 6 * nnzb), x0, s2);
+      s2 = fma(ldg_v<T>(vv + 7 * nnzb), x1, s2);
+      s2 = fma(ldg_v<T>(vv + 8 * nnzb), x2, s2);
     }
   }
 #pragma unroll
@@ -573,7 +604,7 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
       xi1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2), xi2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
 }
 
-template <typename T, int G>
+template <typename T, int G, typename V = T>
 void launch_gs_pdl(const Phase& P, cudaStream_t s) {
   constexpr int U = (sizeof(T) == 8) ? (G >= 16 ? 2 : 3) : (G >= 16 ? 3 : 4);
   cudaLaunchConfig_t cfg{};
@@ -585,8 +616,8 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U>, P.n, P.rows, P.rowptr, P.col,
-                              (const T*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U, V>, P.n, P.rows, P.rowptr, P.col,
+                              (const V*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
                               (const T*)P.dinv, P.wt));
 }
 
@@ -597,42 +628,53 @@ __global__ void __launch_bounds__(256) k_phase(const Phase P) {
 }
 
 // the block-row operations as their own specialised kernels (the hot path)
-template <typename T, int G, int MODE>
+template <typename T, int G, int MODE, typename V = T>
 __global__ void __launch_bounds__(256) k_rows(const Phase P) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  rows_body<T, G, MODE, false>(P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz,
+  rows_body<T, G, MODE, false, V>(P.n, P.rows, P.rowptr, P.col, (const V*)P.val, P.nnz,
                                (const T*)P.x, (const T*)P.b, (T*)P.y, (const T*)P.dinv,
                                (T)P.omega, P.wt, tid >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 
-template <typename T, int G>
+template <typename T, int G, typename V>
 void launch_rows_mode(const Phase& P, int grid, cudaStream_t s) {
   switch (P.mode) {
-    case kApply: k_rows<T, G, kApply><<<grid, 256, 0, s>>>(P); break;
-    case kResid: k_rows<T, G, kResid><<<grid, 256, 0, s>>>(P); break;
-    case kGS: k_rows<T, G, kGS><<<grid, 256, 0, s>>>(P); break;
-    default: k_rows<T, G, kJacobi><<<grid, 256, 0, s>>>(P); break;
+    case kApply: k_rows<T, G, kApply, V><<<grid, 256, 0, s>>>(P); break;
+    case kResid: k_rows<T, G, kResid, V><<<grid, 256, 0, s>>>(P); break;
+    case kGS: k_rows<T, G, kGS, V><<<grid, 256, 0, s>>>(P); break;
+    default: k_rows<T, G, kJacobi, V><<<grid, 256, 0, s>>>(P); break;
   }
 }
 
-template <typename T>
-void launch_rows(const Phase& P, cudaStream_t s, bool pdl) {
+template <typename T, typename V>
+void launch_rows_v(const Phase& P, cudaStream_t s, bool pdl) {
   if (pdl && P.mode == kGS && P.rows) {
     switch (P.G) {
-      case 4: launch_gs_pdl<T, 4>(P, s); return;
-      case 8: launch_gs_pdl<T, 8>(P, s); return;
-      case 16: launch_gs_pdl<T, 16>(P, s); return;
-      default: launch_gs_pdl<T, 32>(P, s); return;
+      case 4: launch_gs_pdl<T, 4, V>(P, s); return;
+      case 8: launch_gs_pdl<T, 8, V>(P, s); return;
+      case 16: launch_gs_pdl<T, 16, V>(P, s); return;
+      default: launch_gs_pdl<T, 32, V>(P, s); return;
     }
   }
   // one group of G lanes per row: nrows * G threads
   const int grid = (int)(((int64_t)P.n * P.G + 255) / 256);
   switch (P.G) {
-    case 4: launch_rows_mode<T, 4>(P, grid, s); break;
-    case 8: launch_rows_mode<T, 8>(P, grid, s); break;
-    case 16: launch_rows_mode<T, 16>(P, grid, s); break;
-    default: launch_rows_mode<T, 32>(P, grid, s); break;
+    case 4: launch_rows_mode<T, 4, V>(P, grid, s); break;
+    case 8: launch_rows_mode<T, 8, V>(P, grid, s); break;
+    case 16: launch_rows_mode<T, 16, V>(P, grid, s); break;
+    default: launch_rows_mode<T, 32, V>(P, grid, s); break;
   }
+}
+
+template <typename T>
+void launch_rows(const Phase& P, cudaStream_t s, bool pdl) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (P.vbf) {
+      launch_rows_v<float, __nv_bfloat16>(P, s, pdl);
+      return;
+    }
+  }
+  launch_rows_v<T, T>(P, s, pdl);
 }
 
 // The recorded phases of the small coarse levels in one thread-block cluster.
@@ -798,6 +840,10 @@ struct Emit {
     P.mode = mode; P.G = G; P.n = nrows; P.rows = order ? order + first : nullptr;
     P.rowptr = lv.k_rowptr() + first; P.col = lv.k_col();
     P.val = val; P.nnz = lv.nnzb; P.x = x; P.b = b; P.y = y; P.dinv = dinv; P.omega = omega;
+    if (sizeof(T) == 4 && lv.val16.p && (const void*)val == (const void*)lv.val32.p) {
+      P.val = lv.val16.p;   // BF16 storage of this level's values
+      P.vbf = 1;
+    }
     put(P, nrows, G);
   }
   void zero(T* a, int64_t n) {

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
 #include "amg_internal.cuh"
 
 namespace amgp2 {
@@ -133,6 +135,14 @@ __global__ void k_aos3_to_planes(const double* __restrict__ aos, double* __restr
 #pragma unroll
     for (int e = 0; e < 3; ++e) planes[e * nnz + k] = aos[3 * k + e];
   }
+}
+
+// FP64 -> BF16 bit patterns, rounded to nearest even
+__global__ void k_to_bf16(const double* __restrict__ a, unsigned short* __restrict__ b,
+                          int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = __bfloat16_as_ushort(__double2bfloat16(a[k]));
 }
 
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -1088,6 +1098,12 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
   if (fp32) {
     lv.val32.alloc(9 * (size_t)std::max<int64_t>(lv.nnzb, 1));
     launch_to_float(lv.k_val(), lv.val32, 9 * lv.nnzb, s, h);
+    if (h->bf16_coarse && &lv != h->L[0].get() && lv.nnzb > 0) {
+      lv.val16.alloc(9 * (size_t)lv.nnzb);
+      k_to_bf16<<<grid_for(9 * lv.nnzb), 256, 0, s>>>(lv.k_val(), lv.val16, 9 * lv.nnzb);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
     lv.dinv32.alloc(12 * (size_t)std::max(n, 1));
     launch_to_float(lv.dinv, lv.dinv32, 12 * (int64_t)n, s, h);
     if (!coarsest) {
