@@ -370,6 +370,70 @@ def run_profile(args):
         h.free()
 
 
+# iteration counts the paper prints for its Sec. 4.1 setting (levels L1..L4 = 4^3..32^3),
+# quoted as context: tables of the AMG solver and of AMG-preconditioned CG, V- and
+# W-cycles; None where the paper reports no convergence
+PAPER_TABLES = {
+    ("laplace", "amg", 1): {"JA-1-1": [129, 125, 124, 128], "JA-2-2": [65, 65, 65, 66],
+                            "GS-1-1": [43, 46, 47, 47], "GS-2-2": [23, 24, 24, 24]},
+    ("laplace", "amg", 2): {"JA-1-1": [128, 124, 121, 123], "JA-2-2": [65, 64, 63, 64],
+                            "GS-1-1": [43, 46, 47, 47], "GS-2-2": [23, 24, 24, 24]},
+    ("laplace", "pcg", 1): {"JA-1-1": [30, 30, 30, 30], "JA-2-2": [21, 22, 22, 22],
+                            "GS-1-1": [26, 29, 29, 30], "GS-2-2": [17, 19, 19, 19]},
+    ("laplace", "pcg", 2): {"JA-1-1": [30, 30, 30, 29], "JA-2-2": [21, 21, 21, 21],
+                            "GS-1-1": [26, 29, 29, 29], "GS-2-2": [17, 18, 18, 18]},
+    ("elasticity", "amg", 1): {"JA-1-1": [None] * 4, "JA-2-2": [None] * 4,
+                               "GS-1-1": [80, 78, 76, 75], "GS-2-2": [44, 40, 39, 39]},
+    ("elasticity", "amg", 2): {"JA-1-1": [None] * 4, "JA-2-2": [None] * 4,
+                               "GS-1-1": [80, 78, 75, 73], "GS-2-2": [44, 40, 39, 44]},
+    ("elasticity", "pcg", 1): {"JA-1-1": [50, 81, None, None], "JA-2-2": [32, 63, None, None],
+                               "GS-1-1": [40, 43, 43, 42], "GS-2-2": [28, 27, 27, 27]},
+    ("elasticity", "pcg", 2): {"JA-1-1": [47, 80, None, None], "JA-2-2": [32, 62, None, None],
+                               "GS-1-1": [39, 44, 42, 41], "GS-2-2": [28, 27, 27, 26]},
+}
+
+
+def run_replay(args):
+    """The paper's Sec. 4.1 iteration tables replayed on the GPU (plain FP64 cycle):
+    vector Laplacian and elasticity with u = 0 on z = 0 and u = (0,0,1) on z = 1,
+    stand-alone AMG and AMG-PCG, V- and W-cycles, JA-m-m-0.5 and GS-m-m, levels
+    4^3..32^3, relative residual 1e-11, at most 200 iterations.  Our Gauss-Seidel is
+    the multicolour symmetric one, so the GS rows are a comparison, not a parity."""
+    import torch
+    import __graft_entry__ as ge
+    from fem_inputs.problems import paper_setting_problem
+    ge.build()
+    from paper_1503_01287_gb300 import binding as B
+    sizes = [4, 8, 16, 32][:args.replay_levels]
+    out = {"workload": "paper Sec. 4.1 tables, replayed", "tol": 1e-11, "max_iterations": 200,
+           "levels_n": sizes, "rows": []}
+    t0 = time.time()
+    for kind in ("laplace", "elasticity"):
+        for n in sizes:
+            prob = paper_setting_problem(kind, n)
+            b = torch.from_numpy(prob.rhs()).cuda()
+            for sm_name, sm, m in (("JA-1-1", B.AMG_SMOOTHER_JACOBI, 1),
+                                   ("JA-2-2", B.AMG_SMOOTHER_JACOBI, 2),
+                                   ("GS-1-1", B.AMG_SMOOTHER_GS, 1),
+                                   ("GS-2-2", B.AMG_SMOOTHER_GS, 2)):
+                for nu in (1, 2):
+                    for method, kr in (("amg", B.AMG_KRYLOV_NONE), ("pcg", B.AMG_KRYLOV_PCG)):
+                        h = B.setup_problem(prob, B.default_options(
+                            smoother=sm, m_pre=m, m_post=m, nu=nu, krylov=kr,
+                            max_iterations=200))
+                        x = torch.zeros_like(b)
+                        st = h.solve(b, x, 1e-11, device_ptrs=True)
+                        h.free()
+                        out["rows"].append({
+                            "kind": kind, "method": method, "cycle": "V" if nu == 1 else "W",
+                            "smoother": sm_name, "n": n, "dofs": prob.n_dof,
+                            "iterations": st.iterations if st.converged else None,
+                            "solve_ms": st.solve_ms,
+                            "paper": PAPER_TABLES[(kind, method, nu)][sm_name][sizes.index(n)]})
+    out["wall_s"] = time.time() - t0
+    print(json.dumps(out), flush=True)
+
+
 def run_batched(args):
     """64 uneven elasticity problems x 16 right-hand sides in one amg_solve_batched
     launch (box meshes n ~ U{8..24}, side lengths ~ U[1,4], nu ~ U[0.2,0.45],
@@ -435,7 +499,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mesh", action="store_true",
                     help="skip the iteration-count-versus-mesh-size study")
-    ap.add_argument("--workload", default="elasticity", choices=["elasticity", "batched"])
+    ap.add_argument("--workload", default="elasticity",
+                    choices=["elasticity", "batched", "replay"])
+    ap.add_argument("--replay-levels", type=int, default=4,
+                    help="replay: levels L1.. of the paper's tables (4^3, 8^3, 16^3, 32^3)")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--profile", action="store_true",
@@ -449,6 +516,8 @@ def main():
         return run_profile(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "replay":
+        return run_replay(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

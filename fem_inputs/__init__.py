@@ -8,5 +8,6 @@ from .mesh import BoxMesh, box_mesh, boundary_faces  # noqa: F401
 from .problems import (KIND_CODES, TAG_DIRICHLET, TAG_EDGE, TAG_VERTEX, Problem,  # noqa: F401
                        elasticity_problem, elasticity_quadratic_problem, lame,
                        mixed_elasticity_problem, rigid_body_modes, stokes_lid_problem,
-                       unconstrained_elasticity, vector_laplace_problem)
+                       paper_setting_problem, unconstrained_elasticity,
+                       vector_laplace_problem)
 from .configs import CONFIGS, make_config  # noqa: F401

@@ -361,3 +361,17 @@ def test_mesh_independent_iterations_laplace():
         its.append(res.iterations)
     assert max(its) - min(its) <= 5, its
     assert all(15 <= i <= 40 for i in its), its
+
+
+def test_paper_setting_laplace_reproduces_the_linear_solution():
+    """Sec. 4.1 setting (u = 0 on z = 0, u = (0,0,1) on z = 1, zero Neumann data): the
+    vector Laplacian's solution (0, 0, z) is in the P2 space, so the AMG-PCG solution
+    plus the Dirichlet lift equals its interpolant."""
+    from fem_inputs.problems import paper_setting_problem
+    for n in (2, 3):
+        p = paper_setting_problem("laplace", n)
+        r, _ = amg.solve(p, tol=1e-12)
+        assert r.converged
+        full = r.x.reshape(-1, 3) + p.lift
+        assert np.abs(full - p.exact_u).max() <= 1e-11
+        assert np.all(p.exact_u[:, :2] == 0.0)
