@@ -390,15 +390,23 @@ PAPER_TABLES = {
                                "GS-1-1": [40, 43, 43, 42], "GS-2-2": [28, 27, 27, 27]},
     ("elasticity", "pcg", 2): {"JA-1-1": [47, 80, None, None], "JA-2-2": [32, 62, None, None],
                                "GS-1-1": [39, 44, 42, 41], "GS-2-2": [28, 27, 27, 26]},
+    # mixed elasticity (Sec. 4.4), V-cycle, relative residual 1e-9
+    ("mixed", "amg", "BS"): {"1-1": [135, 133, 125, 117], "2-2": [71, 70, 66, 62]},
+    ("mixed", "gmres", "BS"): {"1V": [27, 27, 27, 27], "2V": [18, 19, 19, 19]},
+    ("mixed", "amg", "sGS"): {"1-1": [107, 104, 99, 93], "2-2": [54, 53, 53, 59]},
+    ("mixed", "gmres", "sGS"): {"1V": [14, 18, 19, 21], "2V": [12, 15, 15, 15]},
+    ("mixed", "gmres", "Vanka"): {"1V": [60, 45, 49, 69], "2V": [42, 30, 32, 45]},
 }
 
 
 def run_replay(args):
-    """The paper's Sec. 4.1 iteration tables replayed on the GPU (plain FP64 cycle):
-    vector Laplacian and elasticity with u = 0 on z = 0 and u = (0,0,1) on z = 1,
-    stand-alone AMG and AMG-PCG, V- and W-cycles, JA-m-m-0.5 and GS-m-m, levels
-    4^3..32^3, relative residual 1e-11, at most 200 iterations.  Our Gauss-Seidel is
-    the multicolour symmetric one, so the GS rows are a comparison, not a parity."""
+    """The paper's iteration tables replayed on the GPU (plain FP64 cycle), Sec. 4.1
+    setting (u = 0 on z = 0, u = (0,0,1) on z = 1): vector Laplacian and elasticity,
+    stand-alone AMG and AMG-PCG, V- and W-cycles, JA-m-m-0.5 and GS-m-m, relative
+    residual 1e-11, at most 200 iterations; mixed elasticity (Sec. 4.4), sGS and
+    Braess-Sarazin smoothers, stand-alone AMG and FGMRES with 1 or 2 V-cycles,
+    relative residual 1e-9.  Levels 4^3..32^3.  Our Gauss-Seidel is the multicolour
+    symmetric one and the sGS scaling is a reading, so the rows are a comparison."""
     import torch
     import __graft_entry__ as ge
     from fem_inputs.problems import paper_setting_problem
@@ -430,6 +438,27 @@ def run_replay(args):
                             "iterations": st.iterations if st.converged else None,
                             "solve_ms": st.solve_ms,
                             "paper": PAPER_TABLES[(kind, method, nu)][sm_name][sizes.index(n)]})
+    # mixed elasticity (Sec. 4.4): stand-alone AMG with m-m smoothing steps and FGMRES
+    # with 1 or 2 V-cycles per preconditioner, sGS and Braess-Sarazin smoothers
+    for n in sizes:
+        prob = paper_setting_problem("mixed", n)
+        b = torch.from_numpy(prob.rhs()).cuda()
+        for sm_name, sm in (("sGS", B.AMG_SMOOTHER_SGS), ("BS", B.AMG_SMOOTHER_BS)):
+            runs = [("amg", f"{m}-{m}", dict(m_pre=m, m_post=m, krylov=B.AMG_KRYLOV_NONE,
+                                             max_iterations=300)) for m in (1, 2)]
+            runs += [("gmres", f"{c}V", dict(cycles=c, krylov=B.AMG_KRYLOV_FGMRES,
+                                             max_iterations=300)) for c in (1, 2)]
+            for method, label, kw in runs:
+                h = B.setup_problem(prob, B.default_options(smoother=sm, **kw))
+                x = torch.zeros_like(b)
+                st = h.solve(b, x, 1e-9, device_ptrs=True)
+                h.free()
+                out["rows"].append({
+                    "kind": "mixed", "method": method, "cycle": "V", "smoother": sm_name,
+                    "setting": label, "n": n, "dofs": prob.n_dof,
+                    "iterations": st.iterations if st.converged else None,
+                    "solve_ms": st.solve_ms,
+                    "paper": PAPER_TABLES[("mixed", method, sm_name)][label][sizes.index(n)]})
     out["wall_s"] = time.time() - t0
     print(json.dumps(out), flush=True)
 

@@ -194,16 +194,22 @@ def vector_laplace_problem(n: int, seed: int = 0, dirichlet_faces=((2, 0),)) -> 
 
 
 def paper_setting_problem(kind: str, n: int) -> Problem:
-    """The test problem of the paper's Sec. 4.1 for the vector Laplacian and
-    pure-displacement elasticity: unit cube of n^3 cubes, u = (0, 0, 0) on z = 0,
-    u = (0, 0, 1) on z = 1, zero Neumann data on the other faces, no body force;
-    elasticity with mu = 1.15e6, lambda = 1.73e6.  For the vector Laplacian the
-    exact solution (0, 0, z) lies in the P2 space."""
+    """The test problem of the paper's Sec. 4.1 for the vector Laplacian,
+    pure-displacement elasticity and (Sec. 4.4) mixed elasticity: unit cube of n^3
+    cubes, u = (0, 0, 0) on z = 0, u = (0, 0, 1) on z = 1, zero Neumann data on the
+    other faces, no body force; elasticity with mu = 1.15e6, lambda = 1.73e6 (mixed
+    form: c(p, q) = (1/lambda) int p q, Taylor-Hood P2/P1).  For the vector
+    Laplacian the exact solution (0, 0, z) lies in the P2 space."""
     mesh = box_mesh(n)
+    mu, lam = 1.15e6, 1.73e6
+    saddle = None
     if kind == "laplace":
         rowptr, col, val = assemble_velocity(mesh, "laplace")
     elif kind == "elasticity":
-        rowptr, col, val = assemble_velocity(mesh, "elasticity", mu=1.15e6, lam=1.73e6)
+        rowptr, col, val = assemble_velocity(mesh, "elasticity", mu=mu, lam=lam)
+    elif kind == "mixed":
+        (rowptr, col, val), bpart, cpart = _saddle_parts(mesh, "mixed", mu, lam)
+        saddle = (*bpart, *cpart, np.zeros(mesh.n_vertices))
     else:
         raise ValueError(kind)
     bottom = boundary_faces(mesh, 2, 0)
@@ -214,9 +220,14 @@ def paper_setting_problem(kind: str, n: int) -> Problem:
     lift[top_v, 2] = 1.0          # vertex coefficients; edge coefficients of linear data are 0
     exact = hierarchical_interpolant(mesh, lambda x: np.stack(
         [np.zeros(len(x)), np.zeros(len(x)), x[:, 2]], axis=1)) if kind == "laplace" else None
-    prob = Problem(f"paper_{kind}_n{n}", kind, mesh, rowptr, col, val, tags,
-                   np.zeros((mesh.n_nodes, 3)), lift, exact_u=exact,
-                   params={"n": n, "setting": "Sec. 4.1"})
+    f = np.zeros((mesh.n_nodes, 3))
+    params = {"n": n, "setting": "Sec. 4.1"}
+    if saddle is None:
+        prob = Problem(f"paper_{kind}_n{n}", kind, mesh, rowptr, col, val, tags, f, lift,
+                       exact_u=exact, params=params)
+    else:
+        prob = Problem(f"paper_{kind}_n{n}", kind, mesh, rowptr, col, val, tags, f, lift,
+                       *saddle, params={**params, "lam": lam, "mu": mu})
     return eliminate_dirichlet(prob)
 
 
