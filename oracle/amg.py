@@ -302,6 +302,8 @@ def build_hierarchy(prob, opts: Options | None = None) -> Hierarchy:
         h.coarse_factor = sd.factor_coarsest(h)
         if opts.smoother == "bs":
             sd.bs_setup(h)
+        if opts.smoother == "vanka":
+            sd.vanka_setup(h)
     else:
         h.coarse_factor = ("cplu", complete_pivot_lu(levels[-1].A.toarray()))
     return h

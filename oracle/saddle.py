@@ -47,6 +47,9 @@ def attach_pressure(lv, prob):
     lv.B = b
     lv.C = c
     lv.c_pattern = amg.block_pattern(prob.c_rowptr, prob.c_col, npres)
+    # structural node pattern of B (pressure rows x velocity nodes)
+    lv.extra["b_pattern"] = sp.csr_matrix(
+        (np.ones(len(prob.b_col)), prob.b_col, prob.b_rowptr), shape=(npres, n))
     lv.extra["stokes"] = prob.kind == "stokes"
     # Stokes: pressure normalisation weights w_i = int phi_i (problem data)
     lv.extra["pmass"] = prob.p_weights if prob.kind == "stokes" else None
@@ -65,6 +68,10 @@ def coarsen_pressure(cur, nxt):
     cp.data[:] = 1.0
     cp.sort_indices()
     nxt.c_pattern = cp
+    bp = (cur.H_structure.T @ cur.extra["b_pattern"] @ cur.P_structure).tocsr()
+    bp.data[:] = 1.0
+    bp.sort_indices()
+    nxt.extra["b_pattern"] = bp
     nxt.extra["stokes"] = cur.extra["stokes"]
     nxt.extra["pmass"] = None
 
@@ -134,6 +141,78 @@ def s_cycle(h, l, rhs):
     return rec(0, rhs)
 
 
+VANKA_OMEGA = 0.7    # damping of the Vanka correction (not stated in the paper; see the pins)
+
+
+def vanka_setup(h):
+    """Per non-coarsest level: the patches (pressure unknown k and the velocity
+    nodes of the structural pattern of row k of B) and their local matrices
+    K_k = [A_k B_k^T; B_k -C_kk], kept as the pieces of its block elimination:
+    A_k^{-1} (A_k a principal submatrix of the SPD A: Cholesky), w_k = A_k^{-1} B_k^T
+    and the scalar Schur complement s_k = B_k w_k + C_kk; and the first-fit greedy
+    colouring, in patch order, of the patches' overlap graph (two patches conflict
+    when they share a velocity node)."""
+    L = len(h.levels) - 1
+    for l in range(L):
+        lv = h.levels[l]
+        bp = lv.extra["b_pattern"]
+        A = lv.A.tocsr()
+        B = lv.B.tocsr()
+        C = lv.C.tocsr()
+        patches, ainv, w, sk = [], [], [], []
+        for k in range(lv.npres):
+            nodes = np.sort(bp.indices[bp.indptr[k]:bp.indptr[k + 1]])
+            dofs = (3 * nodes[:, None] + np.arange(3)).ravel()
+            Ak = A[dofs][:, dofs].toarray()
+            Bk = B[k, dofs].toarray().ravel()
+            fac = sla.cho_factor(Ak)
+            Ai = sla.cho_solve(fac, np.eye(len(dofs)))
+            wk = Ai @ Bk
+            patches.append(dofs)
+            ainv.append(Ai)
+            w.append(wk)
+            sk.append(float(Bk @ wk + C[k, k]))
+        overlap = (bp @ bp.T).tocsr()
+        colour = amg.greedy_colouring(overlap)
+        lv.extra["vanka"] = {"dofs": patches, "ainv": ainv, "w": w, "s": np.array(sk),
+                             "B": B, "colour": colour,
+                             "ncolours": int(colour.max()) + 1 if len(colour) else 0}
+
+
+def vanka_local_solve(vk, k, ru, rp):
+    """[du; dp] = K_k^{-1} [ru; rp] by block elimination: y = A_k^{-1} ru,
+    dp = (B_k y - rp) / s_k (0 when s_k = 0: the patch's pressure couples to no
+    free velocity and has no C entry), du = y - w_k dp."""
+    y = vk["ainv"][k] @ ru
+    dofs = vk["dofs"][k]
+    bk = vk["B"][k, dofs].toarray().ravel()
+    s_k = vk["s"][k]
+    dp = (bk @ y - rp) / s_k if s_k != 0.0 else 0.0
+    return y - vk["w"][k] * dp, dp
+
+
+def smooth_vanka(h, l, x, b, post):
+    """Multiplicative Vanka, Eq. (locpatchsm), over the patch colours (ascending
+    before the coarse correction, descending after it): per colour the residual of
+    the whole level is updated, then every patch of the colour adds
+    omega K_k^{-1} r_k to its unknowns (patches of one colour do not overlap)."""
+    lv = h.levels[l]
+    vk = lv.extra["vanka"]
+    nu = 3 * lv.n
+    x = x.copy()
+    order = range(vk["ncolours"])
+    if post:
+        order = reversed(list(order))
+    for c in order:
+        r = b - apply_K(lv, x)
+        for k in np.nonzero(vk["colour"] == c)[0]:
+            dofs = vk["dofs"][k]
+            du, dp = vanka_local_solve(vk, k, r[dofs], r[nu + k])
+            x[dofs] += VANKA_OMEGA * du
+            x[nu + k] += VANKA_OMEGA * dp
+    return x
+
+
 def smooth_bs(h, l, x, b):
     """One Braess-Sarazin step, Eq. (bssm) with K^ of Eq. (bssmpre)."""
     lv = h.levels[l]
@@ -170,6 +249,8 @@ def smooth(h, l, x, b, post):
     o = h.opts
     if o.smoother == "bs":
         return smooth_bs(h, l, x, b)
+    if o.smoother == "vanka":
+        return smooth_vanka(h, l, x, b, post)
     nu = 3 * lv.n
     u, p = x[:nu].copy(), x[nu:].copy()
     f, g = b[:nu], b[nu:]

@@ -67,3 +67,63 @@ def test_bs_fgmres_reaches_the_direct_solution():
     K = saddle.coarse_matrix(h.levels[0])
     x = np.linalg.solve(K, prob.rhs())
     assert np.linalg.norm(res.x - x) <= 1e-9 * np.linalg.norm(x)
+
+
+# --------------------------------------------------------------------------- Vanka
+
+def test_vanka_local_solve_is_the_patch_inverse():
+    """Block elimination of Eq. (locpatchsm)'s local matrix equals a dense solve
+    of [A_k B_k^T; B_k -C_kk] assembled from the level's matrices."""
+    prob = fp.paper_setting_problem("mixed", 3)
+    h = amg.build_hierarchy(prob, amg.Options(smoother="vanka"))
+    lv = h.levels[0]
+    vk = lv.extra["vanka"]
+    A, Bm, Cm = lv.A.toarray(), lv.B.toarray(), lv.C.toarray()
+    rng = np.random.default_rng(1)
+    checked = 0
+    for k in range(0, lv.npres, 7):
+        dofs = vk["dofs"][k]
+        m = len(dofs)
+        K = np.zeros((m + 1, m + 1))
+        K[:m, :m] = A[np.ix_(dofs, dofs)]
+        K[m, :m] = K[:m, m] = Bm[k, dofs]
+        K[m, m] = -Cm[k, k]
+        r = rng.standard_normal(m + 1)
+        du, dp = saddle.vanka_local_solve(vk, k, r[:m], r[m])
+        want = np.linalg.solve(K, r)
+        assert np.linalg.norm(np.concatenate([du, [dp]]) - want) <= 1e-9 * np.linalg.norm(want)
+        checked += 1
+    assert checked > 3
+
+
+def test_vanka_patches_and_colouring():
+    """Patch k holds the velocity nodes of row k of B; patches of one colour share
+    no velocity node; the colouring is first-fit in patch order."""
+    prob = fp.mixed_elasticity_problem(3, nu=0.49, seed=2)
+    h = amg.build_hierarchy(prob, amg.Options(smoother="vanka"))
+    for lv in h.levels[:-1]:
+        vk = lv.extra["vanka"]
+        bp = lv.extra["b_pattern"]
+        col = vk["colour"]
+        owner = {}
+        for k in range(lv.npres):
+            nodes = bp.indices[bp.indptr[k]:bp.indptr[k + 1]]
+            assert np.array_equal(np.unique(vk["dofs"][k] // 3), np.sort(nodes))
+            for j in nodes:
+                for k2 in owner.get(j, []):
+                    assert col[k2] != col[k]
+                owner.setdefault(j, []).append(k)
+        # first fit: every patch's colour is the smallest not used by earlier conflicting ones
+        for k in range(lv.npres):
+            nb = {col[k2] for j in bp.indices[bp.indptr[k]:bp.indptr[k + 1]]
+                  for k2 in owner[j] if k2 < k}
+            assert col[k] == min(set(range(len(nb) + 1)) - nb)
+
+
+def test_vanka_fgmres_reaches_the_direct_solution():
+    prob = fp.mixed_elasticity_problem(3, nu=0.49, seed=2)
+    res, h = amg.solve(prob, amg.Options(smoother="vanka"), tol=1e-12)
+    assert res.converged
+    K = saddle.coarse_matrix(h.levels[0])
+    x = np.linalg.solve(K, prob.rhs())
+    assert np.linalg.norm(res.x - x) <= 1e-9 * np.linalg.norm(x)
