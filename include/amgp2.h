@@ -63,13 +63,20 @@ enum amg_smoother {
   AMG_SMOOTHER_GS = 0,      /* symmetric multicolour 3x3-block Gauss-Seidel     */
   AMG_SMOOTHER_JACOBI = 1,  /* damped 3x3-block Jacobi (omega, default 0.5)     */
   AMG_SMOOTHER_SGS = 2,     /* segregated Gauss-Seidel for saddle systems       */
-  AMG_SMOOTHER_BS = 3       /* Braess-Sarazin type for saddle systems, Eqs.
+  AMG_SMOOTHER_BS = 3,      /* Braess-Sarazin type for saddle systems, Eqs.
                                (bssm) / (bssmpre): x += K^{-1} (b - K x) with
                                K^ = [A^ B^T; B B A^{-1} B^T - S^], A^ = 2 diag(A),
                                S^{-1} one V(1,1)-cycle (damped scalar Jacobi 0.5)
                                of the graph AMG on S = C + B A^{-1} B^T through
                                the pressure prolongations H, direct solve on the
                                coarsest pressure level                          */
+  AMG_SMOOTHER_VANKA = 4    /* multiplicative Vanka, Eq. (locpatchsm): patch k =
+                               pressure unknown k and the velocity nodes of row
+                               k of B; x += omega [A_k B_k^T; B_k -C_kk]^{-1} r_k
+                               (omega 0.7) over the patches of one colour of the
+                               patch overlap graph, residual updated between
+                               colours (ascending before, descending after the
+                               coarse correction); at most 512 unknowns a patch */
 };
 
 enum amg_precision {

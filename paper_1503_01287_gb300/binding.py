@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libamgp2.so")
 
 # enums (include/amgp2.h)
 AMG_VECTOR_LAPLACE, AMG_ELASTICITY, AMG_MIXED_ELASTICITY, AMG_STOKES = 0, 1, 2, 3
-AMG_SMOOTHER_GS, AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SGS, AMG_SMOOTHER_BS = 0, 1, 2, 3
+AMG_SMOOTHER_GS, AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SGS, AMG_SMOOTHER_BS, AMG_SMOOTHER_VANKA = (
+    0, 1, 2, 3, 4)
 AMG_FP64, AMG_FP32, AMG_FP32_BF16 = 0, 1, 2
 AMG_KRYLOV_AUTO, AMG_KRYLOV_PCG, AMG_KRYLOV_FCG, AMG_KRYLOV_FGMRES, AMG_KRYLOV_NONE = 0, 1, 2, 3, 4
 AMG_OK, AMG_NOT_CONVERGED = 0, 1

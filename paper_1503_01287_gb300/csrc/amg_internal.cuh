@@ -138,6 +138,17 @@ struct Level {
   std::vector<std::unique_ptr<SLevel>> S;
   DBuf<double> s_coarse_inv;
   int s_coarse_m = 0;
+  // Vanka smoother: patch k = pressure unknown k with the velocity nodes of row k
+  // of B (m_k = 3 * row length unknowns); A_k^{-1} row-major at vk_off[k],
+  // w_k = A_k^{-1} B_k^T at 3 * b_rowptr[k], s_k = B_k w_k + C_kk; the patches in
+  // colour order (vk_rows[vk_colour_ptr[c] ..]) of the overlap-graph colouring
+  DBuf<long long> vk_off;
+  DBuf<double> vk_ainv, vk_w, vk_s;
+  DBuf<float> vk_ainv32, vk_w32, vk_s32;
+  DBuf<int> vk_colour, vk_rows;
+  std::vector<int> vk_colour_ptr;
+  int vk_ncolours = 0;
+  int vk_mmax = 0;
   int64_t h_nnz = 0;
   DBuf<int> h_rowptr, h_col, ht_rowptr, ht_col;
   DBuf<double> h_val, ht_val;

@@ -101,11 +101,19 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
     if (opt) h->opt = *opt;
     else amg_default_options(&h->opt);
     if (h->opt.smoother < 0) h->opt.smoother = saddle ? AMG_SMOOTHER_SGS : AMG_SMOOTHER_GS;
-    if (saddle && h->opt.smoother != AMG_SMOOTHER_SGS && h->opt.smoother != AMG_SMOOTHER_BS)
+    const bool saddle_smoother = h->opt.smoother == AMG_SMOOTHER_SGS ||
+                                 h->opt.smoother == AMG_SMOOTHER_BS ||
+                                 h->opt.smoother == AMG_SMOOTHER_VANKA;
+    if (saddle && !saddle_smoother)
       fail(AMG_ERR_UNSUPPORTED,
-           "saddle kinds use the segregated Gauss-Seidel or the Braess-Sarazin smoother");
-    if (!saddle && (h->opt.smoother == AMG_SMOOTHER_SGS || h->opt.smoother == AMG_SMOOTHER_BS))
-      fail(AMG_ERR_INVALID, "the segregated and Braess-Sarazin smoothers need a saddle kind");
+           "saddle kinds use the segregated Gauss-Seidel, Braess-Sarazin or Vanka smoother");
+    if (!saddle && saddle_smoother)
+      fail(AMG_ERR_INVALID, "the sGS, Braess-Sarazin and Vanka smoothers need a saddle kind");
+    if (h->opt.smoother == AMG_SMOOTHER_VANKA) {
+      // the Vanka patch phase runs as its own launches only
+      h->opt.cluster_from = 0;
+      h->opt.cycle_kernel = 1;
+    }
     if (h->opt.precision != AMG_FP64 && h->opt.precision != AMG_FP32 &&
         h->opt.precision != AMG_FP32_BF16)
       fail(AMG_ERR_INVALID, "unknown precision");

@@ -373,11 +373,81 @@ __device__ __forceinline__ void vec_body(int64_t n, const T* __restrict__ d, con
   }
 }
 
+// Vanka patch corrections of one colour (Eq. (locpatchsm)), one warp per patch k:
+// r_k gathered into registers (unknown j = lane + 32 q of the patch), y = A_k^{-1} r_u
+// (row by row, warp-reduced), dp = (B_k y - r_p) / s_k (0 when s_k = 0),
+// du = y - w_k dp, x_patch += omega du, p_k += omega dp.  Patches of one colour
+// share no unknown.
+constexpr int kVankaRegs = 16;   // 16 x 32 = 512 unknowns a patch
+
+template <typename T>
+__device__ __forceinline__ void vanka_body(int npatch, const int* __restrict__ patches,
+                                           const int* __restrict__ brow,
+                                           const int* __restrict__ bcol,
+                                           const T* __restrict__ bval, int64_t bnnz,
+                                           const long long* __restrict__ off,
+                                           const T* __restrict__ ainv,
+                                           const T* __restrict__ w, const T* __restrict__ sk,
+                                           const T* r, T* x, int n4, T omega, int warp,
+                                           int nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (int t = warp; t < npatch; t += nwarps) {
+    const int k = patches[t];
+    const int q0 = brow[k], m = 3 * (brow[k + 1] - q0);
+    T rj[kVankaRegs], yv[kVankaRegs];
+#pragma unroll
+    for (int q = 0; q < kVankaRegs; ++q) {
+      const int j = lane + 32 * q;
+      rj[q] = j < m ? r[4 * bcol[q0 + j / 3] + j % 3] : T(0);
+      yv[q] = T(0);
+    }
+    const T* Ai = ainv + off[k];
+#pragma unroll
+    for (int qb = 0; qb < kVankaRegs; ++qb) {
+      if (32 * qb >= m) break;
+      for (int ii = 0; ii < 32; ++ii) {
+        const int i = 32 * qb + ii;
+        if (i >= m) break;
+        const T* row = Ai + (int64_t)i * m;
+        T part = T(0);
+#pragma unroll
+        for (int q = 0; q < kVankaRegs; ++q) {
+          const int j = lane + 32 * q;
+          if (j < m) part = fma(row[j], rj[q], part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == ii) yv[qb] = part;
+      }
+    }
+    T bd = T(0);
+#pragma unroll
+    for (int q = 0; q < kVankaRegs; ++q) {
+      const int j = lane + 32 * q;
+      if (j < m) bd = fma(bval[(j % 3) * bnnz + q0 + j / 3], yv[q], bd);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bd += __shfl_xor_sync(0xffffffffu, bd, o);
+    const T s = sk[k];
+    const T dp = s != T(0) ? (bd - r[n4 + k]) / s : T(0);
+    const T* wk = w + 3 * (int64_t)q0;
+#pragma unroll
+    for (int q = 0; q < kVankaRegs; ++q) {
+      const int j = lane + 32 * q;
+      if (j < m) {
+        const int dof = 4 * bcol[q0 + j / 3] + j % 3;
+        x[dof] += omega * (yv[q] - wk[j] * dp);
+      }
+    }
+    if (lane == 0) x[n4 + k] += omega * dp;
+  }
+}
+
 // ------------------------------------------------------------------- phases
 
 enum PhaseType : int {
   PH_ZERO = 0, PH_COPY, PH_ROWS, PH_RESTRICT, PH_PROLONG, PH_RESTRICT1, PH_PROLONG1,
-  PH_COARSE, PH_BT_ADD, PH_PROWS, PH_SROWS, PH_VEC
+  PH_COARSE, PH_BT_ADD, PH_PROWS, PH_SROWS, PH_VEC, PH_VANKA
 };
 
 // One operation of the cycle with its operands (a plain record, copied to the
@@ -403,6 +473,7 @@ struct Phase {
   double omega;
   const double* wt;       // the level's learned weights (null: plain method)
   int vbf;                // PH_ROWS: values stored as BF16 (FP32 arithmetic)
+  const long long* off;   // PH_VANKA: offsets of the patch inverses
 };
 
 template <typename T, bool COH, typename V = T>
@@ -621,6 +692,15 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
                               (const T*)P.dinv, P.wt));
 }
 
+// the Vanka patch phase as its own kernel (its register tile stays out of the
+// generic phase kernels; the Vanka smoother runs with per-operation launches)
+template <typename T>
+__global__ void __launch_bounds__(256) k_vanka(const Phase P) {
+  vanka_body<T>(P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz, P.off, (const T*)P.dinv,
+                (const T*)P.cval, (const T*)P.sd, (const T*)P.x, (T*)P.y, P.n3, (T)P.omega,
+                (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
 // one operation as its own kernel
 template <typename T>
 __global__ void __launch_bounds__(256) k_phase(const Phase P) {
@@ -797,6 +877,21 @@ template <> struct SVec<float> {
   static const float* ahinv(Level& l) { return l.ahinv32; }
 };
 
+template <typename T> struct VkVec;
+template <> struct VkVec<double> {
+  static const double* ainv(Level& l) { return l.vk_ainv; }
+  static const double* w(Level& l) { return l.vk_w; }
+  static const double* s(Level& l) { return l.vk_s; }
+};
+template <> struct VkVec<float> {
+  static const float* ainv(Level& l) { return l.vk_ainv32; }
+  static const float* w(Level& l) { return l.vk_w32; }
+  static const float* s(Level& l) { return l.vk_s32; }
+};
+
+// damping of the Vanka correction (the paper gives none; 0.7 is the reading)
+constexpr double kVankaOmega = 0.7;
+
 // damping of the scalar Jacobi smoother of the S-cycle (Braess-Sarazin)
 constexpr double kBsJacobi = 0.5;
 
@@ -822,6 +917,7 @@ struct Emit {
     }
     if (work <= 0) return;
     if (P.type == PH_ROWS) launch_rows<T>(P, h->stream, h->use_pdl);
+    else if (P.type == PH_VANKA) k_vanka<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
     else k_phase<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
     h->launches++;
   }
@@ -883,6 +979,16 @@ struct Emit {
     Phase P = blank(PH_VEC);
     P.mode = mode; P.n = (int)n; P.dinv = d; P.x = x; P.b = b; P.omega = (double)omega; P.y = y;
     put(P, n);
+  }
+  void vanka(Level& lv, int c, const T* r, T* x) {
+    if (rec) fail(AMG_ERR_UNSUPPORTED, "the Vanka smoother runs with per-operation launches");
+    Phase P = blank(PH_VANKA);
+    const int a = lv.vk_colour_ptr[c];
+    P.n = lv.vk_colour_ptr[c + 1] - a; P.rows = lv.vk_rows.p + a;
+    P.rowptr = lv.b_rowptr; P.col = lv.b_col; P.val = LvVec<T>::bval(lv); P.nnz = lv.b_nnz;
+    P.off = lv.vk_off; P.dinv = VkVec<T>::ainv(lv); P.cval = VkVec<T>::w(lv);
+    P.sd = VkVec<T>::s(lv); P.x = r; P.y = x; P.n3 = 4 * lv.n; P.omega = kVankaOmega;
+    put(P, P.n, 32);
   }
   void coarse_s(Level& lv, const T* b, T* x) {
     Phase P = blank(PH_COARSE);
@@ -981,6 +1087,16 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
     int l = 0;
     while (h->L[l].get() != &lv) ++l;
     e_smooth_bs<T>(e, h, l, x, b);
+    return;
+  }
+  if (h->saddle && h->opt.smoother == AMG_SMOOTHER_VANKA) {
+    // multiplicative over the patch colours: the residual of the level before each
+    T* r = LvVec<T>::r(lv);
+    for (int q = 0; q < lv.vk_ncolours; ++q) {
+      const int c = post ? lv.vk_ncolours - 1 - q : q;
+      e_residual<T>(e, lv, x, b, r, true);
+      e.vanka(lv, c, r, x);
+    }
     return;
   }
   if (h->saddle) {

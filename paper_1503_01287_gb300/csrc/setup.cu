@@ -1002,11 +1002,23 @@ int64_t galerkin(amg_handle* h, int nc, int ncols_c, const DBuf<int>& rrow, cons
   return cnnz;
 }
 
+// First-fit greedy colouring of a graph in increasing vertex index (round-based,
+// equal to the sequential result); `rows` receives the vertices colour by colour.
+void colour_graph(amg_handle* h, int n, const DBuf<int>& rowptr, const DBuf<int>& col,
+                  DBuf<int>& colour, int& ncolours, std::vector<int>& colour_ptr,
+                  DBuf<int>& rows);
+
 void colour_level(amg_handle* h, Level& lv) {
+  colour_graph(h, lv.n, lv.rowptr, lv.col, lv.colour, lv.ncolours, lv.colour_ptr,
+               lv.colour_rows);
+}
+
+void colour_graph(amg_handle* h, int n, const DBuf<int>& rowptr, const DBuf<int>& col,
+                  DBuf<int>& colour, int& ncolours, std::vector<int>& colour_ptr,
+                  DBuf<int>& rows) {
   cudaStream_t s = h->stream;
-  int n = lv.n;
-  lv.colour.alloc(std::max(n, 1));
-  AMG_CUDA(cudaMemsetAsync(lv.colour.p, 0xff, n * sizeof(int), s));
+  colour.alloc(std::max(n, 1));
+  AMG_CUDA(cudaMemsetAsync(colour.p, 0xff, n * sizeof(int), s));
   DBuf<int> rem;
   rem.alloc(1);
   int remaining = n;
@@ -1015,7 +1027,7 @@ void colour_level(amg_handle* h, Level& lv) {
     if (round > n + batch) fail(AMG_ERR_TIMEOUT, "colouring rounds exceeded their bound");
     for (int b = 0; b < batch; ++b) {
       AMG_CUDA(cudaMemsetAsync(rem.p, 0, sizeof(int), s));
-      k_colour_round<<<grid_for(n), 256, 0, s>>>(n, lv.rowptr, lv.col, lv.colour, rem);
+      k_colour_round<<<grid_for(n), 256, 0, s>>>(n, rowptr, col, colour, rem);
       h->launches++;
     }
     AMG_LAUNCH_CHECK();
@@ -1023,24 +1035,24 @@ void colour_level(amg_handle* h, Level& lv) {
     AMG_CUDA(cudaStreamSynchronize(s));
   }
   std::vector<int> hc(n);
-  AMG_CUDA(cudaMemcpyAsync(hc.data(), lv.colour.p, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaMemcpyAsync(hc.data(), colour.p, n * sizeof(int), cudaMemcpyDeviceToHost, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   int nc = 0;
   for (int c : hc) nc = std::max(nc, c + 1);
-  lv.ncolours = nc;
-  lv.colour_ptr.assign(nc + 1, 0);
-  lv.colour_rows.alloc(std::max(n, 1));
+  ncolours = nc;
+  colour_ptr.assign(nc + 1, 0);
+  rows.alloc(std::max(n, 1));
   DBuf<int> fl, pos;
   fl.alloc(std::max(n, 1));
   pos.alloc(n + 1);
   int off = 0;
   for (int c = 0; c < nc; ++c) {
-    k_colour_flag<<<grid_for(n), 256, 0, s>>>(n, lv.colour, c, fl);
+    k_colour_flag<<<grid_for(n), 256, 0, s>>>(n, colour, c, fl);
     int cnt = (int)exclusive_scan(fl, pos, n, s, h);
-    k_colour_scatter<<<grid_for(n), 256, 0, s>>>(n, lv.colour, c, pos, off, lv.colour_rows);
+    k_colour_scatter<<<grid_for(n), 256, 0, s>>>(n, colour, c, pos, off, rows);
     h->launches += 2;
     off += cnt;
-    lv.colour_ptr[c + 1] = off;
+    colour_ptr[c + 1] = off;
   }
   AMG_LAUNCH_CHECK();
 }
@@ -1362,6 +1374,197 @@ void bs_setup(amg_handle* h) {
   AMG_CUDA(cudaStreamSynchronize(s));
 }
 
+// ============================================================================ Vanka setup
+//
+// Patch k: pressure unknown k and the velocity nodes b_col[b_rowptr[k] ..] of row
+// k of B (ascending), m_k = 3 * (row length) velocity unknowns.  A_k^{-1} is
+// formed in place in its slot (row-major m_k x m_k at off[k]).
+
+constexpr int kVankaMax = 512;   // unknowns of a patch (the cycle kernel's register tile)
+
+__device__ __forceinline__ int find_col(const int* __restrict__ col, int a, int e, int j) {
+  while (a < e) {
+    const int mid = (a + e) >> 1;
+    const int c = col[mid];
+    if (c == j) return mid;
+    if (c < j) a = mid + 1;
+    else e = mid;
+  }
+  return -1;
+}
+
+// dense A_k: block (a, b) = A[node_a][node_b] (zero when not stored)
+__global__ void k_vk_gather(int np, const int* __restrict__ brow, const int* __restrict__ bcol,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, int64_t nnzb,
+                            const long long* __restrict__ off, double* __restrict__ ainv) {
+  for (int k = blockIdx.x; k < np; k += gridDim.x) {
+    const int q0 = brow[k], len = brow[k + 1] - q0, m = 3 * len;
+    double* M = ainv + off[k];
+    for (int t = threadIdx.x; t < len * len; t += blockDim.x) {
+      const int a = t / len, b = t % len;
+      const int na = bcol[q0 + a], nb = bcol[q0 + b];
+      const int q = find_col(col, rowptr[na], rowptr[na + 1], nb);
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          M[(int64_t)(3 * a + r) * m + 3 * b + c] = q >= 0 ? val[(3 * r + c) * nnzb + q] : 0.0;
+    }
+  }
+}
+
+// In-place Gauss-Jordan inversion of the SPD A_k (no pivoting: every pivot of an
+// SPD matrix is positive); a non-positive pivot sets *flag and leaves the patch.
+__global__ void k_vk_invert(int np, const int* __restrict__ brow,
+                            const long long* __restrict__ off, double* __restrict__ ainv,
+                            int* flag) {
+  extern __shared__ int vk_sh[];
+  double* colk = reinterpret_cast<double*>(vk_sh);   // column k before the step
+  double* rowk = colk + kVankaMax;                     // row k after scaling
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const int m = 3 * (brow[p + 1] - brow[p]);
+    double* M = ainv + off[p];
+    bool bad = false;
+    for (int k = 0; k < m && !bad; ++k) {
+      const double piv = M[(int64_t)k * m + k];
+      __syncthreads();
+      if (!(piv > 0.0)) {
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        bad = true;
+        break;
+      }
+      for (int i = threadIdx.x; i < m; i += blockDim.x) colk[i] = M[(int64_t)i * m + k];
+      for (int j = threadIdx.x; j < m; j += blockDim.x)
+        rowk[j] = (j == k ? 1.0 : M[(int64_t)k * m + j]) / piv;
+      __syncthreads();
+      for (int j = threadIdx.x; j < m; j += blockDim.x) M[(int64_t)k * m + j] = rowk[j];
+      for (int t = threadIdx.x; t < (m - 1) * m; t += blockDim.x) {
+        int i = t / m;
+        const int j = t % m;
+        if (i >= k) ++i;
+        const double base = j == k ? 0.0 : M[(int64_t)i * m + j];
+        M[(int64_t)i * m + j] = base - colk[i] * rowk[j];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// w_k = A_k^{-1} B_k^T, s_k = B_k w_k + C_kk
+__global__ void k_vk_ws(int np, const int* __restrict__ brow, const double* __restrict__ bval,
+                        int64_t bnnz, const int* __restrict__ crow,
+                        const int* __restrict__ ccol, const double* __restrict__ cval,
+                        const long long* __restrict__ off, const double* __restrict__ ainv,
+                        double* __restrict__ w, double* __restrict__ sk) {
+  __shared__ double red[8];
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const int q0 = brow[p], m = 3 * (brow[p + 1] - q0);
+    const double* M = ainv + off[p];
+    double* wp = w + 3 * (int64_t)q0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j)
+        acc = fma(M[(int64_t)i * m + j], bval[(j % 3) * bnnz + q0 + j / 3], acc);
+      wp[i] = acc;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+      part = fma(bval[(j % 3) * bnnz + q0 + j / 3], wp[j], part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+      double c = 0.0;
+      for (int q = crow[p]; q < crow[p + 1]; ++q)
+        if (ccol[q] == p) c = cval[q];
+      sk[p] = t + c;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_fill_int(int* a, int v, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    a[k] = v;
+}
+
+__global__ void k_iota(int* a, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    a[k] = k;
+}
+
+// Patches, local inverses and the patch colouring of every non-coarsest saddle level.
+void vanka_setup(amg_handle* h) {
+  cudaStream_t s = h->stream;
+  const bool fp32 = h->opt.precision == AMG_FP32;
+  const int L = (int)h->L.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    Level& lv = *h->L[l];
+    const int np = lv.np;
+    std::vector<int> br(np + 1);
+    AMG_CUDA(cudaMemcpyAsync(br.data(), lv.b_rowptr.p, (np + 1) * sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<long long> off(np + 1, 0);
+    int mmax = 0;
+    for (int k = 0; k < np; ++k) {
+      const long long m = 3LL * (br[k + 1] - br[k]);
+      mmax = std::max<int>(mmax, (int)m);
+      off[k + 1] = off[k] + m * m;
+    }
+    if (mmax > kVankaMax) fail(AMG_ERR_UNSUPPORTED, "Vanka patch larger than 512 unknowns");
+    lv.vk_mmax = mmax;
+    lv.vk_off.alloc(np + 1);
+    AMG_CUDA(cudaMemcpyAsync(lv.vk_off.p, off.data(), (np + 1) * sizeof(long long),
+                             cudaMemcpyHostToDevice, s));
+    lv.vk_ainv.alloc(std::max<long long>(off[np], 1));
+    lv.vk_w.alloc(std::max<int64_t>(3 * lv.b_nnz, 1));
+    lv.vk_s.alloc(std::max(np, 1));
+    const int grid = std::max(1, std::min(np, 152 * 8));
+    k_vk_gather<<<grid, 256, 0, s>>>(np, lv.b_rowptr, lv.b_col, lv.rowptr, lv.col, lv.val,
+                                     lv.nnzb, lv.vk_off, lv.vk_ainv);
+    AMG_LAUNCH_CHECK();
+    Flag f(h);
+    f.reset();
+    k_vk_invert<<<grid, 256, 2 * kVankaMax * sizeof(double), s>>>(np, lv.b_rowptr, lv.vk_off,
+                                                                  lv.vk_ainv, h->flag);
+    AMG_LAUNCH_CHECK();
+    k_vk_ws<<<grid, 256, 0, s>>>(np, lv.b_rowptr, lv.b_val, lv.b_nnz, lv.c_rowptr, lv.c_col,
+                                 lv.c_val, lv.vk_off, lv.vk_ainv, lv.vk_w, lv.vk_s);
+    AMG_LAUNCH_CHECK();
+    h->launches += 3;
+    if (f.read()) fail(AMG_ERR_BREAKDOWN, "Vanka patch matrix A_k is not positive definite");
+    if (fp32) {
+      lv.vk_ainv32.alloc(std::max<long long>(off[np], 1));
+      launch_to_float(lv.vk_ainv, lv.vk_ainv32, off[np], s, h);
+      lv.vk_w32.alloc(std::max<int64_t>(3 * lv.b_nnz, 1));
+      launch_to_float(lv.vk_w, lv.vk_w32, 3 * lv.b_nnz, s, h);
+      lv.vk_s32.alloc(std::max(np, 1));
+      launch_to_float(lv.vk_s, lv.vk_s32, np, s, h);
+    }
+    // overlap graph of the patches: the pattern of B B^T (node level)
+    DBuf<int> irow, icol, trow, tcol, orow, ocol;
+    DBuf<double> ones, ival, tval, oval;
+    ones.alloc(std::max<int64_t>(lv.b_nnz, 1));
+    launch_fill(ones, 1.0, lv.b_nnz, s, h);
+    irow.alloc(lv.n + 1);
+    k_iota<<<grid_for(lv.n + 1), 256, 0, s>>>(irow, lv.n + 1);
+    icol.alloc(std::max(lv.n, 1));
+    k_iota<<<grid_for(lv.n), 256, 0, s>>>(icol, lv.n);
+    ival.alloc(std::max(lv.n, 1));
+    launch_fill(ival, 1.0, lv.n, s, h);
+    h->launches += 2;
+    transpose(h, np, lv.n, lv.b_rowptr, lv.b_col, ones, 1, lv.b_nnz, trow, tcol, tval);
+    galerkin<1>(h, np, np, lv.b_rowptr, lv.b_col, ones, irow, icol, ival, lv.n, trow, tcol, tval,
+                orow, ocol, oval);
+    colour_graph(h, np, orow, ocol, lv.vk_colour, lv.vk_ncolours, lv.vk_colour_ptr, lv.vk_rows);
+    AMG_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
 void factor_coarsest(amg_handle* h) {
   Level& lv = *h->L.back();
   cudaStream_t s = h->stream;
@@ -1439,6 +1642,7 @@ void build_hierarchy(amg_handle* h, const amg_matrix* m, const int32_t* tags) {
   for (size_t l = 0; l < h->L.size(); ++l) h->L[l]->wt = h->wts.p + 4 * l;
   factor_coarsest(h);
   if (h->saddle && h->opt.smoother == AMG_SMOOTHER_BS) bs_setup(h);
+  if (h->saddle && h->opt.smoother == AMG_SMOOTHER_VANKA) vanka_setup(h);
   autotune_levels(h);
   AMG_CUDA(cudaStreamSynchronize(s));
 }

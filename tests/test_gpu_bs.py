@@ -120,3 +120,65 @@ def test_bs_fp32_cycle():
     print(f"\nBS {st.iterations} iterations, sGS {st_sgs.iterations}")
     h.free()
     sg.free()
+
+
+# --------------------------------------------------------------------------- Vanka
+
+def vanka(prob, **kw):
+    return B().setup_problem(prob, B().default_options(smoother=B().AMG_SMOOTHER_VANKA, **kw))
+
+
+@pytest.mark.parametrize("kind", ["mixed", "mixed_jittered", "stokes"])
+def test_vanka_step_matches_oracle(kind):
+    prob = PROBS[kind]()
+    h = vanka(prob)
+    oh = amg.build_hierarchy(prob, amg.Options(smoother="vanka"))
+    rng = np.random.default_rng(4)
+    x0 = rng.standard_normal(prob.n_dof)
+    b = rng.standard_normal(prob.n_dof)
+    for post in (False, True):
+        xg = cuda(x0)
+        h.level_smooth(0, xg, cuda(b), post=post)
+        want = saddle.smooth(oh, 0, x0, b, post=post)
+        got = xg.cpu().numpy()
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want), post
+    h.free()
+
+
+def test_vanka_preconditioner_matches_oracle():
+    prob = PROBS["mixed"]()
+    h = vanka(prob)
+    oh = amg.build_hierarchy(prob, amg.Options(smoother="vanka"))
+    r = np.random.default_rng(3).standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(cuda(r), z)
+    want = amg.precondition(oh, r)
+    assert np.linalg.norm(z.cpu().numpy() - want) <= 1e-10 * np.linalg.norm(want)
+    h.free()
+
+
+@pytest.mark.parametrize("kind", ["mixed", "stokes"])
+def test_vanka_fgmres_matches_oracle(kind):
+    prob = PROBS[kind]()
+    h = vanka(prob)
+    b = cuda(prob.rhs())
+    x = torch.zeros_like(b)
+    st = h.solve(b, x, 1e-10, device_ptrs=True)
+    xv = x.cpu().numpy()
+    ref, _ = amg.solve(prob, amg.Options(smoother="vanka"), tol=1e-10)
+    assert st.converged and st.true_rel_residual <= 1e-9
+    assert abs(st.iterations - ref.iterations) <= 2, (st.iterations, ref.iterations)
+    n3 = 3 * prob.n_nodes
+    assert np.linalg.norm(xv[:n3] - ref.x[:n3]) <= 1e-7 * np.linalg.norm(ref.x[:n3])
+    h.free()
+
+
+def test_vanka_fp32_cycle():
+    prob = fp.mixed_elasticity_problem(5, nu=0.499, seed=5)
+    h = vanka(prob, precision=B().AMG_FP32)
+    b = cuda(prob.rhs())
+    x = torch.zeros_like(b)
+    st = h.solve(b, x, 1e-8, device_ptrs=True)
+    assert st.converged and st.true_rel_residual <= 1.5e-8
+    print(f"\nVanka FP32 cycle: {st.iterations} iterations")
+    h.free()
