@@ -404,8 +404,8 @@ def run_replay(args):
     setting (u = 0 on z = 0, u = (0,0,1) on z = 1): vector Laplacian and elasticity,
     stand-alone AMG and AMG-PCG, V- and W-cycles, JA-m-m-0.5 and GS-m-m, relative
     residual 1e-11, at most 200 iterations; mixed elasticity (Sec. 4.4), sGS and
-    Braess-Sarazin smoothers, stand-alone AMG and FGMRES with 1 or 2 V-cycles,
-    relative residual 1e-9.  Levels 4^3..32^3.  Our Gauss-Seidel is the multicolour
+    Braess-Sarazin smoothers (stand-alone AMG and FGMRES with 1 or 2 V-cycles) and
+    the Vanka smoother (FGMRES), relative residual 1e-9.  Levels 4^3..32^3.  Our Gauss-Seidel is the multicolour
     symmetric one and the sGS scaling is a reading, so the rows are a comparison."""
     import torch
     import __graft_entry__ as ge
@@ -443,9 +443,11 @@ def run_replay(args):
     for n in sizes:
         prob = paper_setting_problem("mixed", n)
         b = torch.from_numpy(prob.rhs()).cuda()
-        for sm_name, sm in (("sGS", B.AMG_SMOOTHER_SGS), ("BS", B.AMG_SMOOTHER_BS)):
-            runs = [("amg", f"{m}-{m}", dict(m_pre=m, m_post=m, krylov=B.AMG_KRYLOV_NONE,
-                                             max_iterations=300)) for m in (1, 2)]
+        for sm_name, sm in (("sGS", B.AMG_SMOOTHER_SGS), ("BS", B.AMG_SMOOTHER_BS),
+                            ("Vanka", B.AMG_SMOOTHER_VANKA)):
+            runs = [] if sm_name == "Vanka" else [
+                ("amg", f"{m}-{m}", dict(m_pre=m, m_post=m, krylov=B.AMG_KRYLOV_NONE,
+                                         max_iterations=300)) for m in (1, 2)]
             runs += [("gmres", f"{c}V", dict(cycles=c, krylov=B.AMG_KRYLOV_FGMRES,
                                              max_iterations=300)) for c in (1, 2)]
             for method, label, kw in runs:
