@@ -1381,6 +1381,8 @@ void bs_setup(amg_handle* h) {
 // formed in place in its slot (row-major m_k x m_k at off[k]).
 
 constexpr int kVankaMax = 512;   // unknowns of a patch (the cycle kernel's register tile)
+constexpr int kVankaSmem = 237;  // patches factorised in shared memory: m (m + 1) / 2 + m
+                                 // doubles within 227 KB
 
 __device__ __forceinline__ int find_col(const int* __restrict__ col, int a, int e, int j) {
   while (a < e) {
@@ -1412,8 +1414,9 @@ __global__ void k_vk_gather(int np, const int* __restrict__ brow, const int* __r
   }
 }
 
-// In-place Gauss-Jordan inversion of the SPD A_k (no pivoting: every pivot of an
-// SPD matrix is positive); a non-positive pivot sets *flag and leaves the patch.
+// Patches above kVankaSmem unknowns: in-place Gauss-Jordan inversion of the SPD A_k
+// in global memory (no pivoting: every pivot of an SPD matrix is positive); a
+// non-positive pivot sets *flag and leaves the patch.
 __global__ void k_vk_invert(int np, const int* __restrict__ brow,
                             const long long* __restrict__ off, double* __restrict__ ainv,
                             int* flag) {
@@ -1422,6 +1425,7 @@ __global__ void k_vk_invert(int np, const int* __restrict__ brow,
   double* rowk = colk + kVankaMax;                     // row k after scaling
   for (int p = blockIdx.x; p < np; p += gridDim.x) {
     const int m = 3 * (brow[p + 1] - brow[p]);
+    if (m <= kVankaSmem) continue;     // done by k_vk_chol
     double* M = ainv + off[p];
     bool bad = false;
     for (int k = 0; k < m && !bad; ++k) {
@@ -1446,6 +1450,77 @@ __global__ void k_vk_invert(int np, const int* __restrict__ brow,
       }
       __syncthreads();
     }
+  }
+}
+
+// Patches of at most kVankaSmem unknowns: Cholesky of A_k, inverse of the factor
+// and A_k^{-1} = L^{-T} L^{-1}, all in shared memory (packed lower triangle, row i
+// at i (i + 1) / 2), then A_k^{-1} written over A_k in its slot.  Larger patches
+// are left to k_vk_invert.  A non-positive pivot sets *flag.
+__global__ void __launch_bounds__(512) k_vk_chol(int np, const int* __restrict__ brow,
+                                                  const long long* __restrict__ off,
+                                                  double* __restrict__ ainv, int* flag) {
+  extern __shared__ int vk_sh[];
+  double* L = reinterpret_cast<double*>(vk_sh);
+  __shared__ int bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const int m = 3 * (brow[p + 1] - brow[p]);
+    if (m > kVankaSmem) continue;
+    double* M = ainv + off[p];
+    double* tmp = L + m * (m + 1) / 2;
+    auto at = [&](int i, int j) -> double& { return L[i * (i + 1) / 2 + j]; };
+    for (int i = warp; i < m; i += nwarps)
+      for (int j = lane; j <= i; j += 32) at(i, j) = M[(int64_t)i * m + j];
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    // Cholesky, right-looking
+    for (int k = 0; k < m; ++k) {
+      if (threadIdx.x == 0) {
+        const double d = at(k, k);
+        if (!(d > 0.0)) bad = 1;
+        at(k, k) = d > 0.0 ? sqrt(d) : 1.0;
+      }
+      __syncthreads();
+      const double lkk = at(k, k);
+      for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) at(i, k) /= lkk;
+      __syncthreads();
+      for (int i = k + 1 + warp; i < m; i += nwarps) {
+        const double lik = at(i, k);
+        for (int j = k + 1 + lane; j <= i; j += 32) at(i, j) -= lik * at(j, k);
+      }
+      __syncthreads();
+    }
+    if (bad) {
+      if (threadIdx.x == 0) atomicOr(flag, 2);
+      __syncthreads();
+      continue;
+    }
+    // L^{-1} in place, column by column from the last:
+    // (L^{-1})_ij = -(1 / L_jj) sum_{k=j+1..i} (L^{-1})_ik L_kj
+    for (int j = m - 1; j >= 0; --j) {
+      for (int i = j + 1 + warp; i < m; i += nwarps) {
+        double acc = 0.0;
+        for (int k = j + 1 + lane; k <= i; k += 32) acc = fma(at(i, k), at(k, j), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) tmp[i] = -acc / at(j, j);
+      }
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) at(i, j) = tmp[i];
+      __syncthreads();
+      if (threadIdx.x == 0) at(j, j) = 1.0 / at(j, j);
+      __syncthreads();
+    }
+    // A^{-1}_ij = sum_{k >= max(i, j)} (L^{-1})_ki (L^{-1})_kj
+    for (int i = warp; i < m; i += nwarps)
+      for (int j = lane; j <= i; j += 32) {
+        double acc = 0.0;
+        for (int k = i; k < m; ++k) acc = fma(at(k, i), at(k, j), acc);
+        M[(int64_t)i * m + j] = acc;
+        M[(int64_t)j * m + i] = acc;
+      }
+    __syncthreads();
   }
 }
 
@@ -1529,9 +1604,24 @@ void vanka_setup(amg_handle* h) {
     AMG_LAUNCH_CHECK();
     Flag f(h);
     f.reset();
-    k_vk_invert<<<grid, 256, 2 * kVankaMax * sizeof(double), s>>>(np, lv.b_rowptr, lv.vk_off,
-                                                                  lv.vk_ainv, h->flag);
+    const int msm = std::min(mmax, kVankaSmem);
+    const size_t chol_shm = (size_t)(msm * (msm + 1) / 2 + msm) * sizeof(double);
+    static bool chol_attr = false;
+    if (!chol_attr) {
+      AMG_CUDA(cudaFuncSetAttribute(k_vk_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((kVankaSmem * (kVankaSmem + 1) / 2 + kVankaSmem) *
+                                          sizeof(double))));
+      chol_attr = true;
+    }
+    k_vk_chol<<<std::max(1, std::min(np, 152 * 2)), 512, chol_shm, s>>>(np, lv.b_rowptr,
+                                                                       lv.vk_off, lv.vk_ainv,
+                                                                       h->flag);
     AMG_LAUNCH_CHECK();
+    if (mmax > kVankaSmem) {
+      k_vk_invert<<<grid, 256, 2 * kVankaMax * sizeof(double), s>>>(np, lv.b_rowptr, lv.vk_off,
+                                                                    lv.vk_ainv, h->flag);
+      AMG_LAUNCH_CHECK();
+    }
     k_vk_ws<<<grid, 256, 0, s>>>(np, lv.b_rowptr, lv.b_val, lv.b_nnz, lv.c_rowptr, lv.c_col,
                                  lv.c_val, lv.vk_off, lv.vk_ainv, lv.vk_w, lv.vk_s);
     AMG_LAUNCH_CHECK();
