@@ -19,8 +19,10 @@ target 0 by definition, so the plain method is the yardstick of every sample.
 
 Training.  Adam on the mean squared error with the amg_mlp_* kernels (BF16
 products, FP32 accumulation), full batch, problems split 90 / 10 into
-training and validation sets.  The parameters (float32, AMG_MLP_NPARAM) are
-written to --out and a summary (data, losses, timings) next to it as .json.
+training and validation sets, learning rate divided by 10 over the last third;
+the parameters with the lowest validation error are kept.  They (float32,
+AMG_MLP_NPARAM) are written to --out, the measured dataset next to it as
+.data.npz (retrain with --data) and a summary (data, losses, timings) as .json.
 
 Problems are generated by a process pool started with `spawn` before the
 first CUDA call, a chunk ahead of the GPU measurements.
@@ -121,18 +123,25 @@ def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: floa
     loss = torch.zeros(1, device="cuda")
     Xt, Tt, Xv, Tv = dev(X[train_idx]), dev(T[train_idx]), dev(X[val_idx]), dev(T[val_idx])
     hist = []
+    best, best_val = theta.clone(), float("inf")
+    yv = torch.zeros(max(len(val_idx), 1), device="cuda")
     t0 = time.time()
     for step in range(1, steps + 1):
+        # learning rate: constant, then divided by 10 over the last third
+        lr_k = lr if step <= 2 * steps // 3 else lr * 0.1
         B.mlp_gradient(theta, Xt, Tt, g, loss)
-        B.mlp_adam(theta, g, m, v, step, lr)
-        if step % 500 == 0 or step == steps:
-            tr = loss.item()
-            yv = torch.zeros(len(val_idx), device="cuda")
+        B.mlp_adam(theta, g, m, v, step, lr_k)
+        if step % 100 == 0 or step == steps:
             B.mlp_forward(theta, Xv, yv)
-            vl = float(((yv - Tv) ** 2).mean().item()) if len(val_idx) else float("nan")
-            hist.append({"step": step, "train_mse": tr, "val_mse": vl})
+            vl = float(((yv[:len(val_idx)] - Tv) ** 2).mean().item()) if len(val_idx) else 0.0
+            if vl < best_val:       # the parameters with the lowest validation error
+                best_val = vl
+                best.copy_(theta)
+            if step % 500 == 0 or step == steps:
+                hist.append({"step": step, "train_mse": loss.item(), "val_mse": vl})
     torch.cuda.synchronize()
-    return theta.cpu().numpy(), hist, time.time() - t0
+    hist.append({"kept": "lowest validation error", "val_mse": best_val})
+    return best.cpu().numpy(), hist, time.time() - t0
 
 
 def main(argv=None):
@@ -145,7 +154,12 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights",
                                                   "mlp_theta.npy"))
+    ap.add_argument("--data", default=None,
+                    help="train on a dataset written by an earlier run (<out>.data.npz) "
+                         "instead of measuring one")
     args = ap.parse_args(argv)
+    if args.data:
+        return train_only(args)
 
     specs = [problem_spec(i) for i in range(args.problems)]
     ctx = mp.get_context("spawn")
@@ -184,6 +198,9 @@ def main(argv=None):
     X = np.concatenate([F, R[:, 0:3]], axis=1).astype(np.float32)
     T = R[:, 3].astype(np.float32)
     owner = np.array(owner)
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.savez(os.path.splitext(args.out)[0] + ".data.npz", X=X, T=T, owner=owner, rows=R,
+             plain=np.array(plain))
     perm = np.random.default_rng(11).permutation(len(plain))
     val_p = set(perm[:max(1, len(plain) // 10)].tolist())
     val_idx = np.array([i for i in range(len(T)) if owner[i] in val_p], dtype=np.int64)
@@ -207,6 +224,30 @@ def main(argv=None):
     with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
         json.dump(summary, fh, indent=1)
     print(json.dumps({k: v for k, v in summary.items() if k != "history"}), flush=True)
+    print(json.dumps(hist[-1]), flush=True)
+
+
+def train_only(args):
+    """Retrain on a saved dataset (seconds on the GPU)."""
+    import torch
+    from . import binding as B
+    B.load_library()
+    d = np.load(args.data)
+    X, T, owner = d["X"], d["T"], d["owner"]
+    nprob = int(owner.max()) + 1
+    perm = np.random.default_rng(11).permutation(nprob)
+    val_p = np.zeros(nprob, dtype=bool)
+    val_p[perm[:max(1, nprob // 10)]] = True
+    val_idx = np.nonzero(val_p[owner])[0]
+    train_idx = np.nonzero(~val_p[owner])[0]
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch)
+    np.save(args.out, theta.astype(np.float32))
+    summary = {"data": os.path.basename(args.data), "samples": int(len(T)),
+               "train_samples": int(len(train_idx)), "val_samples": int(len(val_idx)),
+               "steps": args.steps, "lr": args.lr, "target_mean": float(T.mean()),
+               "target_std": float(T.std()), "history": hist, "train_s": train_s}
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
+        json.dump(summary, fh, indent=1)
     print(json.dumps(hist[-1]), flush=True)
 
 
