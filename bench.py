@@ -360,10 +360,11 @@ def run_profile(args):
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
     for prec in (B.AMG_FP32, B.AMG_FP64):
-        # the launch configuration the bench selects (one launch per operation with
-        # programmatic dependent launch), without graph replay so that a profiler
-        # sees every kernel
-        opts = B.default_options(precision=prec, cycle_kernel=1, cluster_from=0, use_graphs=0)
+        # the launch configuration the bench's setup selects (given explicitly: timing
+        # under a profiler would choose differently), without graph replay so that a
+        # profiler sees every kernel
+        opts = B.default_options(precision=prec, cycle_kernel=args.cycle_kernel,
+                                 cluster_from=args.cluster_from, use_graphs=0)
         h = B.setup_problem(prob, opts, stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)
@@ -542,6 +543,10 @@ def main():
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--profile", action="store_true",
                     help="setup, then exactly one FP32-cycle solve and one FP64 solve (for ncu)")
+    ap.add_argument("--cluster-from", type=int, default=0,
+                    help="profile: cluster sub-cycle start level (the bench's choice)")
+    ap.add_argument("--cycle-kernel", type=int, default=1,
+                    help="profile: 1 per-operation launches, 2 persistent cycle")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
