@@ -452,7 +452,7 @@ int amg_get_weights(const amg_handle* h, double* w, int32_t capacity);
  * grid ws in [AMG_WS_MIN, AMG_WS_MAX] (AMG_GRID_NWS points) x wc (AMG_GRID_NWC)
  * x log2 wp (AMG_GRID_NWP, saddle kinds; wp = 1 otherwise), then two probe
  * solves of K x = K y (y pseudo-random, zero on Dirichlet nodes) to a relative
- * residual of 1e-4 with the plain and with the chosen weights; the chosen
+ * residual of 1e-8 with the plain and with the chosen weights; the chosen
  * weights stay only if their factor rel_residual^(1/iterations) is smaller.
  * out receives the decision.  Later amg_solve calls use the weights in place.
  */

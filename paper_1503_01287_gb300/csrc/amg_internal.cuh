@@ -268,7 +268,7 @@ int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stat
 void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
 
 // learned.cu: statistics of the hierarchy, weights, selection with fallback
-constexpr double kProbeTol = 1e-4;
+constexpr double kProbeTol = 1e-8;   // the probe solves run to the stopping tolerance of the workloads
 void compute_features(amg_handle* h, double* out);
 void set_weights(amg_handle* h, const double* w3);
 void get_weights(const amg_handle* h, double* out);

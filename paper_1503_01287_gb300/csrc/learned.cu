@@ -209,7 +209,7 @@ void get_weights(const amg_handle* h, double* out) {
 }
 
 // Convergence factor of a short solve: rel_residual^(1/iterations) of the
-// handle's Krylov method on b = K y (y a fixed pseudo-random vector) to 1e-4.
+// handle's Krylov method on b = K y (y a fixed pseudo-random vector) to 1e-8.
 double probe_rate(amg_handle* h, DBuf<double>& b, DBuf<double>& x, int* iters) {
   amg_stats st{};
   AMG_CUDA(cudaMemsetAsync(x.p, 0, x.bytes(), h->stream));
