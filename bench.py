@@ -470,6 +470,66 @@ def run_replay(args):
     print(json.dumps(out), flush=True)
 
 
+def run_mixed(args):
+    """Mixed displacement-pressure elasticity on jittered 40^3 cubes, nu in {0.49, 0.499,
+    0.4999}: the chosen solve (FP32 cycle, sGS smoother with the weights that the
+    trained network selects, measured fallback included, FGMRES(300)) against the plain
+    FP64 solve (sGS, FGMRES(300)), both to 1e-8.  value = DOF of the three systems over
+    the summed solve times (CUDA events of amg_solve); setup and weight selection are
+    reported beside it."""
+    import torch
+    import __graft_entry__ as ge
+    from fem_inputs.configs import CONFIGS, make_config
+    ge.build()
+    from paper_1503_01287_gb300 import binding as B
+    theta = np.load(os.path.join(ROOT, "paper_1503_01287_gb300", "weights", "mlp_theta.npy"))
+    cfg = CONFIGS["mixed_elast_n40"]
+    t0 = time.time()
+    probs = make_config("mixed_elast_n40", n=args.n_mixed)
+    gen_s = time.time() - t0
+    rows = []
+    tot = {"dofs": 0, "chosen_ms": 0.0, "plain_ms": 0.0}
+    for prob in probs:
+        b = torch.from_numpy(prob.rhs()).cuda()
+        x = torch.zeros_like(b)
+        t1 = time.time()
+        ch = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
+                                                     gmres_restart=cfg["gmres_restart"],
+                                                     max_iterations=1000))
+        res = ch.learn_weights(theta)
+        setup_learn_s = time.time() - t1
+        pl = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64,
+                                                     gmres_restart=cfg["gmres_restart"],
+                                                     max_iterations=1000))
+        out = {}
+        for name, h in (("chosen", ch), ("plain_fp64", pl)):
+            for _ in range(max(1, args.warmup)):
+                x.zero_()
+                h.solve(b, x, cfg["tol"], device_ptrs=True)
+            ms, st = [], None
+            for _ in range(max(1, args.steps)):
+                x.zero_()
+                st = h.solve(b, x, cfg["tol"], device_ptrs=True)
+                ms.append(st.solve_ms)
+            out[name] = {"iterations": st.iterations, "converged": bool(st.converged),
+                         "true_rel_residual": st.true_rel_residual,
+                         "ms": float(np.median(ms))}
+            h.free()
+        rows.append({"nu": prob.params["nu"], "dofs": prob.n_dof, **out,
+                     "weights": list(res.weights), "fell_back": res.fell_back,
+                     "setup_and_selection_s": setup_learn_s})
+        tot["dofs"] += prob.n_dof
+        tot["chosen_ms"] += out["chosen"]["ms"]
+        tot["plain_ms"] += out["plain_fp64"]["ms"]
+    line = {"metric": "DOF/s solved to 1e-8 rel. residual, mixed elasticity 40^3 P2/P1, "
+                      "nu in {0.49, 0.499, 0.4999}: learned weights + FP32 cycle, FGMRES(300)",
+            "value": tot["dofs"] / (tot["chosen_ms"] * 1e-3), "unit": "DOF/s",
+            "plain_fp64_value": tot["dofs"] / (tot["plain_ms"] * 1e-3),
+            "config": {"workload": f"mixed_elast_n{args.n_mixed}", "tol": cfg["tol"]},
+            "rows": rows, "generate_s": gen_s}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """64 uneven elasticity problems x 16 right-hand sides in one amg_solve_batched
     launch (box meshes n ~ U{8..24}, side lengths ~ U[1,4], nu ~ U[0.2,0.45],
@@ -536,7 +596,8 @@ def main():
     ap.add_argument("--no-mesh", action="store_true",
                     help="skip the iteration-count-versus-mesh-size study")
     ap.add_argument("--workload", default="elasticity",
-                    choices=["elasticity", "batched", "replay"])
+                    choices=["elasticity", "batched", "replay", "mixed"])
+    ap.add_argument("--n-mixed", type=int, default=40, help="mixed: cubes per side")
     ap.add_argument("--replay-levels", type=int, default=4,
                     help="replay: levels L1.. of the paper's tables (4^3, 8^3, 16^3, 32^3)")
     ap.add_argument("--batch", type=int, default=64)
@@ -558,6 +619,8 @@ def main():
         return run_batched(args)
     if args.workload == "replay":
         return run_replay(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
