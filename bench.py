@@ -446,10 +446,6 @@ def run_replay(args):
         b = torch.from_numpy(prob.rhs()).cuda()
         for sm_name, sm in (("sGS", B.AMG_SMOOTHER_SGS), ("BS", B.AMG_SMOOTHER_BS),
                             ("Vanka", B.AMG_SMOOTHER_VANKA)):
-            if sm_name == "Vanka" and n > 8:
-                # the patch inverses are formed by Gauss-Jordan in global memory, which
-                # costs O(m^3) L2 traffic per patch: the replay stops at 8^3
-                continue
             runs = [] if sm_name == "Vanka" else [
                 ("amg", f"{m}-{m}", dict(m_pre=m, m_post=m, krylov=B.AMG_KRYLOV_NONE,
                                          max_iterations=300)) for m in (1, 2)]

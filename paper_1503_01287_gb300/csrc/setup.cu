@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "amg_internal.cuh"
@@ -1383,6 +1384,8 @@ void bs_setup(amg_handle* h) {
 constexpr int kVankaMax = 512;   // unknowns of a patch (the cycle kernel's register tile)
 constexpr int kVankaSmem = 237;  // patches factorised in shared memory: m (m + 1) / 2 + m
                                  // doubles within 227 KB
+constexpr int kVkCl = 8;         // CTAs of the cluster that inverts larger patches
+constexpr int kVankaCluster = 470;   // ceil(m / 8) m + m doubles within 227 KB a CTA
 
 __device__ __forceinline__ int find_col(const int* __restrict__ col, int a, int e, int j) {
   while (a < e) {
@@ -1425,7 +1428,7 @@ __global__ void k_vk_invert(int np, const int* __restrict__ brow,
   double* rowk = colk + kVankaMax;                     // row k after scaling
   for (int p = blockIdx.x; p < np; p += gridDim.x) {
     const int m = 3 * (brow[p + 1] - brow[p]);
-    if (m <= kVankaSmem) continue;     // done by k_vk_chol
+    if (m <= kVankaCluster) continue;  // done by k_vk_chol or k_vk_gj_cluster
     double* M = ainv + off[p];
     bool bad = false;
     for (int k = 0; k < m && !bad; ++k) {
@@ -1524,6 +1527,72 @@ __global__ void __launch_bounds__(512) k_vk_chol(int np, const int* __restrict__
   }
 }
 
+// Patches above kVankaSmem and up to kVankaCluster unknowns: Gauss-Jordan inversion
+// with the matrix spread over the shared memory of an 8-CTA thread-block cluster
+// (CTA r holds rows [r R, (r + 1) R), R = ceil(m / 8)).  Step k: the owner of row k
+// scales it; every CTA copies it through distributed shared memory and eliminates
+// column k from its own rows.  No pivoting (A_k is SPD); a non-positive pivot sets
+// *flag and leaves the patch.
+__global__ void __launch_bounds__(1024, 1) k_vk_gj_cluster(int np, const int* __restrict__ brow,
+                                                          const long long* __restrict__ off,
+                                                          double* __restrict__ ainv, int* flag) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  extern __shared__ int vk_sh[];
+  double* loc = reinterpret_cast<double*>(vk_sh);
+  __shared__ double fcol[64];
+  __shared__ int bad;
+  const unsigned rank = cl.block_rank();
+  const int ncl = gridDim.x / kVkCl, cid = blockIdx.x / kVkCl;
+  for (int p = cid; p < np; p += ncl) {
+    const int m = 3 * (brow[p + 1] - brow[p]);
+    if (m <= kVankaSmem || m > kVankaCluster) continue;
+    const int R = (m + kVkCl - 1) / kVkCl;
+    const int r0 = (int)rank * R, r1 = min(m, r0 + R), nr = max(0, r1 - r0);
+    double* rowk = loc + (size_t)R * m;        // m doubles after the owned rows
+    double* M = ainv + off[p];
+    for (int t = threadIdx.x; t < nr * m; t += blockDim.x)
+      loc[t] = M[(int64_t)(r0 + t / m) * m + t % m];
+    if (threadIdx.x == 0) bad = 0;
+    cl.sync();
+    for (int k = 0; k < m; ++k) {
+      const unsigned owner = (unsigned)(k / R);
+      if (rank == owner) {
+        double* rk = loc + (size_t)(k - r0) * m;
+        const double piv = rk[k];
+        __syncthreads();
+        if (!(piv > 0.0)) {
+          if (threadIdx.x == 0) bad = 1;
+        } else {
+          for (int j = threadIdx.x; j < m; j += blockDim.x) rk[j] = (j == k ? 1.0 : rk[j]) / piv;
+        }
+      }
+      cl.sync();
+      const double* src = cl.map_shared_rank(loc, owner) + (size_t)(k - (int)owner * R) * m;
+      const int obad = *cl.map_shared_rank(&bad, owner);
+      for (int j = threadIdx.x; j < m; j += blockDim.x) rowk[j] = src[j];
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) fcol[i] = loc[(size_t)i * m + k];
+      __syncthreads();
+      if (!obad) {
+        for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
+          const int i = t / m, j = t % m;
+          if (r0 + i == k) continue;
+          const double base = j == k ? 0.0 : loc[t];
+          loc[t] = base - fcol[i] * rowk[j];
+        }
+      }
+      cl.sync();
+      if (obad) {
+        if (threadIdx.x == 0 && rank == 0) atomicOr(flag, 2);
+        break;
+      }
+    }
+    for (int t = threadIdx.x; t < nr * m; t += blockDim.x)
+      M[(int64_t)(r0 + t / m) * m + t % m] = loc[t];
+    cl.sync();
+  }
+}
+
 // w_k = A_k^{-1} B_k^T, s_k = B_k w_k + C_kk
 __global__ void k_vk_ws(int np, const int* __restrict__ brow, const double* __restrict__ bval,
                         int64_t bnnz, const int* __restrict__ crow,
@@ -1618,6 +1687,36 @@ void vanka_setup(amg_handle* h) {
                                                                        h->flag);
     AMG_LAUNCH_CHECK();
     if (mmax > kVankaSmem) {
+      const int mc = std::min(mmax, kVankaCluster);
+      const int Rc = (mc + kVkCl - 1) / kVkCl;
+      const size_t cl_shm = ((size_t)Rc * mc + mc) * sizeof(double);
+      static bool cl_attr = false;
+      if (!cl_attr) {
+        const int Rmax = (kVankaCluster + kVkCl - 1) / kVkCl;
+        AMG_CUDA(cudaFuncSetAttribute(k_vk_gj_cluster,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(((size_t)Rmax * kVankaCluster + kVankaCluster) *
+                                            sizeof(double))));
+        cl_attr = true;
+      }
+      cudaLaunchConfig_t cfg{};
+      const int nclusters = std::max(1, std::min(np, 152 / kVkCl));
+      cfg.gridDim = dim3((unsigned)(nclusters * kVkCl));
+      cfg.blockDim = dim3(1024);
+      cfg.dynamicSmemBytes = cl_shm;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kVkCl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      AMG_CUDA(cudaLaunchKernelEx(&cfg, k_vk_gj_cluster, np, (const int*)lv.b_rowptr.p,
+                                  (const long long*)lv.vk_off.p, lv.vk_ainv.p, h->flag.p));
+      h->launches++;
+    }
+    if (mmax > kVankaCluster) {
       k_vk_invert<<<grid, 256, 2 * kVankaMax * sizeof(double), s>>>(np, lv.b_rowptr, lv.vk_off,
                                                                     lv.vk_ainv, h->flag);
       AMG_LAUNCH_CHECK();
