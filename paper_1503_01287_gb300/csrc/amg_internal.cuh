@@ -147,6 +147,8 @@ struct Level {
   DBuf<float> vk_ainv32, vk_w32, vk_s32;
   DBuf<int> vk_colour, vk_rows;
   std::vector<int> vk_colour_ptr;
+  DBuf<int> vk_cnodes;             // velocity nodes of the patches, colour by colour
+  std::vector<int> vk_cnode_ptr;
   int vk_ncolours = 0;
   int vk_mmax = 0;
   int64_t h_nnz = 0;

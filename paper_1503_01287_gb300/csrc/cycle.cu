@@ -692,6 +692,66 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
                               (const T*)P.dinv, P.wt));
 }
 
+// Residual r = b - K x restricted to the unknowns of one Vanka colour: the velocity
+// nodes of its patches (warp per node, one block of the node's A row and one entry
+// of its B^T row per lane and step) and the pressure unknowns of its patches (the
+// last npres warps' work).  Reads x only, so every patch of the colour then sees the
+// residual of the colour's start.
+template <typename T>
+__global__ void __launch_bounds__(256) k_vk_resid(
+    int nnodes, const int* __restrict__ nodes, int npres, const int* __restrict__ pres,
+    const int* __restrict__ rowptr, const int* __restrict__ col, const T* __restrict__ val,
+    int64_t nnzb, const int* __restrict__ btrow, const int* __restrict__ btcol,
+    const T* __restrict__ btval, const int* __restrict__ brow, const int* __restrict__ bcol,
+    const T* __restrict__ bval, int64_t bnnz, const int* __restrict__ crow,
+    const int* __restrict__ ccol, const T* __restrict__ cval, const T* x, const T* b, T* r,
+    int n4) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nnodes + npres; w += nwarps) {
+    if (w < nnodes) {
+      const int i = nodes[w];
+      T s0 = T(0), s1 = T(0), s2 = T(0);
+      for (int k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) {
+        T x0, x1, x2;
+        ld3(x, col[k], x0, x1, x2);
+        s0 = fma(val[k], x0, fma(val[nnzb + k], x1, fma(val[2 * nnzb + k], x2, s0)));
+        s1 = fma(val[3 * nnzb + k], x0, fma(val[4 * nnzb + k], x1, fma(val[5 * nnzb + k], x2, s1)));
+        s2 = fma(val[6 * nnzb + k], x0, fma(val[7 * nnzb + k], x1, fma(val[8 * nnzb + k], x2, s2)));
+      }
+      for (int q = btrow[i] + lane; q < btrow[i + 1]; q += 32) {
+        const T pk = x[n4 + btcol[q]];
+        s0 = fma(btval[q], pk, s0);
+        s1 = fma(btval[bnnz + q], pk, s1);
+        s2 = fma(btval[2 * bnnz + q], pk, s2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      }
+      if (lane == 0) {
+        T b0, b1, b2;
+        ld3(b, i, b0, b1, b2);
+        st3(r, i, b0 - s0, b1 - s1, b2 - s2);
+      }
+    } else {
+      const int k = pres[w - nnodes];
+      T acc = T(0);
+      for (int q = brow[k] + lane; q < brow[k + 1]; q += 32) {
+        T u0, u1, u2;
+        ld3(x, bcol[q], u0, u1, u2);
+        acc = fma(bval[q], u0, fma(bval[bnnz + q], u1, fma(bval[2 * bnnz + q], u2, acc)));
+      }
+      for (int q = crow[k] + lane; q < crow[k + 1]; q += 32) acc -= cval[q] * x[n4 + ccol[q]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) r[n4 + k] = b[n4 + k] - acc;
+    }
+  }
+}
+
 // the Vanka patch phase as its own kernel (its register tile stays out of the
 // generic phase kernels; the Vanka smoother runs with per-operation launches)
 template <typename T>
@@ -980,6 +1040,18 @@ struct Emit {
     P.mode = mode; P.n = (int)n; P.dinv = d; P.x = x; P.b = b; P.omega = (double)omega; P.y = y;
     put(P, n);
   }
+  void vanka_resid(Level& lv, int c, const T* x, const T* b, T* r) {
+    if (rec) fail(AMG_ERR_UNSUPPORTED, "the Vanka smoother runs with per-operation launches");
+    const int a = lv.vk_colour_ptr[c], np = lv.vk_colour_ptr[c + 1] - a;
+    const int na = lv.vk_cnode_ptr[c], nn = lv.vk_cnode_ptr[c + 1] - na;
+    if (nn + np <= 0) return;
+    k_vk_resid<T><<<gridn((int64_t)(nn + np) * 32), 256, 0, h->stream>>>(
+        nn, lv.vk_cnodes.p + na, np, lv.vk_rows.p + a, lv.rowptr, lv.col, LvVec<T>::val(lv),
+        lv.nnzb, lv.bt_rowptr, lv.bt_col, LvVec<T>::btval(lv), lv.b_rowptr, lv.b_col,
+        LvVec<T>::bval(lv), lv.b_nnz, lv.c_rowptr, lv.c_col, LvVec<T>::cval(lv), x, b, r,
+        4 * lv.n);
+    h->launches++;
+  }
   void vanka(Level& lv, int c, const T* r, T* x) {
     if (rec) fail(AMG_ERR_UNSUPPORTED, "the Vanka smoother runs with per-operation launches");
     Phase P = blank(PH_VANKA);
@@ -1090,11 +1162,12 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
     return;
   }
   if (h->saddle && h->opt.smoother == AMG_SMOOTHER_VANKA) {
-    // multiplicative over the patch colours: the residual of the level before each
+    // multiplicative over the patch colours: the residual at the colour's unknowns
+    // before each
     T* r = LvVec<T>::r(lv);
     for (int q = 0; q < lv.vk_ncolours; ++q) {
       const int c = post ? lv.vk_ncolours - 1 - q : q;
-      e_residual<T>(e, lv, x, b, r, true);
+      e.vanka_resid(lv, c, x, b, r);     // the residual at the colour's unknowns
       e.vanka(lv, c, r, x);
     }
     return;

@@ -1750,6 +1750,26 @@ void vanka_setup(amg_handle* h) {
     galerkin<1>(h, np, np, lv.b_rowptr, lv.b_col, ones, irow, icol, ival, lv.n, trow, tcol, tval,
                 orow, ocol, oval);
     colour_graph(h, np, orow, ocol, lv.vk_colour, lv.vk_ncolours, lv.vk_colour_ptr, lv.vk_rows);
+    // velocity nodes of every colour's patches (disjoint within a colour)
+    std::vector<int> rows_h(std::max(np, 1)), bcol_h(std::max<int64_t>(lv.b_nnz, 1));
+    AMG_CUDA(cudaMemcpyAsync(rows_h.data(), lv.vk_rows.p, np * sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaMemcpyAsync(bcol_h.data(), lv.b_col.p, lv.b_nnz * sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> cn;
+    cn.reserve(lv.b_nnz);
+    lv.vk_cnode_ptr.assign(lv.vk_ncolours + 1, 0);
+    for (int c = 0; c < lv.vk_ncolours; ++c) {
+      for (int t = lv.vk_colour_ptr[c]; t < lv.vk_colour_ptr[c + 1]; ++t) {
+        const int k = rows_h[t];
+        for (int q = br[k]; q < br[k + 1]; ++q) cn.push_back(bcol_h[q]);
+      }
+      lv.vk_cnode_ptr[c + 1] = (int)cn.size();
+    }
+    lv.vk_cnodes.alloc(std::max<size_t>(cn.size(), 1));
+    AMG_CUDA(cudaMemcpyAsync(lv.vk_cnodes.p, cn.data(), cn.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
     AMG_CUDA(cudaStreamSynchronize(s));
   }
 }
