@@ -439,6 +439,23 @@ def run_replay(args):
                             "iterations": st.iterations if st.converged else None,
                             "solve_ms": st.solve_ms,
                             "paper": PAPER_TABLES[(kind, method, nu)][sm_name][sizes.index(n)]})
+    # black-box comparison (Table 3): non-separating coarsening of the whole matrix
+    # graph, GS-1-1, two W-cycles per iteration; vector Laplacian, AMG and AMG-PCG
+    paper_t3 = {"amg": [90, 158, None, None], "pcg": [22, 25, 36, 64]}
+    for n in sizes:
+        prob = paper_setting_problem("laplace", n)
+        b = torch.from_numpy(prob.rhs()).cuda()
+        for method, kr in (("amg", B.AMG_KRYLOV_NONE), ("pcg", B.AMG_KRYLOV_PCG)):
+            h = B.setup_problem(prob, B.default_options(
+                separate=0, nu=2, cycles=2, krylov=kr, max_iterations=200))
+            x = torch.zeros_like(b)
+            st = h.solve(b, x, 1e-11, device_ptrs=True)
+            h.free()
+            out["rows"].append({
+                "kind": "laplace", "method": method, "cycle": "2W", "smoother": "GS-1-1",
+                "setting": "non-separating", "n": n, "dofs": prob.n_dof,
+                "iterations": st.iterations if st.converged else None,
+                "solve_ms": st.solve_ms, "paper": paper_t3[method][sizes.index(n)]})
     # mixed elasticity (Sec. 4.4): stand-alone AMG with m-m smoothing steps and FGMRES
     # with 1 or 2 V-cycles per preconditioner, sGS and Braess-Sarazin smoothers
     for n in sizes:
@@ -470,7 +487,8 @@ def run_mixed(args):
     """Mixed displacement-pressure elasticity on jittered 40^3 cubes, nu in {0.49, 0.499,
     0.4999}: the chosen solve (FP32 cycle, sGS smoother with the weights that the
     trained network selects, measured fallback included, FGMRES(300)) against the plain
-    FP64 solve (sGS, FGMRES(300)), both to 1e-8.  value = DOF of the three systems over
+    FP64 solve (sGS, FGMRES(300)), both to 1e-8; the Braess-Sarazin smoother with the
+    FP32 cycle beside them.  value = DOF of the three systems over
     the summed solve times (CUDA events of amg_solve); setup and weight selection are
     reported beside it."""
     import torch
@@ -497,8 +515,12 @@ def run_mixed(args):
         pl = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64,
                                                      gmres_restart=cfg["gmres_restart"],
                                                      max_iterations=1000))
+        bs = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
+                                                     smoother=B.AMG_SMOOTHER_BS,
+                                                     gmres_restart=cfg["gmres_restart"],
+                                                     max_iterations=1000))
         out = {}
-        for name, h in (("chosen", ch), ("plain_fp64", pl)):
+        for name, h in (("chosen", ch), ("plain_fp64", pl), ("braess_sarazin_fp32", bs)):
             for _ in range(max(1, args.warmup)):
                 x.zero_()
                 h.solve(b, x, cfg["tol"], device_ptrs=True)
@@ -517,10 +539,12 @@ def run_mixed(args):
         tot["dofs"] += prob.n_dof
         tot["chosen_ms"] += out["chosen"]["ms"]
         tot["plain_ms"] += out["plain_fp64"]["ms"]
+        tot["bs_ms"] = tot.get("bs_ms", 0.0) + out["braess_sarazin_fp32"]["ms"]
     line = {"metric": "DOF/s solved to 1e-8 rel. residual, mixed elasticity 40^3 P2/P1, "
                       "nu in {0.49, 0.499, 0.4999}: learned weights + FP32 cycle, FGMRES(300)",
             "value": tot["dofs"] / (tot["chosen_ms"] * 1e-3), "unit": "DOF/s",
             "plain_fp64_value": tot["dofs"] / (tot["plain_ms"] * 1e-3),
+            "braess_sarazin_fp32_value": tot["dofs"] / (tot["bs_ms"] * 1e-3),
             "config": {"workload": f"mixed_elast_n{args.n_mixed}", "tol": cfg["tol"]},
             "rows": rows, "generate_s": gen_s}
     print(json.dumps(line), flush=True)
