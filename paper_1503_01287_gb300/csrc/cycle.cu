@@ -373,73 +373,80 @@ __device__ __forceinline__ void vec_body(int64_t n, const T* __restrict__ d, con
   }
 }
 
-// Vanka patch corrections of one colour (Eq. (locpatchsm)), one warp per patch k:
-// r_k gathered into registers (unknown j = lane + 32 q of the patch), y = A_k^{-1} r_u
-// (row by row, warp-reduced), dp = (B_k y - r_p) / s_k (0 when s_k = 0),
-// du = y - w_k dp, x_patch += omega du, p_k += omega dp.  Patches of one colour
-// share no unknown.
+// Vanka patch corrections of one colour (Eq. (locpatchsm)), one CTA of 256 threads
+// per patch k: every warp holds r_k in registers (unknown j = lane + 32 q of the
+// patch), the 8 warps share the rows of y = A_k^{-1} r_u (two rows in flight per
+// warp, warp-reduced, into shared memory), then dp = (B_k y - r_p) / s_k (0 when
+// s_k = 0), du = y - w_k dp, x_patch += omega du, p_k += omega dp.  Patches of one
+// colour share no unknown.
 constexpr int kVankaRegs = 16;   // 16 x 32 = 512 unknowns a patch
 
 template <typename T>
-__device__ __forceinline__ void vanka_body(int npatch, const int* __restrict__ patches,
-                                           const int* __restrict__ brow,
-                                           const int* __restrict__ bcol,
-                                           const T* __restrict__ bval, int64_t bnnz,
-                                           const long long* __restrict__ off,
-                                           const T* __restrict__ ainv,
-                                           const T* __restrict__ w, const T* __restrict__ sk,
-                                           const T* r, T* x, int n4, T omega, int warp,
-                                           int nwarps) {
-  const int lane = threadIdx.x & 31;
-  for (int t = warp; t < npatch; t += nwarps) {
+__global__ void __launch_bounds__(256) k_vanka(int npatch, const int* __restrict__ patches,
+                                               const int* __restrict__ brow,
+                                               const int* __restrict__ bcol,
+                                               const T* __restrict__ bval, int64_t bnnz,
+                                               const long long* __restrict__ off,
+                                               const T* __restrict__ ainv,
+                                               const T* __restrict__ w,
+                                               const T* __restrict__ sk, const T* r, T* x,
+                                               int n4, T omega) {
+  __shared__ T ysh[32 * kVankaRegs];
+  __shared__ T red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < npatch; t += gridDim.x) {
     const int k = patches[t];
     const int q0 = brow[k], m = 3 * (brow[k + 1] - q0);
-    T rj[kVankaRegs], yv[kVankaRegs];
+    T rj[kVankaRegs];
 #pragma unroll
     for (int q = 0; q < kVankaRegs; ++q) {
       const int j = lane + 32 * q;
       rj[q] = j < m ? r[4 * bcol[q0 + j / 3] + j % 3] : T(0);
-      yv[q] = T(0);
     }
     const T* Ai = ainv + off[k];
+    for (int i0 = 2 * warp; i0 < m; i0 += 16) {
+      const int i1 = i0 + 1;
+      const T* row0 = Ai + (int64_t)i0 * m;
+      const T* row1 = Ai + (int64_t)min(i1, m - 1) * m;
+      T p0 = T(0), p1 = T(0);
 #pragma unroll
-    for (int qb = 0; qb < kVankaRegs; ++qb) {
-      if (32 * qb >= m) break;
-      for (int ii = 0; ii < 32; ++ii) {
-        const int i = 32 * qb + ii;
-        if (i >= m) break;
-        const T* row = Ai + (int64_t)i * m;
-        T part = T(0);
-#pragma unroll
-        for (int q = 0; q < kVankaRegs; ++q) {
-          const int j = lane + 32 * q;
-          if (j < m) part = fma(row[j], rj[q], part);
+      for (int q = 0; q < kVankaRegs; ++q) {
+        const int j = lane + 32 * q;
+        if (j < m) {
+          p0 = fma(row0[j], rj[q], p0);
+          p1 = fma(row1[j], rj[q], p1);
         }
+      }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == ii) yv[qb] = part;
+      for (int o = 16; o > 0; o >>= 1) {
+        p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+      }
+      if (lane == 0) {
+        ysh[i0] = p0;
+        if (i1 < m) ysh[i1] = p1;
       }
     }
+    __syncthreads();
     T bd = T(0);
-#pragma unroll
-    for (int q = 0; q < kVankaRegs; ++q) {
-      const int j = lane + 32 * q;
-      if (j < m) bd = fma(bval[(j % 3) * bnnz + q0 + j / 3], yv[q], bd);
-    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+      bd = fma(bval[(j % 3) * bnnz + q0 + j / 3], ysh[j], bd);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bd += __shfl_xor_sync(0xffffffffu, bd, o);
-    const T s = sk[k];
-    const T dp = s != T(0) ? (bd - r[n4 + k]) / s : T(0);
-    const T* wk = w + 3 * (int64_t)q0;
+    if (lane == 0) red[warp] = bd;
+    __syncthreads();
+    T tot = T(0);
 #pragma unroll
-    for (int q = 0; q < kVankaRegs; ++q) {
-      const int j = lane + 32 * q;
-      if (j < m) {
-        const int dof = 4 * bcol[q0 + j / 3] + j % 3;
-        x[dof] += omega * (yv[q] - wk[j] * dp);
-      }
+    for (int q = 0; q < 8; ++q) tot += red[q];
+    const T s = sk[k];
+    const T dp = s != T(0) ? (tot - r[n4 + k]) / s : T(0);
+    const T* wk = w + 3 * (int64_t)q0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const int dof = 4 * bcol[q0 + j / 3] + j % 3;
+      x[dof] += omega * (ysh[j] - wk[j] * dp);
     }
-    if (lane == 0) x[n4 + k] += omega * dp;
+    if (threadIdx.x == 0) x[n4 + k] += omega * dp;
+    __syncthreads();
   }
 }
 
@@ -752,15 +759,6 @@ __global__ void __launch_bounds__(256) k_vk_resid(
   }
 }
 
-// the Vanka patch phase as its own kernel (its register tile stays out of the
-// generic phase kernels; the Vanka smoother runs with per-operation launches)
-template <typename T>
-__global__ void __launch_bounds__(256) k_vanka(const Phase P) {
-  vanka_body<T>(P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz, P.off, (const T*)P.dinv,
-                (const T*)P.cval, (const T*)P.sd, (const T*)P.x, (T*)P.y, P.n3, (T)P.omega,
-                (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
-}
-
 // one operation as its own kernel
 template <typename T>
 __global__ void __launch_bounds__(256) k_phase(const Phase P) {
@@ -977,7 +975,10 @@ struct Emit {
     }
     if (work <= 0) return;
     if (P.type == PH_ROWS) launch_rows<T>(P, h->stream, h->use_pdl);
-    else if (P.type == PH_VANKA) k_vanka<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
+    else if (P.type == PH_VANKA)
+      k_vanka<T><<<(unsigned)std::min<int64_t>(work, 152 * 8), 256, 0, h->stream>>>(
+          P.n, P.rows, P.rowptr, P.col, (const T*)P.val, P.nnz, P.off, (const T*)P.dinv,
+          (const T*)P.cval, (const T*)P.sd, (const T*)P.x, (T*)P.y, P.n3, (T)P.omega);
     else k_phase<T><<<gridn(work * threads_per_item), 256, 0, h->stream>>>(P);
     h->launches++;
   }
