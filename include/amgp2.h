@@ -150,7 +150,9 @@ typedef struct amg_options {
   int32_t cycle_kernel;     /* 0: chosen by timing at setup (default); 1: one
                                launch per operation (with the cluster levels);
                                2: the whole cycle as one persistent cooperative
-                               launch with grid barriers                       */
+                               launch with grid barriers.  With the Vanka
+                               smoother both are forced to per-operation
+                               launches (cluster_from 0, cycle_kernel 1)        */
   double omega;             /* block Jacobi damping (default 0.5)               */
   double omega_p;           /* sGS pressure step omega (default 0.125)          */
 } amg_options;
