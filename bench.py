@@ -177,6 +177,15 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32), stream=sptr)
     setup_chosen_ms = 1e3 * (time.perf_counter() - t0)
+    # the learned weights: selection by the trained network, measured fallback included
+    learned = None
+    if not args.no_learned:
+        t0 = time.perf_counter()
+        theta = np.load(os.path.join(ROOT, "paper_1503_01287_gb300", "weights", "mlp_theta.npy"))
+        res = chosen.learn_weights(theta)
+        learned = {"weights": list(res.weights), "fell_back": res.fell_back,
+                   "rho_plain": res.rho_plain, "rho_learned": res.rho_learned,
+                   "selection_ms": 1e3 * (time.perf_counter() - t0)}
     t0 = time.perf_counter()
     plain = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64), stream=sptr)
     setup_plain_ms = 1e3 * (time.perf_counter() - t0)
@@ -316,6 +325,7 @@ def run_gpu(args, rank, world):
         "iterations": stats[-1]["iterations"],
         "true_rel_residual": true_rel,
         "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
+        "learned_weights": learned,
         "iterations_vs_mesh": mesh,
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
                    "colours": stats[-1]["level_colours"],
@@ -613,6 +623,8 @@ def main():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--ref-n", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="chosen solve without the learned-weights selection")
     ap.add_argument("--no-mesh", action="store_true",
                     help="skip the iteration-count-versus-mesh-size study")
     ap.add_argument("--workload", default="elasticity",
