@@ -56,7 +56,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $BENCH_OUT_DIR (default bench_out/ beside this file)
+        out = os.environ.get("BENCH_OUT_DIR", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
