@@ -502,16 +502,22 @@ def run_mixed(args):
     FP64 solve (sGS, FGMRES(300)), both to 1e-8; the Braess-Sarazin smoother with the
     FP32 cycle beside them.  value = DOF of the three systems over
     the summed solve times (CUDA events of amg_solve); setup and weight selection are
-    reported beside it."""
+    reported beside it.  --workload stokes runs the same comparison on the lid-driven
+    Stokes problem (24^3, Taylor-Hood)."""
     import torch
     import __graft_entry__ as ge
     from fem_inputs.configs import CONFIGS, make_config
     ge.build()
     from paper_1503_01287_gb300 import binding as B
     theta = np.load(os.path.join(ROOT, "paper_1503_01287_gb300", "weights", "mlp_theta.npy"))
-    cfg = CONFIGS["mixed_elast_n40"]
+    stokes = args.workload == "stokes"
+    name = "stokes_lid_n24" if stokes else "mixed_elast_n40"
+    cfg = dict(CONFIGS[name])
+    cfg.setdefault("gmres_restart", 300)
     t0 = time.time()
-    probs = make_config("mixed_elast_n40", n=args.n_mixed)
+    probs = make_config(name, n=args.n_mixed if not stokes else None)
+    if stokes:
+        probs = [probs]
     gen_s = time.time() - t0
     rows = []
     tot = {"dofs": 0, "chosen_ms": 0.0, "plain_ms": 0.0}
@@ -545,19 +551,22 @@ def run_mixed(args):
                          "true_rel_residual": st.true_rel_residual,
                          "ms": float(np.median(ms))}
             h.free()
-        rows.append({"nu": prob.params["nu"], "dofs": prob.n_dof, **out,
+        rows.append({"nu": prob.params.get("nu"), "dofs": prob.n_dof, **out,
                      "weights": list(res.weights), "fell_back": res.fell_back,
                      "setup_and_selection_s": setup_learn_s})
         tot["dofs"] += prob.n_dof
         tot["chosen_ms"] += out["chosen"]["ms"]
         tot["plain_ms"] += out["plain_fp64"]["ms"]
         tot["bs_ms"] = tot.get("bs_ms", 0.0) + out["braess_sarazin_fp32"]["ms"]
-    line = {"metric": "DOF/s solved to 1e-8 rel. residual, mixed elasticity 40^3 P2/P1, "
-                      "nu in {0.49, 0.499, 0.4999}: learned weights + FP32 cycle, FGMRES(300)",
+    line = {"metric": ("DOF/s solved to 1e-8 rel. residual, lid-driven Stokes 24^3 "
+                       "Taylor-Hood: learned weights + FP32 cycle, FGMRES(300)") if stokes else
+                      ("DOF/s solved to 1e-8 rel. residual, mixed elasticity 40^3 P2/P1, "
+                       "nu in {0.49, 0.499, 0.4999}: learned weights + FP32 cycle, FGMRES(300)"),
             "value": tot["dofs"] / (tot["chosen_ms"] * 1e-3), "unit": "DOF/s",
             "plain_fp64_value": tot["dofs"] / (tot["plain_ms"] * 1e-3),
             "braess_sarazin_fp32_value": tot["dofs"] / (tot["bs_ms"] * 1e-3),
-            "config": {"workload": f"mixed_elast_n{args.n_mixed}", "tol": cfg["tol"]},
+            "config": {"workload": name if stokes else f"mixed_elast_n{args.n_mixed}",
+                       "tol": cfg["tol"]},
             "rows": rows, "generate_s": gen_s}
     print(json.dumps(line), flush=True)
 
@@ -630,7 +639,7 @@ def main():
     ap.add_argument("--no-mesh", action="store_true",
                     help="skip the iteration-count-versus-mesh-size study")
     ap.add_argument("--workload", default="elasticity",
-                    choices=["elasticity", "batched", "replay", "mixed"])
+                    choices=["elasticity", "batched", "replay", "mixed", "stokes"])
     ap.add_argument("--n-mixed", type=int, default=40, help="mixed: cubes per side")
     ap.add_argument("--replay-levels", type=int, default=4,
                     help="replay: levels L1.. of the paper's tables (4^3, 8^3, 16^3, 32^3)")
@@ -653,7 +662,7 @@ def main():
         return run_batched(args)
     if args.workload == "replay":
         return run_replay(args)
-    if args.workload == "mixed":
+    if args.workload in ("mixed", "stokes"):
         return run_mixed(args)
     if world > 1:
         import torch.distributed as dist
