@@ -22,6 +22,8 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+// opt-in dynamic shared memory of a kernel, once per device
+void max_dynamic_smem(const void* func, int bytes);
 
 #define AMG_CUDA(x) ::amgp2::check_cuda((x), #x, __FILE__, __LINE__)
 #define AMG_LAUNCH_CHECK() ::amgp2::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)

@@ -5,6 +5,8 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
 
 #include <nvtx3/nvToolsExt.h>
@@ -25,6 +27,18 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(buf, sizeof buf, "%s failed at %s:%d: %s", what, file, line, cudaGetErrorString(e));
   cudaGetLastError();  // clear a sticky-free error so the handle stays usable
   throw Error{e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA, buf};
+}
+
+void max_dynamic_smem(const void* func, int bytes) {
+  // the attribute belongs to the current device's context: set once per (device, kernel)
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, func})) return;
+  AMG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({dev, func});
 }
 
 template <class F>

@@ -201,13 +201,8 @@ __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ grad
 constexpr size_t kSmem = sizeof(Smem);
 
 void set_smem() {
-  static bool done = false;
-  if (done) return;
-  AMG_CUDA(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmem));
-  AMG_CUDA(cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmem));
-  done = true;
+  max_dynamic_smem((const void*)k_mlp<true>, (int)kSmem);
+  max_dynamic_smem((const void*)k_mlp<false>, (int)kSmem);
 }
 
 }  // namespace

@@ -973,12 +973,8 @@ int64_t galerkin(amg_handle* h, int nc, int ncols_c, const DBuf<int>& rrow, cons
   (void)ncols_c;
   cudaStream_t s = h->stream;
   size_t shm = (size_t)kGalWarps * kHashSize * sizeof(int);
-  static bool attr = false;
-  if (!attr) {
-    AMG_CUDA(cudaFuncSetAttribute(k_gal_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    AMG_CUDA(cudaFuncSetAttribute(k_gal_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    attr = true;
-  }
+  max_dynamic_smem((const void*)k_gal_count, (int)shm);
+  max_dynamic_smem((const void*)k_gal_fill, (int)shm);
   DBuf<int> cnt;
   cnt.alloc(nc + 1);
   Flag f(h);
@@ -1675,13 +1671,8 @@ void vanka_setup(amg_handle* h) {
     f.reset();
     const int msm = std::min(mmax, kVankaSmem);
     const size_t chol_shm = (size_t)(msm * (msm + 1) / 2 + msm) * sizeof(double);
-    static bool chol_attr = false;
-    if (!chol_attr) {
-      AMG_CUDA(cudaFuncSetAttribute(k_vk_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((kVankaSmem * (kVankaSmem + 1) / 2 + kVankaSmem) *
-                                          sizeof(double))));
-      chol_attr = true;
-    }
+    max_dynamic_smem((const void*)k_vk_chol,
+                     (int)((kVankaSmem * (kVankaSmem + 1) / 2 + kVankaSmem) * sizeof(double)));
     k_vk_chol<<<std::max(1, std::min(np, 152 * 2)), 512, chol_shm, s>>>(np, lv.b_rowptr,
                                                                        lv.vk_off, lv.vk_ainv,
                                                                        h->flag);
@@ -1690,15 +1681,9 @@ void vanka_setup(amg_handle* h) {
       const int mc = std::min(mmax, kVankaCluster);
       const int Rc = (mc + kVkCl - 1) / kVkCl;
       const size_t cl_shm = ((size_t)Rc * mc + mc) * sizeof(double);
-      static bool cl_attr = false;
-      if (!cl_attr) {
-        const int Rmax = (kVankaCluster + kVkCl - 1) / kVkCl;
-        AMG_CUDA(cudaFuncSetAttribute(k_vk_gj_cluster,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(((size_t)Rmax * kVankaCluster + kVankaCluster) *
-                                            sizeof(double))));
-        cl_attr = true;
-      }
+      const int Rmax = (kVankaCluster + kVkCl - 1) / kVkCl;
+      max_dynamic_smem((const void*)k_vk_gj_cluster,
+                       (int)(((size_t)Rmax * kVankaCluster + kVankaCluster) * sizeof(double)));
       cudaLaunchConfig_t cfg{};
       const int nclusters = std::max(1, std::min(np, 152 / kVkCl));
       cfg.gridDim = dim3((unsigned)(nclusters * kVkCl));
