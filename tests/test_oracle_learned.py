@@ -97,3 +97,28 @@ def test_features_interpolation_statistics_by_matrix_products():
         assert f[12] == (1.0 if saddle else 0.0)
         if saddle:
             assert 0.0 < f[11] < 1.0
+
+
+def test_committed_training_data_and_network():
+    """The committed dataset of measured convergence factors and the network trained
+    on it: shapes, the target's definition (plain rows are 0, targets clipped to
+    [-1, 1]), the input layout (13 statistics, ws, wc, log2 wp), and the network's
+    FP64 forward pass fitting the validation problems better than predicting 0."""
+    import os
+    here = os.path.join(os.path.dirname(__file__), "..", "paper_1503_01287_gb300", "weights")
+    d = np.load(os.path.join(here, "mlp_theta.data.npz"))
+    X, T, owner = d["X"], d["T"], d["owner"]
+    assert X.shape == (14000, mlp.NI) and T.shape == (14000,)
+    assert np.all(np.abs(T) <= 1.0)
+    assert int(owner.max()) + 1 == 2000
+    plain = (X[:, 13] == 1.0) & (X[:, 14] == 1.0) & (X[:, 15] == 0.0)
+    assert plain.sum() >= 2000 and np.all(T[plain] == 0.0)
+    assert np.all((X[:, 12] == 0.0) | (X[:, 12] == 1.0))
+    theta = np.load(os.path.join(here, "mlp_theta.npy")).astype(np.float64)
+    assert theta.shape == (mlp.NPARAM,) and np.all(np.isfinite(theta))
+    # validation problems: the 10 % held out by the training script's permutation
+    perm = np.random.default_rng(11).permutation(2000)
+    val = np.isin(owner, perm[:200])
+    y, _ = mlp.forward(theta, X[val].astype(np.float64))
+    mse = np.mean((y - T[val]) ** 2)
+    assert mse < 0.5 * np.mean(T[val] ** 2), (mse, np.mean(T[val] ** 2))
