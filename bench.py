@@ -110,6 +110,7 @@ def oracle_sample(n_sample: int, steps: int, warmup: int):
     h = amg.build_hierarchy(prob)
     times = []
     its = None
+    res = None
     for k in range(warmup + steps):
         t0 = time.perf_counter()
         res, _ = amg.solve(prob, tol=TOL, h=h)
@@ -117,6 +118,7 @@ def oracle_sample(n_sample: int, steps: int, warmup: int):
         its = res.iterations
         if k >= warmup:
             times.append(dt)
+    oracle_sample.last_x = res.x
     return prob.n_dof, times, its
 
 
@@ -266,6 +268,7 @@ def run_gpu(args, rank, world):
     # iteration counts versus mesh size (the paper's mesh-independence study), after the
     # timed region: the same workload family at 4^3, 8^3, 16^3 and the timed size
     mesh = None
+    gpu_x_ref = {}
     if rank == 0 and not args.no_mesh:
         mesh = {"n": [], "dofs": [], "chosen_iterations": [], "chosen_ms": [],
                 "plain_fp64_iterations": [], "plain_fp64_ms": [],
@@ -284,6 +287,8 @@ def run_gpu(args, rank, world):
                 st = hh.solve(bb, xx, TOL, device_ptrs=True)
                 mesh[key + "_iterations"].append(st.iterations)
                 mesh[key + "_ms"].append(st.solve_ms)
+                if n == args.ref_n:
+                    gpu_x_ref[key] = xx.cpu().numpy()
                 hh.free()
         mesh["n"].append(args.n)
         mesh["dofs"].append(ndof)
@@ -303,8 +308,15 @@ def run_gpu(args, rank, world):
                 traffic = int(ln.split(":")[1])
 
     cpu = None
+    err_vs_oracle = None
     if rank == 0 and not args.no_cpu:
         ndof_s, times, its = oracle_sample(args.ref_n, 1, 0)
+        xo = oracle_sample.last_x
+        if gpu_x_ref:
+            # the GPU solutions of the same system (mesh study) against the FP64 oracle's
+            err_vs_oracle = {"n": args.ref_n, "relative_l2": {
+                k: float(np.linalg.norm(v - xo) / np.linalg.norm(xo))
+                for k, v in gpu_x_ref.items()}}
         cpu = {"value": ndof_s / times[0], "unit": "DOF/s", "cores": cpu_threads(),
                "kind": "oracle",
                "sample": f"FP64 AMG-PCG solve phase of elasticity {args.ref_n}^3 "
@@ -329,6 +341,7 @@ def run_gpu(args, rank, world):
         "setup_ms": {"chosen": setup_chosen_ms, "plain_fp64": setup_plain_ms},
         "learned_weights": learned,
         "iterations_vs_mesh": mesh,
+        "error_vs_oracle": err_vs_oracle,
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
                    "colours": stats[-1]["level_colours"],
                    "lanes_per_row": stats[-1]["level_group"],
