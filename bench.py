@@ -551,7 +551,7 @@ def run_mixed(args):
                                                      gmres_restart=cfg["gmres_restart"],
                                                      max_iterations=1000))
         out = {}
-        for name, h in (("chosen", ch), ("plain_fp64", pl), ("braess_sarazin_fp32", bs)):
+        for variant, h in (("chosen", ch), ("plain_fp64", pl), ("braess_sarazin_fp32", bs)):
             for _ in range(max(1, args.warmup)):
                 x.zero_()
                 h.solve(b, x, cfg["tol"], device_ptrs=True)
@@ -560,9 +560,9 @@ def run_mixed(args):
                 x.zero_()
                 st = h.solve(b, x, cfg["tol"], device_ptrs=True)
                 ms.append(st.solve_ms)
-            out[name] = {"iterations": st.iterations, "converged": bool(st.converged),
-                         "true_rel_residual": st.true_rel_residual,
-                         "ms": float(np.median(ms))}
+            out[variant] = {"iterations": st.iterations, "converged": bool(st.converged),
+                            "true_rel_residual": st.true_rel_residual,
+                            "ms": float(np.median(ms))}
             h.free()
         rows.append({"nu": prob.params.get("nu"), "dofs": prob.n_dof, **out,
                      "weights": list(res.weights), "fell_back": res.fell_back,
