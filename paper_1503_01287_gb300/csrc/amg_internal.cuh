@@ -223,8 +223,6 @@ struct amg_handle {
   amgp2::DBuf<double> mb, mx, mr, mz, mp, mq, mro, bred, bscal;
   amgp2::DBuf<int> bit;
   amgp2::DBuf<double> wts;          // 4 learned weights per level (see Level::wt)
-  double plain_rho = 0.0;           // convergence factor of the plain method (fallback)
-  bool learned = false;
   bool bf16_coarse = false;         // AMG_FP32_BF16: levels >= 1 keep BF16 values
   ~amg_handle();
 };

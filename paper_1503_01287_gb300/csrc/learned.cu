@@ -199,7 +199,6 @@ void set_weights(amg_handle* h, const double* w3) {
   AMG_CUDA(cudaMemcpyAsync(h->wts.p, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice,
                            h->stream));
   AMG_CUDA(cudaStreamSynchronize(h->stream));
-  h->learned = !(w3[0] == 1.0 && w3[1] == 1.0 && w3[2] == 1.0);
 }
 
 void get_weights(const amg_handle* h, double* out) {
@@ -293,7 +292,6 @@ void learn_weights(amg_handle* h, const float* theta_host, amg_learned* out) {
   }
   const double* wf = out->fell_back ? plain : chosen;
   for (int e = 0; e < 3; ++e) out->weights[e] = wf[e];
-  h->plain_rho = out->rho_plain;
 }
 
 }  // namespace amgp2
