@@ -20,7 +20,10 @@ target 0 by definition, so the plain method is the yardstick of every sample.
 Training.  Adam on the mean squared error with the amg_mlp_* kernels (BF16
 products, FP32 accumulation), full batch, problems split 90 / 10 into
 training and validation sets, learning rate divided by 10 over the last third;
-the parameters with the lowest validation error are kept.  They (float32,
+the parameters with the lowest validation selection regret are kept (per
+validation problem: how much worse the measured candidate the network ranks
+first is than the best measured one), since the selection uses the network's
+argmin, not its values.  They (float32,
 AMG_MLP_NPARAM) are written to --out, the measured dataset next to it as
 .data.npz (retrain with --data) and a summary (data, losses, timings) as .json.
 
@@ -108,8 +111,21 @@ def measure(prob, n_cand: int, rng: np.random.Generator, torch):
     return feats, rows, (rho_p, it_p, ms_p)
 
 
+def selection_regret(y: np.ndarray, T: np.ndarray, owner: np.ndarray) -> float:
+    """Mean over problems of T[argmin_k y_k] - min_k T_k over each problem's measured
+    candidates: how much slower the network's pick converges than the best measured
+    one (log10 of the factor ratio).  This is what the selection needs from the
+    network (its argmin), unlike the mean squared error over all candidates."""
+    order = np.argsort(owner, kind="stable")
+    o, yy, tt = owner[order], y[order], T[order]
+    starts = np.flatnonzero(np.r_[True, o[1:] != o[:-1]])
+    ends = np.r_[starts[1:], len(o)]
+    reg = [tt[a + int(np.argmin(yy[a:b]))] - tt[a:b].min() for a, b in zip(starts, ends)]
+    return float(np.mean(reg)) if reg else 0.0
+
+
 def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: float, seed: int,
-          torch):
+          torch, owner: np.ndarray | None = None):
     from . import binding as B
     rng = np.random.default_rng(seed)
     # He-scaled normal initialisation, zero biases (W1, b1, W2, b2, W3, b3)
@@ -125,6 +141,8 @@ def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: floa
     hist = []
     best, best_val = theta.clone(), float("inf")
     yv = torch.zeros(max(len(val_idx), 1), device="cuda")
+    Tv_h = T[val_idx]
+    ov = owner[val_idx] if owner is not None else None
     t0 = time.time()
     for step in range(1, steps + 1):
         # learning rate: constant, then divided by 10 over the last third
@@ -134,13 +152,19 @@ def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: floa
         if step % 100 == 0 or step == steps:
             B.mlp_forward(theta, Xv, yv)
             vl = float(((yv[:len(val_idx)] - Tv) ** 2).mean().item()) if len(val_idx) else 0.0
-            if vl < best_val:       # the parameters with the lowest validation error
-                best_val = vl
+            # keep the parameters whose argmin over each validation problem's measured
+            # candidates is best (selection regret); the MSE without problem ids
+            crit = (selection_regret(yv[:len(val_idx)].cpu().numpy(), Tv_h, ov)
+                    if ov is not None and len(val_idx) else vl)
+            if crit < best_val:
+                best_val = crit
                 best.copy_(theta)
             if step % 500 == 0 or step == steps:
-                hist.append({"step": step, "train_mse": loss.item(), "val_mse": vl})
+                hist.append({"step": step, "train_mse": loss.item(), "val_mse": vl,
+                             "val_regret": crit if ov is not None else None})
     torch.cuda.synchronize()
-    hist.append({"kept": "lowest validation error", "val_mse": best_val})
+    hist.append({"kept": "lowest validation selection regret" if owner is not None
+                 else "lowest validation error", "value": best_val})
     return best.cpu().numpy(), hist, time.time() - t0
 
 
@@ -205,7 +229,7 @@ def main(argv=None):
     val_p = set(perm[:max(1, len(plain) // 10)].tolist())
     val_idx = np.array([i for i in range(len(T)) if owner[i] in val_p], dtype=np.int64)
     train_idx = np.array([i for i in range(len(T)) if owner[i] not in val_p], dtype=np.int64)
-    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch)
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner)
 
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, theta.astype(np.float32))
@@ -240,7 +264,7 @@ def train_only(args):
     val_p[perm[:max(1, nprob // 10)]] = True
     val_idx = np.nonzero(val_p[owner])[0]
     train_idx = np.nonzero(~val_p[owner])[0]
-    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch)
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner)
     np.save(args.out, theta.astype(np.float32))
     summary = {"data": os.path.basename(args.data), "samples": int(len(T)),
                "train_samples": int(len(train_idx)), "val_samples": int(len(val_idx)),
