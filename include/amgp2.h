@@ -468,6 +468,10 @@ int amg_learn_weights(amg_handle* h, const float* theta, amg_learned* out);
  *   amg_mlp_gradient  grad = d/dtheta of loss, loss = sum_i (y_i - t_i)^2 / n
  *                     (grad: AMG_MLP_NPARAM floats, loss: 1 float, both
  *                     overwritten)
+ *   amg_mlp_backward  grad = sum_i dy[i] d y_i / d theta for per-sample upstream
+ *                     gradients dy (n floats; the gradient of any loss of the
+ *                     outputs, e.g. a ranking loss over each problem's
+ *                     candidates); grad is overwritten
  *   amg_mlp_adam      one Adam step (beta 0.9 / 0.999, eps 1e-8) of step
  *                     number `step` >= 1 with learning rate lr; m and v are
  *                     the moment buffers (zero before step 1)
@@ -475,6 +479,8 @@ int amg_learn_weights(amg_handle* h, const float* theta, amg_learned* out);
 int amg_mlp_forward(const float* theta, const float* x, int32_t n, float* y, void* stream);
 int amg_mlp_gradient(const float* theta, const float* x, const float* t, int32_t n, float* grad,
                      float* loss, void* stream);
+int amg_mlp_backward(const float* theta, const float* x, const float* dy, int32_t n,
+                     float* grad, void* stream);
 int amg_mlp_adam(float* theta, const float* grad, float* m, float* v, int32_t step, float lr,
                  void* stream);
 

@@ -56,12 +56,12 @@ def loss(theta: np.ndarray, X: np.ndarray, t: np.ndarray) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray, rnd=None) -> np.ndarray:
+def backward(theta: np.ndarray, X: np.ndarray, dy: np.ndarray, rnd=None) -> np.ndarray:
+    """Gradient of sum_i dy_i y_i(theta): back-propagation of per-sample upstream
+    gradients dy through the network."""
     r = rnd or _id
     p = unpack(theta)
     y, (X, z1, h1, z2, h2) = forward(theta, X, rnd)
-    B = len(t)
-    dy = 2.0 * (y - t) / B                      # dL/dy
     g = {"W3": h2.T @ dy, "b3": np.array([dy.sum()])}
     dz2 = np.outer(dy, p["W3"]) * (z2 > 0)
     g["W2"] = r(dz2).T @ r(h1)
@@ -70,6 +70,12 @@ def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray, rnd=None) -> np.ndarra
     g["W1"] = r(dz1).T @ r(X)
     g["b1"] = dz1.sum(axis=0)
     return pack(g)
+
+
+def grad(theta: np.ndarray, X: np.ndarray, t: np.ndarray, rnd=None) -> np.ndarray:
+    """Gradient of the mean squared error: dL/dy = 2 (y - t) / B, back-propagated."""
+    y, _ = forward(theta, X, rnd)
+    return backward(theta, X, 2.0 * (y - t) / len(t), rnd)
 
 
 def init(seed: int) -> np.ndarray:

@@ -43,7 +43,7 @@ EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_la
             "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
             "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc",
             "amg_features", "amg_set_weights", "amg_get_weights", "amg_learn_weights",
-            "amg_mlp_forward", "amg_mlp_gradient", "amg_mlp_adam"]
+            "amg_mlp_forward", "amg_mlp_gradient", "amg_mlp_adam", "amg_mlp_backward"]
 
 N_FEATURES = 13
 MLP_INPUTS = 16
@@ -173,6 +173,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_mlp_forward.restype = C.c_int
     lib.amg_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp, vp]
     lib.amg_mlp_gradient.restype = C.c_int
+    lib.amg_mlp_backward.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.amg_mlp_backward.restype = C.c_int
     lib.amg_mlp_adam.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp]
     lib.amg_mlp_adam.restype = C.c_int
     _lib = lib
@@ -372,6 +374,13 @@ def mlp_gradient(theta, x, t, grad, loss, stream=None):
     n = int(x.shape[0])
     _check(load_library().amg_mlp_gradient(_ptr(theta), _ptr(x), _ptr(t), n, _ptr(grad),
                                            _ptr(loss), stream))
+
+
+def mlp_backward(theta, x, dy, grad, stream=None):
+    """grad = sum_i dy[i] d net(x[i]) / d theta on device tensors (float32)."""
+    n = int(x.shape[0])
+    _check(load_library().amg_mlp_backward(_ptr(theta), _ptr(x), _ptr(dy), n, _ptr(grad),
+                                           stream))
 
 
 def mlp_adam(theta, grad, m, v, step: int, lr: float, stream=None):

@@ -283,6 +283,8 @@ void mlp_gradient(const float* theta, const float* X, const float* t, int n, flo
                   float* loss, cudaStream_t s);
 void mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr,
               cudaStream_t s);
+void mlp_backward(const float* theta, const float* X, const float* dy, int n, float* grad,
+                  cudaStream_t s);
 
 // batched.cu: all problems and right-hand sides in one graph launch
 int solve_batched(amg_handle* const* hs, int np, int nrhs, const double* const* B,

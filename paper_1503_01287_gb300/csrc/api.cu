@@ -627,6 +627,15 @@ int amg_mlp_gradient(const float* theta, const float* x, const float* t, int32_t
   });
 }
 
+int amg_mlp_backward(const float* theta, const float* x, const float* dy, int32_t n,
+                     float* grad, void* stream) {
+  return guarded(nullptr, [&]() -> int {
+    if (n < 0 || !grad || (n > 0 && (!theta || !x || !dy))) fail(AMG_ERR_INVALID, "bad argument");
+    mlp_backward(theta, x, dy, n, grad, (cudaStream_t)stream);
+    return AMG_OK;
+  });
+}
+
 int amg_mlp_adam(float* theta, const float* grad, float* m, float* v, int32_t step, float lr,
                  void* stream) {
   return guarded(nullptr, [&]() -> int {

@@ -62,13 +62,16 @@ struct Smem {
 
 // Forward (and, with BWD, backward) pass of the samples [64 blockIdx.x, +64).
 // y: per-sample outputs (may be null); grad: gradient accumulator (BWD);
-// loss: accumulator of sum (y - t)^2 / n (BWD).
+// loss: accumulator of sum (y - t)^2 / n (BWD with the squared-error loss);
+// dyin: when given (BWD), the per-sample gradient dL/dy_i of any loss, used instead
+// of the squared error (grad then accumulates sum_i dyin_i dy_i/dtheta).
 template <bool BWD>
 __global__ void __launch_bounds__(128) k_mlp(const float* __restrict__ theta,
                                              const float* __restrict__ X,
                                              const float* __restrict__ tgt, int n,
                                              float* __restrict__ yout, float* __restrict__ grad,
-                                             float* __restrict__ loss) {
+                                             float* __restrict__ loss,
+                                             const float* __restrict__ dyin) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& S = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
@@ -118,7 +121,9 @@ __global__ void __launch_bounds__(128) k_mlp(const float* __restrict__ theta,
     for (int j = 0; j < NH; ++j) acc = fmaf(fmaxf(S.z2[tid * NH + j], 0.f), S.w3[j], acc);
     S.y[tid] = acc;
     if (yout && s0 + tid < n) yout[s0 + tid] = acc;
-    if (BWD) {
+    if (BWD && dyin) {           // upstream gradient given per sample
+      S.dy[tid] = (s0 + tid < n) ? dyin[s0 + tid] : 0.f;
+    } else if (BWD) {            // mean squared error against tgt
       const float d = (s0 + tid < n) ? acc - tgt[s0 + tid] : 0.f;
       S.dy[tid] = 2.f * d / (float)n;
       atomicAdd(loss, d * d / (float)n);
@@ -213,7 +218,7 @@ void mlp_forward(const float* theta, const float* X, int n, float* y, cudaStream
   set_smem();
   if (n <= 0) return;
   k_mlp<false><<<(n + TILE - 1) / TILE, 128, kSmem, s>>>(theta, X, nullptr, n, y, nullptr,
-                                                          nullptr);
+                                                          nullptr, nullptr);
   AMG_LAUNCH_CHECK();
 }
 
@@ -223,7 +228,18 @@ void mlp_gradient(const float* theta, const float* X, const float* t, int n, flo
   AMG_CUDA(cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s));
   AMG_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
   if (n <= 0) return;
-  k_mlp<true><<<(n + TILE - 1) / TILE, 128, kSmem, s>>>(theta, X, t, n, nullptr, grad, loss);
+  k_mlp<true><<<(n + TILE - 1) / TILE, 128, kSmem, s>>>(theta, X, t, n, nullptr, grad, loss,
+                                                         nullptr);
+  AMG_LAUNCH_CHECK();
+}
+
+void mlp_backward(const float* theta, const float* X, const float* dy, int n, float* grad,
+                  cudaStream_t s) {
+  set_smem();
+  AMG_CUDA(cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s));
+  if (n <= 0) return;
+  k_mlp<true><<<(n + TILE - 1) / TILE, 128, kSmem, s>>>(theta, X, nullptr, n, nullptr, grad,
+                                                         nullptr, dy);
   AMG_LAUNCH_CHECK();
 }
 

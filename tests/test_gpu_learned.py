@@ -102,6 +102,24 @@ def test_mlp_gradient_matches_oracle(n):
     assert np.dot(got, exact) >= 0.999 * np.linalg.norm(got) * np.linalg.norm(exact)
 
 
+@pytest.mark.parametrize("n", [45, 192])
+def test_mlp_backward_matches_oracle(n):
+    """Back-propagation of given per-sample gradients (the ranking-loss training path)."""
+    theta, X, _ = _draw(n, 300 + n)
+    dy = f32(np.random.default_rng(n).standard_normal(n) / n)
+    g = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    B().mlp_backward(dev(theta), dev(X), dev(dy), g)
+    torch.cuda.synchronize()
+    got = g.cpu().numpy().astype(np.float64)
+    want = mlp.backward(theta, X, dy, bf16)
+    off = 0
+    for name, shape in mlp.SIZES:
+        k = int(np.prod(shape))
+        a, b = got[off:off + k], want[off:off + k]
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-7, name
+        off += k
+
+
 def test_mlp_adam_steps():
     """Step 1 from zero moments is theta - lr g / (|g| + eps); step 2 by the update rule."""
     rng = np.random.default_rng(4)

@@ -122,3 +122,20 @@ def test_committed_training_data_and_network():
     y, _ = mlp.forward(theta, X[val].astype(np.float64))
     mse = np.mean((y - T[val]) ** 2)
     assert mse < 0.5 * np.mean(T[val] ** 2), (mse, np.mean(T[val] ** 2))
+
+
+def test_mlp_backward_matches_central_differences():
+    """backward(theta, X, dy) is the gradient of sum_i dy_i y_i(theta)."""
+    rng = np.random.default_rng(6)
+    theta = mlp.init(2) + 0.05 * rng.standard_normal(mlp.NPARAM)
+    X = rng.standard_normal((16, mlp.NI))
+    dy = rng.standard_normal(16)
+    g = mlp.backward(theta, X, dy)
+    f = lambda th: float(dy @ mlp.forward(th, X)[0])   # noqa: E731
+    idx = rng.choice(mlp.NPARAM, 150, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(mlp.NPARAM)
+        e[i] = h
+        fd = (f(theta + e) - f(theta - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, np.abs(g).max())
