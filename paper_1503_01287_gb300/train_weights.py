@@ -17,8 +17,10 @@ rho = (||r_k|| / ||r_0||)^(1/k).  One training sample is
 (wp and its input are 1 and 0 for the SPD problems).  The plain weights give
 target 0 by definition, so the plain method is the yardstick of every sample.
 
-Training.  Adam on the mean squared error with the amg_mlp_* kernels (BF16
-products, FP32 accumulation), full batch, problems split 90 / 10 into
+Training.  Adam with the amg_mlp_* kernels (BF16 products, FP32 accumulation)
+on the mean squared error of the targets (--loss mse) or on a listwise ranking
+loss of each problem's candidates (--loss rank: the loss gradient per sample is
+formed on the host and back-propagated by amg_mlp_backward), full batch, problems split 90 / 10 into
 training and validation sets, learning rate divided by 10 over the last third;
 the parameters with the lowest validation selection regret are kept (per
 validation problem: how much worse the measured candidate the network ranks
@@ -124,8 +126,28 @@ def selection_regret(y: np.ndarray, T: np.ndarray, owner: np.ndarray) -> float:
     return float(np.mean(reg)) if reg else 0.0
 
 
+RANK_TAU = 0.01   # softmax temperature of the listwise ranking loss (log10 factor units)
+
+
+def rank_loss_grad(y: np.ndarray, T: np.ndarray, groups: int, tau: float = RANK_TAU):
+    """Listwise ranking loss over each problem's measured candidates (rows of the
+    (groups, k) reshapes of y and T): L = -mean_p sum_k q_pk log p_pk with
+    q = softmax(-T / tau) (the measured order) and p = softmax(-y / tau) (the
+    network's), so the candidate the network ranks first is pushed towards the one
+    that measured best.  Returns (L, dL/dy)."""
+    yy = y.reshape(groups, -1) / -tau
+    tt = T.reshape(groups, -1) / -tau
+    yy = yy - yy.max(axis=1, keepdims=True)
+    tt = tt - tt.max(axis=1, keepdims=True)
+    lp = yy - np.log(np.exp(yy).sum(axis=1, keepdims=True))
+    q = np.exp(tt) / np.exp(tt).sum(axis=1, keepdims=True)
+    loss = float(-(q * lp).sum(axis=1).mean())
+    d = (q - np.exp(lp)) / tau / groups
+    return loss, d.reshape(-1)
+
+
 def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: float, seed: int,
-          torch, owner: np.ndarray | None = None):
+          torch, owner: np.ndarray | None = None, loss_kind: str = "mse"):
     from . import binding as B
     rng = np.random.default_rng(seed)
     # He-scaled normal initialisation, zero biases (W1, b1, W2, b2, W3, b3)
@@ -144,10 +166,27 @@ def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: floa
     Tv_h = T[val_idx]
     ov = owner[val_idx] if owner is not None else None
     t0 = time.time()
+    rank = loss_kind == "rank"
+    if rank:
+        # every problem contributes the same number of consecutive rows
+        ot = owner[train_idx]
+        per = int(np.sum(ot == ot[0]))
+        assert len(ot) % per == 0 and np.all(ot.reshape(-1, per) == ot[::per, None])
+        groups = len(ot) // per
+        Th = T[train_idx].astype(np.float64)
+        yt = torch.zeros(len(train_idx), device="cuda")
+        dyt = torch.zeros(len(train_idx), device="cuda")
     for step in range(1, steps + 1):
         # learning rate: constant, then divided by 10 over the last third
         lr_k = lr if step <= 2 * steps // 3 else lr * 0.1
-        B.mlp_gradient(theta, Xt, Tt, g, loss)
+        if rank:
+            B.mlp_forward(theta, Xt, yt)
+            lval, d = rank_loss_grad(yt.cpu().numpy().astype(np.float64), Th, groups)
+            dyt.copy_(torch.from_numpy(d.astype(np.float32)))
+            B.mlp_backward(theta, Xt, dyt, g)
+            loss.fill_(lval)
+        else:
+            B.mlp_gradient(theta, Xt, Tt, g, loss)
         B.mlp_adam(theta, g, m, v, step, lr_k)
         if step % 100 == 0 or step == steps:
             B.mlp_forward(theta, Xv, yv)
@@ -178,6 +217,9 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights",
                                                   "mlp_theta.npy"))
+    ap.add_argument("--loss", default="mse", choices=["mse", "rank"],
+                    help="mse: fit the measured targets; rank: listwise ranking of each "
+                         "problem's candidates (back-propagated with amg_mlp_backward)")
     ap.add_argument("--data", default=None,
                     help="train on a dataset written by an earlier run (<out>.data.npz) "
                          "instead of measuring one")
@@ -229,7 +271,8 @@ def main(argv=None):
     val_p = set(perm[:max(1, len(plain) // 10)].tolist())
     val_idx = np.array([i for i in range(len(T)) if owner[i] in val_p], dtype=np.int64)
     train_idx = np.array([i for i in range(len(T)) if owner[i] not in val_p], dtype=np.int64)
-    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner)
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner,
+                                 args.loss)
 
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, theta.astype(np.float32))
@@ -264,9 +307,10 @@ def train_only(args):
     val_p[perm[:max(1, nprob // 10)]] = True
     val_idx = np.nonzero(val_p[owner])[0]
     train_idx = np.nonzero(~val_p[owner])[0]
-    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner)
+    theta, hist, train_s = train(X, T, train_idx, val_idx, args.steps, args.lr, 3, torch, owner,
+                                 args.loss)
     np.save(args.out, theta.astype(np.float32))
-    summary = {"data": os.path.basename(args.data), "samples": int(len(T)),
+    summary = {"data": os.path.basename(args.data), "loss": args.loss, "samples": int(len(T)),
                "train_samples": int(len(train_idx)), "val_samples": int(len(val_idx)),
                "steps": args.steps, "lr": args.lr, "target_mean": float(T.mean()),
                "target_std": float(T.std()), "history": hist, "train_s": train_s}
