@@ -155,6 +155,11 @@ typedef struct amg_options {
                                launches (cluster_from 0, cycle_kernel 1)        */
   double omega;             /* block Jacobi damping (default 0.5)               */
   double omega_p;           /* sGS pressure step omega (default 0.125)          */
+  int32_t batch_tile;       /* amg_solve_batched: tile of the SpMM row kernels,
+                               -1 chosen per level by timing (default); 0..3 =
+                               (lane groups per row, blocks unrolled) of (1,2),
+                               (2,2), (1,4), (2,4)                              */
+  int32_t pad1;
 } amg_options;
 
 #define AMG_MAX_LEVELS 8

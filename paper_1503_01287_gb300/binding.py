@@ -70,7 +70,8 @@ class AmgOptions(C.Structure):
                 ("gmres_restart", C.c_int32), ("separate", C.c_int32),
                 ("max_iterations", C.c_int32), ("use_graphs", C.c_int32),
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
-                ("omega", C.c_double), ("omega_p", C.c_double)]
+                ("omega", C.c_double), ("omega_p", C.c_double),
+                ("batch_tile", C.c_int32), ("pad1", C.c_int32)]
 
 
 class AmgStats(C.Structure):

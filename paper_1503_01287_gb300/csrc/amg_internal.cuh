@@ -171,6 +171,8 @@ constexpr int kRhs = 16;
 struct BatchLevel {
   DBuf<double> x64, b64, r64, t64;
   DBuf<float> x32, b32, r32, t32;
+  int tile = 0;     // block-row tile of the cycle's SpMM kernels (chosen by timing)
+  int tile64 = 0;   // the same for the FP64 operator (level 0)
 };
 
 }  // namespace amgp2

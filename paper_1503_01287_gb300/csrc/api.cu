@@ -93,6 +93,8 @@ void amg_default_options(amg_options* o) {
   o->cycle_kernel = 0;
   o->omega = 0.5;
   o->omega_p = 0.125;
+  o->batch_tile = -1;
+  o->pad1 = 0;
 }
 
 int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,

@@ -32,9 +32,11 @@ enum MMode { mApply = 0, mResid = 1, mGS = 2, mJacobi = 3 };
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-// 16 lanes per stored row, lane r = right-hand side r.  Row data at
-// rowptr[g]..rowptr[g+1] (colour-major storage when rows != null).
-template <typename T, int MODE>
+// Tile of the SpMM row kernels: S lane groups of 16 per stored row (lane r of a
+// group = right-hand side r), group q taking the blocks q, q + S, ... of the row
+// (S = 2: one warp a row, partial sums combined by a shuffle); U blocks unrolled.
+// Row data at rowptr[g]..rowptr[g+1] (colour-major storage when rows != null).
+template <typename T, int MODE, int S, int U>
 __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict__ rows,
                                                 const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
@@ -43,14 +45,15 @@ __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict
                                                 const T* __restrict__ dinv, T omega,
                                                 const double* __restrict__ wt) {
   if (wt) omega = (T)((double)omega * wt[0]);   // learned relaxation multiplier
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / K;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / (K * S);
+  const int q = (threadIdx.x / K) % S;
   const int r = threadIdx.x % K;
-  if (g >= nrows) return;
+  if (g >= nrows) return;                       // uniform over the S groups of a row
   const int i = rows ? ldg(rows + g) : g;
   const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
   T s0 = T(0), s1 = T(0), s2 = T(0);
-#pragma unroll 2
-  for (int k = a; k < e; ++k) {
+#pragma unroll U
+  for (int k = a + q; k < e; k += S) {
     const int j = ldg(col + k);
     T x0, x1, x2;
     ld3(x, j * K + r, x0, x1, x2);
@@ -64,6 +67,12 @@ __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict
     s2 = fma(ldg(v + 6 * nnzb), x0, s2);
     s2 = fma(ldg(v + 7 * nnzb), x1, s2);
     s2 = fma(ldg(v + 8 * nnzb), x2, s2);
+  }
+  if (S == 2) {   // the two groups of a row are the two halves of one warp
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+    if (q != 0) return;
   }
   const int o = i * K + r;
   if (MODE == mApply) {
@@ -357,27 +366,49 @@ template <> struct MV<float> {
   static const float* rval(Level& l) { return l.r_val32; }
 };
 
+constexpr int kTiles = 4;   // tile t: S = 1 + (t & 1), U = (t & 2) ? 4 : 2
+
+template <typename T, int MODE, int S, int U>
+void launch_rows_m(int nrows, const int* rows, const int* rowptr, Level& lv, const T* val,
+                   const T* x, const T* b, T* y, const T* dinv, T omega, const double* wt,
+                   cudaStream_t s) {
+  const int grid = (int)(((int64_t)nrows * K * S + 255) / 256);
+  k_rows_m<T, MODE, S, U><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x,
+                                               b, y, dinv, omega, wt);
+}
+
+template <typename T, int MODE>
+void launch_tile_m(int tile, int nrows, const int* rows, const int* rowptr, Level& lv,
+                   const T* val, const T* x, const T* b, T* y, const T* dinv, T omega,
+                   const double* wt, cudaStream_t s) {
+  switch (tile) {
+    case 1: launch_rows_m<T, MODE, 2, 2>(nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, wt, s); break;
+    case 2: launch_rows_m<T, MODE, 1, 4>(nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, wt, s); break;
+    case 3: launch_rows_m<T, MODE, 2, 4>(nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, wt, s); break;
+    default: launch_rows_m<T, MODE, 1, 2>(nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, wt, s); break;
+  }
+}
+
 template <typename T>
 void rows_m(amg_handle* h, int mode, Level& lv, int first, int nrows, const T* val, const T* x,
-            const T* b, T* y, const T* dinv, T omega) {
+            const T* b, T* y, const T* dinv, T omega, int tile) {
   if (nrows <= 0) return;
   const int* order = lv.k_rows();
   const int* rows = order ? order + first : nullptr;
   const int* rowptr = lv.k_rowptr() + first;
-  const int grid = (int)(((int64_t)nrows * K + 255) / 256);
   cudaStream_t s = h->stream;
   switch (mode) {
     case mApply:
-      k_rows_m<T, mApply><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, nullptr);
+      launch_tile_m<T, mApply>(tile, nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, nullptr, s);
       break;
     case mResid:
-      k_rows_m<T, mResid><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, nullptr);
+      launch_tile_m<T, mResid>(tile, nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, nullptr, s);
       break;
     case mGS:
-      k_rows_m<T, mGS><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, lv.wt);
+      launch_tile_m<T, mGS>(tile, nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, lv.wt, s);
       break;
     default:
-      k_rows_m<T, mJacobi><<<grid, 256, 0, s>>>(nrows, rows, rowptr, lv.k_col(), val, lv.nnzb, x, b, y, dinv, omega, lv.wt);
+      launch_tile_m<T, mJacobi>(tile, nrows, rows, rowptr, lv, val, x, b, y, dinv, omega, lv.wt, s);
       break;
   }
   h->launches++;
@@ -389,7 +420,8 @@ void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
   BatchLevel& bl = h->B[l];
   if (h->opt.smoother == AMG_SMOOTHER_JACOBI) {
     T* t = MV<T>::t(bl);
-    rows_m<T>(h, mJacobi, lv, 0, lv.n, MV<T>::val(lv), x, b, t, MV<T>::dinv(lv), (T)h->opt.omega);
+    rows_m<T>(h, mJacobi, lv, 0, lv.n, MV<T>::val(lv), x, b, t, MV<T>::dinv(lv), (T)h->opt.omega,
+              bl.tile);
     k_copy_m<T><<<gridk(4 * (int64_t)K * lv.n), 256, 0, h->stream>>>(t, x, 4 * (int64_t)K * lv.n);
     h->launches++;
     return;
@@ -397,7 +429,7 @@ void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
-    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1));
+    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1), bl.tile);
   }
 }
 
@@ -431,7 +463,7 @@ void cycle_m(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
     h->launches++;
   }
   T* r = MV<T>::r(bl);
-  rows_m<T>(h, mResid, lv, 0, lv.n, MV<T>::val(lv), x, b, r, nullptr, T(0));
+  rows_m<T>(h, mResid, lv, 0, lv.n, MV<T>::val(lv), x, b, r, nullptr, T(0), bl.tile);
   k_restrict_m<T><<<gridk((int64_t)nx.n * K), 256, 0, s>>>(nx.n, lv.r_rowptr, lv.r_col,
                                                           MV<T>::rval(lv), r, MV<T>::b(bn));
   h->launches++;
@@ -464,7 +496,7 @@ void precond_m(amg_handle* h, const double* r, double* z) {
 
 void apply_m64(amg_handle* h, const double* x, double* y) {
   Level& lv = *h->L[0];
-  rows_m<double>(h, mApply, lv, 0, lv.n, lv.k_val(), x, nullptr, y, nullptr, 0.0);
+  rows_m<double>(h, mApply, lv, 0, lv.n, lv.k_val(), x, nullptr, y, nullptr, 0.0, h->B[0].tile64);
 }
 
 void dots_m(amg_handle* h, int slot, const double* a0, const double* b0,
@@ -474,6 +506,36 @@ void dots_m(amg_handle* h, int slot, const double* a0, const double* b0,
   k_dots_m<<<kDotBlocks, kDotThreads, 0, h->stream>>>(nel, nd, a0, b0, a1, b1, h->bred);
   k_final_m<<<1, 64, 0, h->stream>>>(h->bred, kDotBlocks, nd, h->bscal.p + slot * K);
   h->launches += 2;
+}
+
+// The fastest tile of the operator pass on one level (CUDA events, the level's
+// multi-right-hand-side work vectors; before any graph is captured).
+template <typename T>
+int tune_tile(amg_handle* h, Level& lv, const T* val, const T* x, T* y) {
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int t = 0; t < kTiles; ++t) {
+    for (int r = 0; r < 7; ++r) {
+      if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+      rows_m<T>(h, mApply, lv, 0, lv.n, val, x, nullptr, y, nullptr, T(0), t);
+    }
+    AMG_CUDA(cudaEventRecord(e1, s));
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 void alloc_batch(amg_handle* h) {
@@ -502,6 +564,18 @@ void alloc_batch(amg_handle* h) {
   h->bscal.alloc((size_t)M_NS * K);
   h->bit.alloc(1);
   AMG_CUDA(cudaStreamSynchronize(h->stream));
+  // SpMM tile per level (the coarsest level is solved densely): given, or timed
+  const int fixed = h->opt.batch_tile;
+  if (fixed >= kTiles) fail(AMG_ERR_INVALID, "batch_tile must be -1 or 0..3");
+  for (size_t l = 0; l + 1 < h->L.size(); ++l) {
+    Level& lv = *h->L[l];
+    BatchLevel& b = h->B[l];
+    if (fixed >= 0) b.tile = fixed;
+    else if (f32) b.tile = tune_tile<float>(h, lv, MV<float>::val(lv), b.x32, b.t32);
+    else b.tile = tune_tile<double>(h, lv, MV<double>::val(lv), b.x64, b.t64);
+  }
+  h->B[0].tile64 = fixed >= 0 ? fixed
+                              : tune_tile<double>(h, *h->L[0], h->L[0]->k_val(), h->mx, h->mq);
 }
 
 // initial block of one problem: x = 0, r = b, z = M r, rz, p = z, active set

@@ -43,13 +43,16 @@ def _rhs(prob, k, rng):
     return out
 
 
-@pytest.mark.parametrize("precision,k", [(0, 5), (1, 5), (1, 16), (1, 1)])
-def test_batched_matches_single_and_direct(precision, k):
+@pytest.mark.parametrize("precision,k,tile", [(0, 5, -1), (1, 5, -1), (1, 16, -1), (1, 1, -1),
+                                             (1, 5, 0), (1, 5, 1), (1, 5, 2), (1, 5, 3),
+                                             (0, 3, 1), (0, 3, 3)])
+def test_batched_matches_single_and_direct(precision, k, tile):
+    """tile -1: the SpMM tile chosen per level by timing; 0..3: each tile forced."""
     probs = _problems()
     rng = np.random.default_rng(7)
     handles, Bs, Xs, rhs = [], [], [], []
     for p in probs:
-        h = B().setup_problem(p, B().default_options(precision=precision))
+        h = B().setup_problem(p, B().default_options(precision=precision, batch_tile=tile))
         r = _rhs(p, k, rng)
         if k >= 3:
             r[2] = 0.0                       # a zero right-hand side converges at once
