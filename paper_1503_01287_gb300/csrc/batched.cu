@@ -368,6 +368,132 @@ template <> struct MV<float> {
 
 constexpr int kTiles = 4;   // tile t: S = 1 + (t & 1), U = (t & 2) ? 4 : 2
 
+// One colour of the multicolour Gauss-Seidel sweep for all right-hand sides,
+// launched with programmatic dependent launch: the row's ids, the column indices
+// and values of its first U blocks of this lane group, b and D^{-1} are loaded
+// before griddepcontrol.wait (none of them is written by the previous colour's
+// kernel or by anything it overlaps: they are setup data, or b, written before the
+// sweep's first colour by a kernel that does not overlap), so this prologue runs
+// under the previous colour; after the wait only the x gathers and the update
+// remain.  Tile as in k_rows_m.
+template <typename T, int S, int U>
+__global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restrict__ rows,
+                                                  const int* __restrict__ rowptr,
+                                                  const int* __restrict__ col,
+                                                  const T* __restrict__ val, int64_t nnzb, T* x,
+                                                  const T* __restrict__ b,
+                                                  const T* __restrict__ dinv,
+                                                  const double* __restrict__ wt) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / (K * S);
+  const int q = (threadIdx.x / K) % S;
+  const int r = threadIdx.x % K;
+  const bool active = g < nrows;       // uniform over the S groups of a row
+  int i = 0, a = 0, e = 0;
+  int j[U];
+  T v[U][9];
+  T b0 = T(0), b1 = T(0), b2 = T(0);
+  T d[9];
+#pragma unroll
+  for (int u = 0; u < U; ++u) j[u] = -1;
+  if (active) {
+    i = __ldg(rows + g);
+    a = __ldg(rowptr + g);
+    e = __ldg(rowptr + g + 1);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = a + q + u * S;
+      if (k < e) {
+        j[u] = __ldg(col + k);
+#pragma unroll
+        for (int w = 0; w < 9; ++w) v[u][w] = __ldg(val + w * nnzb + k);
+      }
+    }
+    if (q == 0) {
+      ld3(b, i * K + r, b0, b1, b2);
+      const T* dp = dinv + 12 * (int64_t)i;
+      ld3(dp, 0, d[0], d[1], d[2]);
+      ld3(dp, 1, d[3], d[4], d[5]);
+      ld3(dp, 2, d[6], d[7], d[8]);
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!active) return;
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (j[u] < 0) continue;
+    T x0, x1, x2;
+    ld3(x, j[u] * K + r, x0, x1, x2);
+    s0 = fma(v[u][0], x0, s0); s0 = fma(v[u][1], x1, s0); s0 = fma(v[u][2], x2, s0);
+    s1 = fma(v[u][3], x0, s1); s1 = fma(v[u][4], x1, s1); s1 = fma(v[u][5], x2, s1);
+    s2 = fma(v[u][6], x0, s2); s2 = fma(v[u][7], x1, s2); s2 = fma(v[u][8], x2, s2);
+  }
+  for (int k = a + q + U * S; k < e; k += S) {   // blocks beyond the prefetched ones
+    const int jj = __ldg(col + k);
+    T x0, x1, x2;
+    ld3(x, jj * K + r, x0, x1, x2);
+    const T* vv = val + k;
+    s0 = fma(__ldg(vv), x0, s0);
+    s0 = fma(__ldg(vv + nnzb), x1, s0);
+    s0 = fma(__ldg(vv + 2 * nnzb), x2, s0);
+    s1 = fma(__ldg(vv + 3 * nnzb), x0, s1);
+    s1 = fma(__ldg(vv + 4 * nnzb), x1, s1);
+    s1 = fma(__ldg(vv + 5 * nnzb), x2, s1);
+    s2 = fma(__ldg(vv + 6 * nnzb), x0, s2);
+    s2 = fma(__ldg(vv + 7 * nnzb), x1, s2);
+    s2 = fma(__ldg(vv + 8 * nnzb), x2, s2);
+  }
+  if (S == 2) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+    if (q != 0) return;
+  }
+  const int o = i * K + r;
+  T x0, x1, x2;
+  ld3(x, o, x0, x1, x2);
+  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+  st3(x, o, x0 + om * (d[0] * r0 + d[1] * r1 + d[2] * r2),
+      x1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2),
+      x2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
+}
+
+template <typename T, int S, int U>
+void launch_gs_m_pdl(int nrows, const int* rows, const int* rowptr, Level& lv, const T* val,
+                     T* x, const T* b, const T* dinv, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(((int64_t)nrows * K * S + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_m_pdl<T, S, U>, nrows, rows, rowptr,
+                              (const int*)lv.k_col(), val, lv.nnzb, x, b, dinv,
+                              (const double*)lv.wt));
+}
+
+// one colour of the batched Gauss-Seidel sweep (x updated in place)
+template <typename T>
+void gs_colour_m(amg_handle* h, Level& lv, int first, int nrows, const T* val, T* x,
+                 const T* b, const T* dinv, int tile) {
+  if (nrows <= 0) return;
+  const int* rows = lv.k_rows() + first;
+  const int* rowptr = lv.k_rowptr() + first;
+  cudaStream_t s = h->stream;
+  switch (tile) {
+    case 1: launch_gs_m_pdl<T, 2, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 2: launch_gs_m_pdl<T, 1, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 3: launch_gs_m_pdl<T, 2, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    default: launch_gs_m_pdl<T, 1, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+  }
+  h->launches++;
+}
+
 template <typename T, int MODE, int S, int U>
 void launch_rows_m(int nrows, const int* rows, const int* rowptr, Level& lv, const T* val,
                    const T* x, const T* b, T* y, const T* dinv, T omega, const double* wt,
@@ -429,7 +555,10 @@ void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
   for (int q = 0; q < lv.ncolours; ++q) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
-    rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1), bl.tile);
+    if (h->use_pdl && lv.k_rows())
+      gs_colour_m<T>(h, lv, a, e - a, MV<T>::val(lv), x, b, MV<T>::dinv(lv), bl.tile);
+    else
+      rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1), bl.tile);
   }
 }
 
