@@ -179,7 +179,9 @@ def run_gpu(args, rank, world):
     sptr = stream.cuda_stream
 
     t0 = time.perf_counter()
-    chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32), stream=sptr)
+    chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
+                                                     outer_pair=args.outer_pair,
+                                                     gs_cluster=args.gs_cluster), stream=sptr)
     setup_chosen_ms = 1e3 * (time.perf_counter() - t0)
     # the learned weights: selection by the trained network, measured fallback included
     learned = None
@@ -251,6 +253,13 @@ def run_gpu(args, rank, world):
     gs_bytes = 40 * info0.nnzb + 80 * info0.n_nodes
     spmv_ms, _ = chosen.time_level_op("apply", 0, B.AMG_FP64, reps=20, warmup=3)
     spmv_bytes = 76 * info0.nnzb + 52 * info0.n_nodes
+    # the Krylov operator of the FP32-cycle solve: FP32-pair values (8 bytes an
+    # entry, as FP64) and the direction as 8 floats a node
+    spmv_pair = None
+    if args.outer_pair:
+        spmv_pair_ms, _ = chosen.time_level_op("apply", 0, B.AMG_FP32_PAIR, reps=20, warmup=3)
+        spmv_pair = {"ms": spmv_pair_ms, "bytes": spmv_bytes,
+                     "gbs": spmv_bytes / (spmv_pair_ms * 1e-3) / 1e9}
     # per-level device times of the cycle operations (CUDA events, handle stream)
     breakdown = []
     for l in range(chosen.n_levels):
@@ -328,7 +337,8 @@ def run_gpu(args, rank, world):
         "metric": metric_name(args.n), "value": value, "unit": "DOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 cycle + f64 outer", "data": "synthetic",
+        "dtype": ("f32 cycle + f32-pair Krylov operator + f64 vectors" if args.outer_pair
+                  else "f32 cycle + f64 outer"), "data": "synthetic",
         "config": {"workload": f"elasticity_n{args.n}: 32^3 cubes x 6 tets P2, E=1 nu=0.3, "
                                f"clamped z=0, U[-1,1]^3 traction z=1"
                                if args.n == 32 else f"elasticity_n{args.n}",
@@ -345,6 +355,7 @@ def run_gpu(args, rank, world):
         "levels": {"nodes": stats[-1]["level_nodes"], "nnzb": stats[-1]["level_nnzb"],
                    "colours": stats[-1]["level_colours"],
                    "lanes_per_row": stats[-1]["level_group"],
+                   "gs_cluster_ctas": stats[-1]["level_gs_cluster"],
                    "cluster_from": stats[-1]["cluster_from"],
                    "cycle_kernel": stats[-1]["cycle_kernel"]},
         "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
@@ -360,6 +371,7 @@ def run_gpu(args, rank, world):
                      "peak_kind": f"{peak_kind} hbm_gbs"},
         "kernels": {"spmv_fp64_level0": {"ms": spmv_ms, "bytes": spmv_bytes,
                                          "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9},
+                    "spmv_pair_level0": spmv_pair,
                     "precond_fp32": {"ms": precond_ms, "launches": precond_launches},
                     "levels_fp32": breakdown},
         "clocks": clocks,
@@ -664,6 +676,10 @@ def main():
                     help="profile: cluster sub-cycle start level (the bench's choice)")
     ap.add_argument("--cycle-kernel", type=int, default=1,
                     help="profile: 1 per-operation launches, 2 persistent cycle")
+    ap.add_argument("--outer-pair", type=int, default=1, choices=[0, 1],
+                    help="elasticity: Krylov operator in FP32 pairs (1) or FP64 (0)")
+    ap.add_argument("--gs-cluster", type=int, default=-1,
+                    help="elasticity: one-cluster colour sweeps (-1 timed, 0 off, k CTAs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -81,12 +81,18 @@ enum amg_smoother {
 
 enum amg_precision {
   AMG_FP64 = 0,             /* cycle in FP64                                    */
-  AMG_FP32 = 1,             /* cycle in FP32, outer Krylov and coarsest in FP64 */
-  AMG_FP32_BF16 = 2         /* AMG_FP32 with the operator values of levels >= 1
+  AMG_FP32 = 1,             /* cycle in FP32, outer Krylov and coarsest in FP64
+                               (the Krylov operator products in FP32 pairs by
+                               default, amg_options.outer_pair)                 */
+  AMG_FP32_BF16 = 2,        /* AMG_FP32 with the operator values of levels >= 1
                                stored in BF16 (rounded to nearest even from the
                                FP64 Galerkin values, converted to FP32 in the
                                kernels); level 0, D^{-1}, P and the pressure
                                parts stay FP32                                  */
+  AMG_FP32_PAIR = 3         /* not a cycle precision: amg_level_apply and
+                               amg_time_level_op on level 0 of an FP32 SPD
+                               handle with outer_pair run the Krylov operator's
+                               FP32-pair kernel (see amg_options.outer_pair)    */
 };
 
 enum amg_krylov {
@@ -159,7 +165,21 @@ typedef struct amg_options {
                                -1 chosen per level by timing (default); 0..3 =
                                (lane groups per row, blocks unrolled) of (1,2),
                                (2,2), (1,4), (2,4)                              */
-  int32_t pad1;
+  int32_t gs_cluster;       /* multicolour Gauss-Seidel sweep of a level whose
+                               iterate, right-hand side and row offsets fit in
+                               shared memory (SPD kinds, up to about 5000 nodes
+                               in FP32, 2800 in FP64): -1
+                               chosen per level by timing at setup (default),
+                               0 one launch per colour, k = 1, 2, 4, 8 or 16:
+                               the whole sweep in one cluster of k CTAs         */
+  int32_t outer_pair;       /* FP32-cycle CG solves of SPD kinds: 1 (default)
+                               the Krylov operator products K p in FP32-pair
+                               arithmetic -- every FP64 value and direction entry
+                               held as two floats hi + lo, each product formed
+                               exactly with an FMA, sums compensated (TwoSum),
+                               about 2^-48 relative; 0 in FP64.  The residual
+                               reported at exit is always recomputed in FP64     */
+  int32_t pad2;
 } amg_options;
 
 #define AMG_MAX_LEVELS 8
@@ -182,6 +202,8 @@ typedef struct amg_stats {
   int32_t cluster_from;     /* cycle variant in use: first level of the cluster
                                sub-cycle (0: none)                              */
   int32_t cycle_kernel;     /* 1: one launch per operation, 2: persistent cycle */
+  int32_t level_gs_cluster[AMG_MAX_LEVELS];  /* CTAs of the one-cluster sweep
+                               (0: one launch per colour)                       */
 } amg_stats;
 
 typedef struct amg_level_info {
@@ -355,8 +377,9 @@ int amg_apply_preconditioner(amg_handle* h, const double* r, double* z);
 int amg_apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
 
 /* y = K_l x on level `level` with the library's FP64 (precision = AMG_FP64) or
- * FP32 (AMG_FP32, values rounded to float, accumulated in float) kernels; x
- * and y are device pointers of 3*n_nodes + n_pres doubles. */
+ * FP32 (AMG_FP32, values rounded to float, accumulated in float) kernels, or on
+ * level 0 the Krylov operator's FP32-pair kernel (AMG_FP32_PAIR); x and y are
+ * device pointers of 3*n_nodes + n_pres doubles. */
 int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const double* x,
                     double* y);
 
@@ -379,7 +402,8 @@ enum amg_level_op {
 /*
  * amg_time_level_op -- device time of one level operation of the cycle, for
  * roofline measurements.  Runs `warmup` untimed then `reps` timed repetitions
- * of `op` on level `level` in `precision` (AMG_FP64 / AMG_FP32) on the handle's
+ * of `op` on level `level` in `precision` (AMG_FP64 / AMG_FP32; AMG_FP32_PAIR
+ * for AMG_OP_APPLY on level 0) on the handle's
  * work vectors, between two CUDA events recorded on the handle's stream;
  * *ms_per_rep receives the mean.  *launches_per_rep receives the kernel
  * launches of one repetition (e.g. the colour count of a GS sweep).

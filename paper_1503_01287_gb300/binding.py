@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libamgp2.so")
 AMG_VECTOR_LAPLACE, AMG_ELASTICITY, AMG_MIXED_ELASTICITY, AMG_STOKES = 0, 1, 2, 3
 AMG_SMOOTHER_GS, AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SGS, AMG_SMOOTHER_BS, AMG_SMOOTHER_VANKA = (
     0, 1, 2, 3, 4)
-AMG_FP64, AMG_FP32, AMG_FP32_BF16 = 0, 1, 2
+AMG_FP64, AMG_FP32, AMG_FP32_BF16, AMG_FP32_PAIR = 0, 1, 2, 3
 AMG_KRYLOV_AUTO, AMG_KRYLOV_PCG, AMG_KRYLOV_FCG, AMG_KRYLOV_FGMRES, AMG_KRYLOV_NONE = 0, 1, 2, 3, 4
 AMG_OK, AMG_NOT_CONVERGED = 0, 1
 AMG_MAX_LEVELS = 8
@@ -71,7 +71,8 @@ class AmgOptions(C.Structure):
                 ("max_iterations", C.c_int32), ("use_graphs", C.c_int32),
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
                 ("omega", C.c_double), ("omega_p", C.c_double),
-                ("batch_tile", C.c_int32), ("pad1", C.c_int32)]
+                ("batch_tile", C.c_int32), ("gs_cluster", C.c_int32),
+                ("outer_pair", C.c_int32), ("pad2", C.c_int32)]
 
 
 class AmgStats(C.Structure):
@@ -84,7 +85,8 @@ class AmgStats(C.Structure):
                 ("level_nnzb", C.c_int64 * AMG_MAX_LEVELS),
                 ("level_colours", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_group", C.c_int32 * AMG_MAX_LEVELS),
-                ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32)]
+                ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
+                ("level_gs_cluster", C.c_int32 * AMG_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -97,7 +99,8 @@ class AmgStats(C.Structure):
                 "level_nnzb": list(self.level_nnzb[:nl]),
                 "level_colours": list(self.level_colours[:nl]),
                 "level_group": list(self.level_group[:nl]),
-                "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel}
+                "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel,
+                "level_gs_cluster": list(self.level_gs_cluster[:nl])}
 
 
 class AmgLearned(C.Structure):

@@ -105,6 +105,15 @@ struct Level {
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
   int group_gs = 0;     // the same for the colour-subset Gauss-Seidel kernel
   int group64 = 0;      // the FP64 operator kernel when the cycle runs in FP32
+  // level 0 of an FP32 SPD handle with outer_pair: the kernel-layout values as
+  // 9 planes of (hi, lo) float pairs, hi = fl32(a), lo = fl32(a - hi)
+  DBuf<float2> val2;
+  int group_pair = 0;
+  // the colour sweep as one launch of a gs_cl-CTA cluster with the iterate in
+  // shared memory (0: one launch per colour), gs_cl_g lanes per block row
+  int gs_cl = 0;
+  int gs_cl_g = 0;
+  int gs_cl_bytes = 0;  // sizeof the arithmetic type the cluster size was chosen for
   // learned weights of this level on the device: [0] relaxation multiplier,
   // [1] coarse-correction scale, [2] pressure-step multiplier (all 1: plain)
   double* wt = nullptr;
@@ -189,6 +198,7 @@ struct amg_handle {
   amgp2::DBuf<double> coarse_inv;  // m x m row-major generalised inverse
   // Krylov state
   amgp2::DBuf<double> kb, kx, kr, kz, kp, kq, kw, kro;   // padded layout
+  amgp2::DBuf<float> kpf;           // the CG direction in pair form (8 floats a node)
   amgp2::DBuf<double> ub, ux;                             // user layout staging
   amgp2::DBuf<double> gm_V, gm_Z;  // FGMRES bases
   amgp2::DBuf<double> red;         // reduction partials
@@ -255,6 +265,11 @@ template <typename T>
 void vcycle(amg_handle* h, int l, bool x_is_zero);
 template <typename T>
 void precondition_device(amg_handle* h, const double* r, double* z);
+// y = K_0 x with the FP32-pair operator (level 0 values split into hi/lo float
+// planes, x as 8 floats a node: hi x,y,z,0 then lo x,y,z,0); y padded FP64
+void apply_pair(amg_handle* h, const float* xp, double* y);
+// the 8-floats-a-node pair form of a padded FP64 vector of n4 = 4 n entries
+void launch_split_pair(const double* x, float* xp, int64_t n4, cudaStream_t s, amg_handle* h);
 // restriction (restrict = true) or prolongation between level and level+1 on
 // the level work vectors, in FP32 or FP64
 void level_transfer(amg_handle* h, int l, bool restrict_, bool f32);

@@ -94,7 +94,9 @@ void amg_default_options(amg_options* o) {
   o->omega = 0.5;
   o->omega_p = 0.125;
   o->batch_tile = -1;
-  o->pad1 = 0;
+  o->gs_cluster = -1;
+  o->outer_pair = 1;
+  o->pad2 = 0;
 }
 
 int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,
@@ -137,6 +139,9 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
       h->bf16_coarse = true;
       h->opt.precision = AMG_FP32;
     }
+    if (h->opt.gs_cluster < -1 || h->opt.gs_cluster > 16 ||
+        (h->opt.gs_cluster > 0 && (h->opt.gs_cluster & (h->opt.gs_cluster - 1))))
+      fail(AMG_ERR_INVALID, "gs_cluster must be -1, 0, 1, 2, 4, 8 or 16");
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
         h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1)
       fail(AMG_ERR_INVALID, "option out of range");
@@ -213,7 +218,9 @@ static void fill_stats(amg_handle* h, amg_stats* st) {
       st->level_nnzb[l] = h->L[l]->nnzb;
       st->level_colours[l] = h->L[l]->ncolours;
       st->level_group[l] = h->L[l]->group;
+      st->level_gs_cluster[l] = h->L[l]->gs_cl;
     } else {
+      st->level_gs_cluster[l] = 0;
       st->level_nodes[l] = st->level_pres[l] = st->level_colours[l] = 0;
       st->level_group[l] = 0;
       st->level_nnzb[l] = 0;
@@ -462,6 +469,15 @@ int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const doubl
       launch_to_float(lv.t64, lv.t32, n4, h->stream, h);
       level_apply<float>(h, level, lv.t32.p, lv.r32.p);
       launch_to_double(lv.r32, lv.r64, n4, h->stream, h);
+    } else if (precision == AMG_FP32_PAIR) {
+      if (level != 0 || !lv.val2.p)
+        fail(AMG_ERR_INVALID, "the FP32-pair operator exists on level 0 of FP32 SPD handles "
+                              "with outer_pair");
+      DBuf<float> xp;
+      xp.alloc(8 * (size_t)lv.n);
+      launch_split_pair(lv.t64, xp, 4 * (int64_t)lv.n, h->stream, h);
+      apply_pair(h, xp, lv.r64);
+      AMG_CUDA(cudaStreamSynchronize(h->stream));
     } else {
       fail(AMG_ERR_INVALID, "unknown precision");
     }
@@ -497,8 +513,17 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
     if ((op == AMG_OP_SMOOTH || op == AMG_OP_RESTRICT || op == AMG_OP_PROLONG) && level == L - 1)
       fail(AMG_ERR_INVALID, "the coarsest level has no smoother or transfer");
     const bool f32 = precision == AMG_FP32;
+    const bool pair = precision == AMG_FP32_PAIR;
     if (f32 && !h->L[0]->val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with FP32");
+    if (pair && (op != AMG_OP_APPLY || level != 0 || !h->L[0]->val2.p))
+      fail(AMG_ERR_INVALID, "the FP32-pair operator is AMG_OP_APPLY on level 0 of FP32 SPD "
+                            "handles with outer_pair");
     Level& lv = *h->L[op == AMG_OP_PRECOND ? 0 : level];
+    DBuf<float> xp;
+    if (pair) {
+      xp.alloc(8 * (size_t)lv.n);
+      AMG_CUDA(cudaMemsetAsync(xp.p, 0, xp.bytes(), h->stream));
+    }
     if (op == AMG_OP_PRECOND && (int64_t)h->kr.n < lv.dofs4()) {
       h->kr.alloc(lv.dofs4());
       h->kz.alloc(lv.dofs4());
@@ -507,7 +532,8 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
     auto once = [&]() {
       switch (op) {
         case AMG_OP_APPLY:
-          if (f32) level_apply<float>(h, level, lv.x32.p, lv.r32.p);
+          if (pair) apply_pair(h, xp.p, lv.r64.p);
+          else if (f32) level_apply<float>(h, level, lv.x32.p, lv.r32.p);
           else level_apply<double>(h, level, lv.x64.p, lv.r64.p);
           break;
         case AMG_OP_RESIDUAL:
@@ -566,8 +592,6 @@ int amg_solve_batched(amg_handle* const* handles, int32_t n_problems, int32_t n_
     if (!(rel_tol > 0.0)) fail(AMG_ERR_INVALID, "rel_tol must be > 0");
     for (int p = 0; p < n_problems; ++p)
       if (!handles[p] || !B[p] || !X[p]) fail(AMG_ERR_INVALID, "null handle or vector");
-    nvtxRangePushA("amg_solve_batched");
-    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     double ms = 0.0;
     return solve_batched(handles, n_problems, n_rhs, B, X, rel_tol, stats, &ms);
   });

@@ -699,6 +699,442 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
                               (const T*)P.dinv, P.wt));
 }
 
+// Multicolour Gauss-Seidel sweep of one small level as ONE launch of a
+// thread-block cluster.  Every CTA keeps in shared memory the level's whole
+// iterate x and right-hand side b (4 values a node) and the row ids and block
+// offsets of the colour-ordered rows; the colours run in sweep order with a
+// cluster barrier between them, and a row's new value is stored into the x copy
+// of every CTA of the cluster (distributed shared memory).  After a barrier a
+// row update therefore reads global memory only for its block columns and values
+// and D_i^{-1}, at addresses known from shared memory: one L2 round trip, which
+// each group of G lanes starts for its next row before the barrier it must
+// wait at (between the barrier's arrive and wait, so that neither waits for the
+// other).  Rows of one colour share no block, so the updates of a colour never
+// read a value written in the same colour (the row's own x_i is read before its
+// own update).
+constexpr int kGsClThreads = 512;
+constexpr int kGsClMaxColours = 127;
+constexpr int kGsClSmemBytes = 200 * 1024;
+
+struct GsColours {
+  int ptr[kGsClMaxColours + 1];   // stored rows of colour c: ptr[c] .. ptr[c+1]
+};
+
+// shared memory of the one-cluster sweep: x and b (4 n values each), the row id
+// and the first block of every stored row (n + 1 offsets)
+template <typename T>
+constexpr int64_t gs_cl_smem(int64_t n) {
+  return 8 * n * (int64_t)sizeof(T) + 4 * n + 4 * (n + 1);
+}
+
+__device__ __forceinline__ void lds3(const float* p, int j, float& a, float& b, float& c) {
+  const float4 v = reinterpret_cast<const float4*>(p)[j];
+  a = v.x; b = v.y; c = v.z;
+}
+__device__ __forceinline__ void lds3(const double* p, int j, double& a, double& b, double& c) {
+  const double2 v = reinterpret_cast<const double2*>(p)[2 * j];
+  a = v.x; b = v.y;
+  c = p[4 * j + 2];
+}
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// blocks carried per lane (register budget of a 512-thread CTA: 128 a thread)
+template <typename T, int G, typename V>
+constexpr int gs_cl_unroll() {
+  return (sizeof(T) == 8 || sizeof(V) == 2 || G >= 16) ? 2 : 3;
+}
+
+// ONE: a single CTA (no cluster): plain shared-memory stores and __syncthreads
+// between the colours, whose bar.sync orders shared memory without the
+// memory fence that a cluster-scope release takes
+template <typename T, int G, int U, typename V, bool ONE>
+__global__ void __launch_bounds__(kGsClThreads, 1)
+    k_gs_cluster(int n, int ncolours, const GsColours cp, int post, int x_zero,
+                 const int* __restrict__ rows, const int* __restrict__ rowptr,
+                 const int* __restrict__ col, const V* __restrict__ val, int64_t nnzb, T* x,
+                 const T* __restrict__ b, const T* __restrict__ dinv,
+                 const double* __restrict__ wt) {
+  extern __shared__ __align__(16) unsigned char gs_smem[];
+  T* xs = reinterpret_cast<T*>(gs_smem);
+  T* bs = xs + 4 * (int64_t)n;
+  int* rows_s = reinterpret_cast<int*>(bs + 4 * (int64_t)n);
+  int* rp_s = rows_s + n;
+  const int cs = ONE ? 1 : (int)cg::this_cluster().num_blocks();
+  const int rank = ONE ? 0 : (int)cg::this_cluster().block_rank();
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane & (G - 1);
+  const int warp = (rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+  const int nwarps = (cs * (int)blockDim.x) >> 5;
+  const int stride = nwarps * RPW;
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
+
+  for (int k = threadIdx.x; k < 4 * n; k += blockDim.x) {
+    xs[k] = x_zero ? T(0) : x[k];
+    bs[k] = __ldg(b + k);
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) rows_s[k] = __ldg(rows + k);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) rp_s[k] = __ldg(rowptr + k);
+  // every copy is complete before any CTA stores into another's
+  if constexpr (ONE) __syncthreads();
+  else cg::this_cluster().sync();
+
+  // operands of this group's next row
+  int pi = 0, pa = 0, pe = 0;
+  int pj[U];
+  T pv[U][9];
+  T pd[9];
+  auto load_row = [&](int g, int end) {
+    pa = pe = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) pj[u] = -1;
+    if (g >= end) return;
+    pi = rows_s[g];
+    pa = rp_s[g];
+    pe = rp_s[g + 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = pa + gl + u * G;
+      if (k < pe) {
+        pj[u] = __ldg(col + k);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) pv[u][q] = ldg_v<T>(val + q * nnzb + k);
+      }
+    }
+    if (gl == 0) {
+      const T* dp = dinv + 12 * (int64_t)pi;
+      ld3(dp, 0, pd[0], pd[1], pd[2]);
+      ld3(dp, 1, pd[3], pd[4], pd[5]);
+      ld3(dp, 2, pd[6], pd[7], pd[8]);
+    }
+  };
+  auto colour_of = [&](int q) { return post ? ncolours - 1 - q : q; };
+
+  {
+    const int c = colour_of(0);
+    load_row(cp.ptr[c] + warp * RPW + sub, cp.ptr[c + 1]);
+  }
+  for (int q = 0; q < ncolours; ++q) {
+    const int c = colour_of(q);
+    const int a = cp.ptr[c], e = cp.ptr[c + 1];
+    for (int base = a + warp * RPW; base < e; base += stride) {
+      const bool active = base + sub < e;
+      const int i = pi, ka = pa, ke = pe;
+      T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pj[u] < 0) continue;
+        T x0, x1, x2;
+        lds3(xs, pj[u], x0, x1, x2);
+        s0 = fma(pv[u][0], x0, s0); s0 = fma(pv[u][1], x1, s0); s0 = fma(pv[u][2], x2, s0);
+        s1 = fma(pv[u][3], x0, s1); s1 = fma(pv[u][4], x1, s1); s1 = fma(pv[u][5], x2, s1);
+        s2 = fma(pv[u][6], x0, s2); s2 = fma(pv[u][7], x1, s2); s2 = fma(pv[u][8], x2, s2);
+      }
+      // blocks beyond the U carried ones
+      for (int k = ka + gl + U * G; k < ke; k += G) {
+        const int jj = __ldg(col + k);
+        T x0, x1, x2;
+        lds3(xs, jj, x0, x1, x2);
+        const V* vv = val + k;
+        s0 = fma(ldg_v<T>(vv), x0, s0);
+        s0 = fma(ldg_v<T>(vv + nnzb), x1, s0);
+        s0 = fma(ldg_v<T>(vv + 2 * nnzb), x2, s0);
+        s1 = fma(ldg_v<T>(vv + 3 * nnzb), x0, s1);
+        s1 = fma(ldg_v<T>(vv + 4 * nnzb), x1, s1);
+        s1 = fma(ldg_v<T>(vv + 5 * nnzb), x2, s1);
+        s2 = fma(ldg_v<T>(vv + 6 * nnzb), x0, s2);
+        s2 = fma(ldg_v<T>(vv + 7 * nnzb), x1, s2);
+        s2 = fma(ldg_v<T>(vv + 8 * nnzb), x2, s2);
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      }
+      T n0 = T(0), n1 = T(0), n2 = T(0);
+      if (active && gl == 0) {
+        T xi0, xi1, xi2, b0, b1, b2;
+        lds3(xs, i, xi0, xi1, xi2);
+        lds3(bs, i, b0, b1, b2);
+        const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+        n0 = xi0 + om * (pd[0] * r0 + pd[1] * r1 + pd[2] * r2);
+        n1 = xi1 + om * (pd[3] * r0 + pd[4] * r1 + pd[5] * r2);
+        n2 = xi2 + om * (pd[6] * r0 + pd[7] * r1 + pd[8] * r2);
+      }
+      // the group's first lane holds the new value: every lane of the group
+      // takes it and stores it into the copies of ranks gl, gl + G, ...
+      n0 = __shfl_sync(0xffffffffu, n0, sub * G);
+      n1 = __shfl_sync(0xffffffffu, n1, sub * G);
+      n2 = __shfl_sync(0xffffffffu, n2, sub * G);
+      // the next row's operands in this colour
+      if (base + stride < e) load_row(base + stride + sub, e);
+      if (active) {
+        if constexpr (ONE) {
+          if (gl == 0) {
+            xs[4 * (int64_t)i] = n0;
+            xs[4 * (int64_t)i + 1] = n1;
+            xs[4 * (int64_t)i + 2] = n2;
+          }
+        } else {
+          for (int r = gl; r < cs; r += G) {
+            T* dst = cg::this_cluster().map_shared_rank(xs, (unsigned)r) + 4 * (int64_t)i;
+            dst[0] = n0;
+            dst[1] = n1;
+            dst[2] = n2;
+          }
+        }
+      }
+    }
+    if constexpr (ONE) {
+      if (q + 1 < ncolours) {
+        const int cn = colour_of(q + 1);
+        load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
+      }
+      __syncthreads();
+    } else {
+      // the barrier in two halves: the arrive releases this colour's stores; the
+      // next colour's first-row operands are loaded between the halves
+      cluster_arrive_release();
+      if (q + 1 < ncolours) {
+        const int cn = colour_of(q + 1);
+        load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
+      }
+      cluster_wait_acquire();
+    }
+  }
+  // every copy now holds the swept iterate: each CTA writes its share
+  for (int k = rank * (int)blockDim.x + (int)threadIdx.x; k < 4 * n; k += cs * (int)blockDim.x)
+    x[k] = xs[k];
+}
+
+// The largest cluster of `cs` CTAs with `smem` bytes each that can be resident
+// (0: cannot launch).
+template <typename T, int G, typename V>
+int gs_cluster_fits(int cs, int smem) {
+  constexpr int U = gs_cl_unroll<T, G, V>();
+  if (cs == 1) {
+    auto one = k_gs_cluster<T, G, U, V, true>;
+    max_dynamic_smem((const void*)one, kGsClSmemBytes);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, one, kGsClThreads, smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per;
+  }
+  auto kern = k_gs_cluster<T, G, U, V, false>;
+  max_dynamic_smem((const void*)kern, kGsClSmemBytes);
+  if (cs > 8 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(kGsClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
+}
+
+template <typename T, int G, typename V>
+void launch_gs_cluster_g(const Level& lv, int cs, bool post, bool x_zero, const V* val, T* x,
+                         const T* b, const T* dinv, cudaStream_t s) {
+  constexpr int U = gs_cl_unroll<T, G, V>();
+  // the shared-memory and cluster-size attributes were set by gs_cluster_fits
+  // when the level's cluster size was chosen
+  GsColours cp;
+  for (int c = 0; c <= lv.ncolours; ++c) cp.ptr[c] = lv.colour_ptr[c];
+  if (cs == 1) {
+    k_gs_cluster<T, G, U, V, true><<<1, kGsClThreads, (size_t)gs_cl_smem<T>(lv.n), s>>>(
+        lv.n, lv.ncolours, cp, (int)post, (int)x_zero, lv.k_rows(), lv.k_rowptr(), lv.k_col(),
+        val, lv.nnzb, x, b, dinv, (const double*)lv.wt);
+    return;
+  }
+  auto kern = k_gs_cluster<T, G, U, V, false>;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(kGsClThreads);
+  cfg.dynamicSmemBytes = (size_t)gs_cl_smem<T>(lv.n);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, kern, lv.n, lv.ncolours, cp, (int)post, (int)x_zero,
+                              lv.k_rows(), lv.k_rowptr(), lv.k_col(), val, lv.nnzb, x, b, dinv,
+                              (const double*)lv.wt));
+}
+
+template <typename T, typename V>
+void launch_gs_cluster_v(const Level& lv, int cs, int G, bool post, bool x_zero, const V* val,
+                         T* x, const T* b, const T* dinv, cudaStream_t s) {
+  switch (G) {
+    case 4: launch_gs_cluster_g<T, 4, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
+    case 8: launch_gs_cluster_g<T, 8, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
+    case 16: launch_gs_cluster_g<T, 16, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
+    default: launch_gs_cluster_g<T, 32, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
+  }
+}
+
+// A level can sweep in one cluster when it is coloured, stored in colour order,
+// has at most kGsClMaxColours colours and its iterate, right-hand side, row ids
+// and block offsets fit in shared memory.
+template <typename T>
+bool gs_cluster_eligible(const Level& lv) {
+  return lv.ncolours > 0 && lv.ncolours <= kGsClMaxColours && lv.k_rows() && lv.np == 0 &&
+         gs_cl_smem<T>(lv.n) <= kGsClSmemBytes;
+}
+
+template <typename T>
+int gs_cluster_fits_level(const Level& lv, int cs, int G) {
+  const int smem = (int)gs_cl_smem<T>(lv.n);
+  if constexpr (std::is_same<T, float>::value) {
+    if (lv.val16.p) {
+      switch (G) {
+        case 4: return gs_cluster_fits<float, 4, __nv_bfloat16>(cs, smem);
+        case 8: return gs_cluster_fits<float, 8, __nv_bfloat16>(cs, smem);
+        case 16: return gs_cluster_fits<float, 16, __nv_bfloat16>(cs, smem);
+        default: return gs_cluster_fits<float, 32, __nv_bfloat16>(cs, smem);
+      }
+    }
+  }
+  switch (G) {
+    case 4: return gs_cluster_fits<T, 4, T>(cs, smem);
+    case 8: return gs_cluster_fits<T, 8, T>(cs, smem);
+    case 16: return gs_cluster_fits<T, 16, T>(cs, smem);
+    default: return gs_cluster_fits<T, 32, T>(cs, smem);
+  }
+}
+
+// ------------------------------------------------------------------- FP32-pair operator
+
+// The Krylov operator y = K_0 x without FP64 arithmetic (FP64 instructions issue
+// at a small fraction of the FP32 rate on this GPU, and the FP64 product kernel
+// is bound by them, not by memory).  Every value a = a_hi + a_lo and vector
+// entry x = x_hi + x_lo is a pair of floats (the FP64 number to about 2^-48).
+// A product is a_hi x_hi exactly (rounded product p plus its error
+// fma(a_hi, x_hi, -p)) plus the cross terms a_hi x_lo + a_lo x_hi; a_lo x_lo
+// (about 2^-48 of the product) is dropped.  The rounded products are summed
+// with TwoSum (Knuth), whose error terms join the low-order accumulator, so the
+// row sum S + s carries about 2^-48 of sum |a_ij x_j|.  The sums use the _rn
+// intrinsics so that the compiler contracts none of them into an FMA.
+__device__ __forceinline__ void pair_fma(float& S, float& s, float2 a, float xh, float xl) {
+  const float p = __fmul_rn(a.x, xh);
+  float e = fmaf(a.x, xh, -p);
+  e = fmaf(a.x, xl, e);
+  e = fmaf(a.y, xh, e);
+  const float t = __fadd_rn(S, p);
+  const float bp = __fsub_rn(t, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  S = t;
+  s = __fadd_rn(s, __fadd_rn(err, e));
+}
+
+// (S, s) += (T, t) for the reduction across the lanes of a row
+__device__ __forceinline__ void pair_add(float& S, float& s, float T, float t) {
+  const float u = __fadd_rn(S, T);
+  const float bp = __fsub_rn(u, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(u, bp)), __fsub_rn(T, bp));
+  S = u;
+  s = __fadd_rn(s, __fadd_rn(err, t));
+}
+
+// One group of G lanes per block row (rows in the level's kernel layout, as the
+// FP64 operator kernel); each lane takes U blocks per step; x gathers are two
+// 16-byte loads (hi and lo of the node).
+template <int G, int U>
+__global__ void __launch_bounds__(256) k_apply_pair(int nrows, const int* __restrict__ rows,
+                                                    const int* __restrict__ rowptr,
+                                                    const int* __restrict__ col,
+                                                    const float2* __restrict__ val, int64_t nnzb,
+                                                    const float* __restrict__ xp,
+                                                    double* __restrict__ y) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane & (G - 1);
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const float4* xv = reinterpret_cast<const float4*>(xp);
+  for (int base = warp * RPW; base < nrows; base += nwarps * RPW) {
+    const int g = base + sub;
+    const bool active = g < nrows;
+    float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f, S2 = 0.f, s2 = 0.f;
+    if (active) {
+      const int a = __ldg(rowptr + g), e = __ldg(rowptr + g + 1);
+      for (int k0 = a + gl; k0 < e; k0 += U * G) {
+        int j[U];
+        float2 v[U][9];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u * G;
+          if (k < e) {
+            j[u] = __ldcs(col + k);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[u][q] = __ldcs(val + q * nnzb + k);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (k0 + u * G >= e) continue;
+          const float4 hi = __ldg(xv + 2 * (int64_t)j[u]);
+          const float4 lo = __ldg(xv + 2 * (int64_t)j[u] + 1);
+          pair_fma(S0, s0, v[u][0], hi.x, lo.x);
+          pair_fma(S0, s0, v[u][1], hi.y, lo.y);
+          pair_fma(S0, s0, v[u][2], hi.z, lo.z);
+          pair_fma(S1, s1, v[u][3], hi.x, lo.x);
+          pair_fma(S1, s1, v[u][4], hi.y, lo.y);
+          pair_fma(S1, s1, v[u][5], hi.z, lo.z);
+          pair_fma(S2, s2, v[u][6], hi.x, lo.x);
+          pair_fma(S2, s2, v[u][7], hi.y, lo.y);
+          pair_fma(S2, s2, v[u][8], hi.z, lo.z);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      float T = __shfl_xor_sync(0xffffffffu, S0, o), t = __shfl_xor_sync(0xffffffffu, s0, o);
+      pair_add(S0, s0, T, t);
+      T = __shfl_xor_sync(0xffffffffu, S1, o); t = __shfl_xor_sync(0xffffffffu, s1, o);
+      pair_add(S1, s1, T, t);
+      T = __shfl_xor_sync(0xffffffffu, S2, o); t = __shfl_xor_sync(0xffffffffu, s2, o);
+      pair_add(S2, s2, T, t);
+    }
+    if (!active || gl != 0) continue;
+    const int i = rows ? __ldg(rows + g) : g;
+    st3(y, i, (double)S0 + (double)s0, (double)S1 + (double)s1, (double)S2 + (double)s2);
+  }
+}
+
+template <int G>
+void launch_apply_pair(const Level& lv, const float* xp, double* y, cudaStream_t s) {
+  constexpr int U = G >= 16 ? 1 : 2;
+  const int grid = (int)std::max<int64_t>(1, ((int64_t)lv.n * G + 255) / 256);
+  k_apply_pair<G, U><<<grid, 256, 0, s>>>(lv.n, lv.k_rows(), lv.k_rowptr(), lv.k_col(),
+                                          lv.val2.p, lv.nnzb, xp, y);
+}
+
 // Residual r = b - K x restricted to the unknowns of one Vanka colour: the velocity
 // nodes of its patches (warp per node, one block of the node's A row and one entry
 // of its B^T row per lane and step) and the pressure unknowns of its patches (the
@@ -1003,6 +1439,22 @@ struct Emit {
     }
     put(P, nrows, G);
   }
+  // a level's whole colour sweep as one cluster launch (never recorded)
+  void gs_cluster(Level& lv, T* x, const T* b, bool post, bool x_zero) {
+    const T* dinv = LvVec<T>::dinv(lv);
+    if constexpr (std::is_same<T, float>::value) {
+      if (lv.val16.p) {
+        launch_gs_cluster_v<float, __nv_bfloat16>(
+            lv, lv.gs_cl, lv.gs_cl_g, post, x_zero,
+            reinterpret_cast<const __nv_bfloat16*>(lv.val16.p), x, b, dinv, h->stream);
+        h->launches++;
+        return;
+      }
+    }
+    launch_gs_cluster_v<T, T>(lv, lv.gs_cl, lv.gs_cl_g, post, x_zero, LvVec<T>::val(lv), x, b,
+                              dinv, h->stream);
+    h->launches++;
+  }
   void zero(T* a, int64_t n) {
     Phase P = blank(PH_ZERO);
     P.y = a; P.n = (int)n;
@@ -1152,6 +1604,11 @@ template <typename T>
 void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
               bool x_is_zero) {
   const int dofs = lv.dofs4();
+  if (!e.rec && lv.gs_cl > 0 && lv.gs_cl_bytes == (int)sizeof(T) && !h->saddle &&
+      h->opt.smoother == AMG_SMOOTHER_GS) {
+    e.gs_cluster(lv, x, b, post, x_is_zero);
+    return;
+  }
   if (x_is_zero) e.zero(x, dofs);
   const int G = group_for(lv);
   const T* val = LvVec<T>::val(lv);
@@ -1470,6 +1927,18 @@ void precondition_device<float>(amg_handle* h, const double* r, double* z) {
   launch_to_double(lv.x32, z, n, h->stream, h);
 }
 
+void apply_pair(amg_handle* h, const float* xp, double* y) {
+  const Level& lv = *h->L[0];
+  if (!lv.val2.p) fail(AMG_ERR_INVALID, "the FP32-pair operator needs an FP32 SPD handle with outer_pair");
+  switch (lv.group_pair) {
+    case 4: launch_apply_pair<4>(lv, xp, y, h->stream); break;
+    case 8: launch_apply_pair<8>(lv, xp, y, h->stream); break;
+    case 32: launch_apply_pair<32>(lv, xp, y, h->stream); break;
+    default: launch_apply_pair<16>(lv, xp, y, h->stream); break;
+  }
+  h->launches++;
+}
+
 void level_transfer(amg_handle* h, int l, bool restrict_, bool f32) {
   Level& lv = *h->L[l];
   Level& nx = *h->L[l + 1];
@@ -1511,6 +1980,7 @@ void autotune_levels(amg_handle* h) {
   const bool f32 = h->opt.precision == AMG_FP32;
   for (size_t l = 0; l < h->L.size(); ++l) {
     Level& lv = *h->L[l];
+    lv.gs_cl = 0;
     int best = 0;
     float best_ms = 1e30f;
     for (int G : {4, 8, 16, 32}) {
@@ -1538,6 +2008,24 @@ void autotune_levels(amg_handle* h) {
       }
       lv.group64 = best;
     }
+    if (l == 0 && lv.val2.p) {   // the FP32-pair Krylov operator
+      DBuf<float> xp;
+      xp.alloc(8 * (size_t)lv.n);
+      AMG_CUDA(cudaMemsetAsync(xp.p, 0, xp.bytes(), s));
+      best = 0;
+      best_ms = 1e30f;
+      for (int G : {4, 8, 16, 32}) {
+        lv.group_pair = G;
+        for (int r = 0; r < 7; ++r) {
+          if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+          apply_pair(h, xp.p, lv.r64.p);
+        }
+        const float ms = elapsed();
+        if (ms < best_ms) { best_ms = ms; best = G; }
+      }
+      lv.group_pair = best;
+      AMG_CUDA(cudaStreamSynchronize(s));
+    }
     if (lv.ncolours == 0 || h->saddle || h->opt.smoother != AMG_SMOOTHER_GS) continue;
     best = 0;
     best_ms = 1e30f;
@@ -1552,6 +2040,45 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group_gs = best;
+    // the sweep as one cluster launch with the iterate in shared memory: the
+    // forced cluster size, else the fastest (cluster size, lanes per row) if it
+    // beats one launch per colour
+    const bool elig = f32 ? gs_cluster_eligible<float>(lv) : gs_cluster_eligible<double>(lv);
+    if (!elig || h->opt.gs_cluster == 0) continue;
+    lv.gs_cl_bytes = f32 ? 4 : 8;
+    auto fits = [&](int cs, int G) {
+      return f32 ? gs_cluster_fits_level<float>(lv, cs, G)
+                 : gs_cluster_fits_level<double>(lv, cs, G);
+    };
+    auto sweeps_ms = [&]() {
+      for (int r = 0; r < 7; ++r) {
+        if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) level_smooth<float>(h, (int)l, lv.x32.p, lv.b32.p, false, false);
+        else level_smooth<double>(h, (int)l, lv.x64.p, lv.b64.p, false, false);
+      }
+      return elapsed();
+    };
+    if (h->opt.gs_cluster > 0) {
+      const int G = lv.group_gs;
+      if (fits(h->opt.gs_cluster, G) >= 1) {
+        lv.gs_cl = h->opt.gs_cluster;
+        lv.gs_cl_g = G;
+      }
+      continue;
+    }
+    float t_best = sweeps_ms();
+    int cs_best = 0, g_best = 0;
+    for (int cs : {1, 2, 4, 8, 16}) {
+      for (int G : {8, 16, 32}) {
+        if (fits(cs, G) < 1) continue;
+        lv.gs_cl = cs;
+        lv.gs_cl_g = G;
+        const float t = sweeps_ms();
+        if (t < t_best) { t_best = t; cs_best = cs; g_best = G; }
+      }
+    }
+    lv.gs_cl = cs_best;
+    lv.gs_cl_g = g_best;
   }
   // cluster sub-cycle: the largest cluster that fits (16, else 8 CTAs), then the
   // fastest start level among 1..L (or none)

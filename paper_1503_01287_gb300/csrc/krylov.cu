@@ -123,6 +123,22 @@ __global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __rest
     p[k] = fma(beta, p[k], z[k]);
 }
 
+// the same, also writing p in the pair form of the FP32-pair operator (8 floats
+// a node: hi of the 4 padded entries, then lo; lo = fl32(p - hi))
+__global__ void k_cg_dir_pair(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                              const double* __restrict__ s, float* __restrict__ pf) {
+  const double beta = s[S_BETA];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fma(beta, p[k], z[k]);
+    p[k] = v;
+    const float hi = (float)v;
+    const int64_t o = 8 * (k >> 2) + (k & 3);
+    pf[o] = hi;
+    pf[o + 4] = (float)(v - (double)hi);
+  }
+}
+
 // w -= sum_i c[i] V_i  (c on the device)
 __global__ void k_basis_sub(int64_t n, int m, const double* __restrict__ V, int64_t ldv,
                             const double* __restrict__ c, double* __restrict__ w) {
@@ -252,6 +268,8 @@ int solve_cg(amg_handle* h, Ctx& c, const double* b, double* x, double tol, bool
   precond(h, r, z);
   c.dots(r, z, S_RZ);
   launch_copy(z, p, n, s, h);
+  // FP32 cycle: the operator products in FP32-pair arithmetic (outer_pair)
+  float* pf = (h->opt.precision == AMG_FP32 && h->L[0]->val2.p) ? h->kpf.p : nullptr;
 
   // the body of one iteration after the first: z = M r, beta, p, q = A p, alpha, x, r
   auto body = [&](bool first) {
@@ -260,10 +278,14 @@ int solve_cg(amg_handle* h, Ctx& c, const double* b, double* x, double tol, bool
       if (flexible) c.dots(r, z, S_RZN, z, ro);
       else c.dots(r, z, S_RZN);
       k_cg_beta<<<1, 1, 0, s>>>(h->scal.p, flexible ? 1 : 0);
-      k_cg_dir<<<gridr(n), 256, 0, s>>>(n, p, z, h->scal.p);
+      if (pf) k_cg_dir_pair<<<gridr(n), 256, 0, s>>>(n, p, z, h->scal.p, pf);
+      else k_cg_dir<<<gridr(n), 256, 0, s>>>(n, p, z, h->scal.p);
       h->launches += 2;
+    } else if (pf) {
+      launch_split_pair(p, pf, n, s, h);
     }
-    apply_K(h, p, q);
+    if (pf) apply_pair(h, pf, q);
+    else apply_K(h, p, q);
     c.dots(p, q, S_PQ);
     k_cg_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p, q, ro, h->scal.p, h->red);
     k_final<<<1, 256, 0, s>>>(h->red, kReduceBlocks, 1, h->scal.p + S_RR);
@@ -522,6 +544,10 @@ int solve_device(amg_handle* h, const double* b_user, double* x_user, double tol
   };
   ensure(h->kb, n); ensure(h->kx, n);
   ensure(h->kr, n); ensure(h->kz, n); ensure(h->kp, n); ensure(h->kq, n); ensure(h->kw, n);
+  if (lv.val2.p && (int64_t)h->kpf.n < 2 * n) {
+    h->kpf.alloc(2 * n);
+    AMG_CUDA(cudaMemsetAsync(h->kpf.p, 0, h->kpf.bytes(), h->stream));
+  }
   ensure(h->red, (int64_t)kReduceBlocks * kMaxDots);
   ensure(h->scal, 64);
   if (!h->it_dev.p) h->it_dev.alloc(1);

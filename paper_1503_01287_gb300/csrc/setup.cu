@@ -146,6 +146,30 @@ __global__ void k_to_bf16(const double* __restrict__ a, unsigned short* __restri
     b[k] = __bfloat16_as_ushort(__double2bfloat16(a[k]));
 }
 
+// FP64 -> (hi, lo) float pairs: hi = fl32(a), lo = fl32(a - hi); hi + lo equals
+// a to about 2^-48 relative (a - hi is exact in FP64)
+__global__ void k_split_pair(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[k];
+    const float hi = (float)v;
+    b[k] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+// a padded FP64 vector (4 entries a node) -> 8 floats a node: the hi parts of
+// the node's 4 entries, then the lo parts
+__global__ void k_split_vec(const double* __restrict__ x, float* __restrict__ xp, int64_t n4) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n4;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[k];
+    const float hi = (float)v;
+    const int64_t o = 8 * (k >> 2) + (k & 3);
+    xp[o] = hi;
+    xp[o + 4] = (float)(v - (double)hi);
+  }
+}
+
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -239,6 +263,11 @@ void launch_copy(const double* a, double* b, int64_t n, cudaStream_t s, amg_hand
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s, amg_handle* h) {
   if (n <= 0) return;
   k_d2f<<<grid_for(n), 256, 0, s>>>(a, b, n);
+  h->launches++;
+}
+void launch_split_pair(const double* x, float* xp, int64_t n4, cudaStream_t s, amg_handle* h) {
+  if (n4 <= 0) return;
+  k_split_vec<<<grid_for(n4), 256, 0, s>>>(x, xp, n4);
   h->launches++;
 }
 void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s, amg_handle* h) {
@@ -1110,6 +1139,12 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
     if (h->bf16_coarse && &lv != h->L[0].get() && lv.nnzb > 0) {
       lv.val16.alloc(9 * (size_t)lv.nnzb);
       k_to_bf16<<<grid_for(9 * lv.nnzb), 256, 0, s>>>(lv.k_val(), lv.val16, 9 * lv.nnzb);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
+    if (&lv == h->L[0].get() && !h->saddle && h->opt.outer_pair && lv.nnzb > 0) {
+      lv.val2.alloc(9 * (size_t)lv.nnzb);
+      k_split_pair<<<grid_for(9 * lv.nnzb), 256, 0, s>>>(lv.k_val(), lv.val2, 9 * lv.nnzb);
       AMG_LAUNCH_CHECK();
       h->launches++;
     }
