@@ -614,7 +614,8 @@ def run_batched(args):
     handles, Bs, Xs = [], [], []
     t0 = time.perf_counter()
     for p in probs:
-        h = B.setup_problem(p, B.default_options(precision=B.AMG_FP32))
+        h = B.setup_problem(p, B.default_options(precision=B.AMG_FP32,
+                                                  outer_pair=args.outer_pair))
         handles.append(h)
         Bs.append(torch.from_numpy(np.ascontiguousarray(p.f.reshape(args.rhs, -1))).cuda())
         Xs.append(torch.zeros(args.rhs * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
@@ -636,7 +637,9 @@ def run_batched(args):
                   f"({args.batch} uneven problems x {args.rhs} RHS, FP32 V-cycle, FCG)",
         "value": dof_rhs / (ms * 1e-3), "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 cycle + f64 outer", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": ("f32 cycle + f32-pair Krylov operator + f64 vectors" if args.outer_pair
+                  else "f32 cycle + f64 outer"), "data": "synthetic",
         "config": {"workload": f"batched_elast: {args.batch} problems, n in "
                                f"{min(sp['n'] for sp in specs)}..{max(sp['n'] for sp in specs)}",
                    "dof_total": sum(p.n_dof for p in probs), "rhs": args.rhs, "tol": TOL},
@@ -677,7 +680,7 @@ def main():
     ap.add_argument("--cycle-kernel", type=int, default=1,
                     help="profile: 1 per-operation launches, 2 persistent cycle")
     ap.add_argument("--outer-pair", type=int, default=1, choices=[0, 1],
-                    help="elasticity: Krylov operator in FP32 pairs (1) or FP64 (0)")
+                    help="elasticity, batched: Krylov operator in FP32 pairs (1) or FP64 (0)")
     ap.add_argument("--gs-cluster", type=int, default=-1,
                     help="elasticity: one-cluster colour sweeps (-1 timed, 0 off, k CTAs)")
     args = ap.parse_args()

@@ -182,6 +182,7 @@ struct BatchLevel {
   DBuf<float> x32, b32, r32, t32;
   int tile = 0;     // block-row tile of the cycle's SpMM kernels (chosen by timing)
   int tile64 = 0;   // the same for the FP64 operator (level 0)
+  int tile_pair = 0;   // the same for the FP32-pair operator (level 0)
 };
 
 }  // namespace amgp2
@@ -233,6 +234,7 @@ struct amg_handle {
   // batched (multi-right-hand-side) solves
   std::vector<amgp2::BatchLevel> B;
   amgp2::DBuf<double> mb, mx, mr, mz, mp, mq, mro, bred, bscal;
+  amgp2::DBuf<float> mpf;           // the directions in pair form (FP32-pair operator)
   amgp2::DBuf<int> bit;
   amgp2::DBuf<double> wts;          // 4 learned weights per level (see Level::wt)
   bool bf16_coarse = false;         // AMG_FP32_BF16: levels >= 1 keep BF16 values

@@ -8,7 +8,8 @@
 // for all right-hand sides is one contiguous 16 x 16-byte (FP32) access.
 //
 // Each problem runs flexible CG per right-hand side (Polak-Ribiere beta, the
-// FP64 outer iteration of the FP32 or FP64 cycle); converged right-hand sides
+// FP64 outer iteration of the FP32 or FP64 cycle; with the FP32 cycle the
+// operator products K p are FP32-pair SpMM, see k_apply_pair_m); converged right-hand sides
 // are frozen (alpha = beta = 0).  The whole batch is ONE CUDA graph: one branch
 // per problem, each branch an initial block followed by a conditional WHILE
 // node whose body is one iteration and its device-side stopping test.
@@ -99,6 +100,53 @@ __global__ void __launch_bounds__(256) k_rows_m(int nrows, const int* __restrict
   T x0, x1, x2;
   ld3(x, o, x0, x1, x2);
   st3(y, o, x0 + omega * c0, x1 + omega * c1, x2 + omega * c2);
+}
+
+// y = K_0 x for all right-hand sides in FP32-pair arithmetic (pair_fma): the
+// values are (hi, lo) float pairs, x holds 8 floats a (node, right-hand side)
+// -- hi of the 4 padded entries, then lo -- and y is FP64.  Tiles as k_rows_m.
+template <int S, int U>
+__global__ void __launch_bounds__(256) k_apply_pair_m(int nrows, const int* __restrict__ rows,
+                                                      const int* __restrict__ rowptr,
+                                                      const int* __restrict__ col,
+                                                      const float2* __restrict__ val,
+                                                      int64_t nnzb, const float* __restrict__ xp,
+                                                      double* __restrict__ y) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) / (K * S);
+  const int q = (threadIdx.x / K) % S;
+  const int r = threadIdx.x % K;
+  if (g >= nrows) return;                       // uniform over the S groups of a row
+  const int i = rows ? ldg(rows + g) : g;
+  const int a = ldg(rowptr + g), e = ldg(rowptr + g + 1);
+  const float4* xv = reinterpret_cast<const float4*>(xp);
+  float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f, S2 = 0.f, s2 = 0.f;
+#pragma unroll U
+  for (int k = a + q; k < e; k += S) {
+    const int j = ldg(col + k);
+    const float4 hi = ldg(xv + 2 * ((int64_t)j * K + r));
+    const float4 lo = ldg(xv + 2 * ((int64_t)j * K + r) + 1);
+    const float2* v = val + k;
+    pair_fma(S0, s0, ldg(v), hi.x, lo.x);
+    pair_fma(S0, s0, ldg(v + nnzb), hi.y, lo.y);
+    pair_fma(S0, s0, ldg(v + 2 * nnzb), hi.z, lo.z);
+    pair_fma(S1, s1, ldg(v + 3 * nnzb), hi.x, lo.x);
+    pair_fma(S1, s1, ldg(v + 4 * nnzb), hi.y, lo.y);
+    pair_fma(S1, s1, ldg(v + 5 * nnzb), hi.z, lo.z);
+    pair_fma(S2, s2, ldg(v + 6 * nnzb), hi.x, lo.x);
+    pair_fma(S2, s2, ldg(v + 7 * nnzb), hi.y, lo.y);
+    pair_fma(S2, s2, ldg(v + 8 * nnzb), hi.z, lo.z);
+  }
+  if (S == 2) {   // the two groups of a row are the two halves of one warp
+    float T = __shfl_xor_sync(0xffffffffu, S0, 16), t = __shfl_xor_sync(0xffffffffu, s0, 16);
+    pair_add(S0, s0, T, t);
+    T = __shfl_xor_sync(0xffffffffu, S1, 16); t = __shfl_xor_sync(0xffffffffu, s1, 16);
+    pair_add(S1, s1, T, t);
+    T = __shfl_xor_sync(0xffffffffu, S2, 16); t = __shfl_xor_sync(0xffffffffu, s2, 16);
+    pair_add(S2, s2, T, t);
+    if (q != 0) return;
+  }
+  st3(y, i * K + r, (double)S0 + (double)s0, (double)S1 + (double)s1,
+      (double)S2 + (double)s2);
 }
 
 // bc_(I,r) = sum_t w_t v_(i_t, r)
@@ -295,12 +343,21 @@ __global__ void k_beta_m(double* s) {
   s[M_RZ * K + r] = s[M_RZN * K + r];
 }
 
+// p = z + beta p per right-hand side; with pf, also p's pair form (8 floats a
+// (node, right-hand side): hi of the 4 padded entries, then lo = fl32(p - hi))
 __global__ void k_dir_m(int64_t nel, double* __restrict__ p, const double* __restrict__ z,
-                        const double* __restrict__ s) {
+                        const double* __restrict__ s, float* __restrict__ pf) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nel;
        f += (int64_t)gridDim.x * blockDim.x) {
     const int rhs = (int)((f >> 2) % K);
-    p[f] = fma(s[M_BETA * K + rhs], p[f], z[f]);
+    const double v = fma(s[M_BETA * K + rhs], p[f], z[f]);
+    p[f] = v;
+    if (pf) {
+      const float hi = (float)v;
+      const int64_t o = 8 * (f >> 2) + (f & 3);
+      pf[o] = hi;
+      pf[o + 4] = (float)(v - (double)hi);
+    }
   }
 }
 
@@ -517,6 +574,25 @@ void launch_tile_m(int tile, int nrows, const int* rows, const int* rowptr, Leve
   }
 }
 
+template <int S, int U>
+void launch_pair_m(const Level& lv, const float* xp, double* y, cudaStream_t s) {
+  const int grid = (int)(((int64_t)lv.n * K * S + 255) / 256);
+  k_apply_pair_m<S, U><<<grid, 256, 0, s>>>(lv.n, lv.k_rows(), lv.k_rowptr(), lv.k_col(),
+                                            lv.val2.p, lv.nnzb, xp, y);
+}
+
+// y = K_0 x (FP32-pair operator, x in pair form) with the given tile
+void apply_pair_m(amg_handle* h, const float* xp, double* y, int tile) {
+  const Level& lv = *h->L[0];
+  switch (tile) {
+    case 1: launch_pair_m<2, 2>(lv, xp, y, h->stream); break;
+    case 2: launch_pair_m<1, 4>(lv, xp, y, h->stream); break;
+    case 3: launch_pair_m<2, 4>(lv, xp, y, h->stream); break;
+    default: launch_pair_m<1, 2>(lv, xp, y, h->stream); break;
+  }
+  h->launches++;
+}
+
 template <typename T>
 void rows_m(amg_handle* h, int mode, Level& lv, int first, int nrows, const T* val, const T* x,
             const T* b, T* y, const T* dinv, T omega, int tile) {
@@ -669,6 +745,34 @@ int tune_tile(amg_handle* h, Level& lv, const T* val, const T* x, T* y) {
   return best;
 }
 
+// the same for the FP32-pair operator of level 0
+int tune_pair_tile(amg_handle* h) {
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int t = 0; t < kTiles; ++t) {
+    for (int r = 0; r < 7; ++r) {
+      if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+      apply_pair_m(h, h->mpf, h->mq, t);
+    }
+    AMG_CUDA(cudaEventRecord(e1, s));
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
 void alloc_batch(amg_handle* h) {
   if (!h->B.empty()) return;
   if (h->saddle) fail(AMG_ERR_UNSUPPORTED, "batched solves are provided for the SPD kinds");
@@ -691,6 +795,8 @@ void alloc_batch(amg_handle* h) {
   const int64_t n0 = 4 * (int64_t)K * h->L[0]->n;
   z64(h->mb, n0); z64(h->mx, n0); z64(h->mr, n0); z64(h->mz, n0);
   z64(h->mp, n0); z64(h->mq, n0); z64(h->mro, n0);
+  // FP32 cycle with the FP32-pair Krylov operator: the directions in pair form
+  if (f32 && h->L[0]->val2.p) z32(h->mpf, 2 * n0);
   h->bred.alloc((size_t)kDotBlocks * 2 * K);
   h->bscal.alloc((size_t)M_NS * K);
   h->bit.alloc(1);
@@ -707,6 +813,7 @@ void alloc_batch(amg_handle* h) {
   }
   h->B[0].tile64 = fixed >= 0 ? fixed
                               : tune_tile<double>(h, *h->L[0], h->L[0]->k_val(), h->mx, h->mq);
+  if (h->mpf.p) h->B[0].tile_pair = fixed >= 0 ? fixed : tune_pair_tile(h);
 }
 
 // initial block of one problem: x = 0, r = b, z = M r, rz, p = z, active set
@@ -725,13 +832,15 @@ void emit_init(amg_handle* h, const double* bu, int nrhs, double tol) {
   dots_m(h, M_RZ, h->mr, h->mz);
   k_copy_m<double><<<gridk(nel), 256, 0, s>>>(h->mz, h->mp, nel);
   h->launches++;
+  if (h->mpf.p) launch_split_pair(h->mp, h->mpf, nel, s, h);
 }
 
 // one iteration of flexible CG per right-hand side and the stopping test
 void emit_iteration(amg_handle* h, cudaGraphConditionalHandle cond) {
   cudaStream_t s = h->stream;
   const int64_t nel = 4 * (int64_t)K * h->L[0]->n;
-  apply_m64(h, h->mp, h->mq);
+  if (h->mpf.p) apply_pair_m(h, h->mpf, h->mq, h->B[0].tile_pair);
+  else apply_m64(h, h->mp, h->mq);
   dots_m(h, M_PQ, h->mp, h->mq);
   k_update_m<<<kDotBlocks, kDotThreads, 0, s>>>(nel, h->mx, h->mr, h->mp, h->mq, h->mro,
                                                 h->bscal, h->bred);
@@ -741,7 +850,7 @@ void emit_iteration(amg_handle* h, cudaGraphConditionalHandle cond) {
   precond_m(h, h->mr, h->mz);
   dots_m(h, M_RZN, h->mr, h->mz, h->mz, h->mro);
   k_beta_m<<<1, 32, 0, s>>>(h->bscal);
-  k_dir_m<<<gridk(nel), 256, 0, s>>>(nel, h->mp, h->mz, h->bscal);
+  k_dir_m<<<gridk(nel), 256, 0, s>>>(nel, h->mp, h->mz, h->bscal, h->mpf.p);
   h->launches += 2;
 }
 

@@ -1039,29 +1039,8 @@ int gs_cluster_fits_level(const Level& lv, int cs, int G) {
 // fma(a_hi, x_hi, -p)) plus the cross terms a_hi x_lo + a_lo x_hi; a_lo x_lo
 // (about 2^-48 of the product) is dropped.  The rounded products are summed
 // with TwoSum (Knuth), whose error terms join the low-order accumulator, so the
-// row sum S + s carries about 2^-48 of sum |a_ij x_j|.  The sums use the _rn
-// intrinsics so that the compiler contracts none of them into an FMA.
-__device__ __forceinline__ void pair_fma(float& S, float& s, float2 a, float xh, float xl) {
-  const float p = __fmul_rn(a.x, xh);
-  float e = fmaf(a.x, xh, -p);
-  e = fmaf(a.x, xl, e);
-  e = fmaf(a.y, xh, e);
-  const float t = __fadd_rn(S, p);
-  const float bp = __fsub_rn(t, S);
-  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-  S = t;
-  s = __fadd_rn(s, __fadd_rn(err, e));
-}
-
-// (S, s) += (T, t) for the reduction across the lanes of a row
-__device__ __forceinline__ void pair_add(float& S, float& s, float T, float t) {
-  const float u = __fadd_rn(S, T);
-  const float bp = __fsub_rn(u, S);
-  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(u, bp)), __fsub_rn(T, bp));
-  S = u;
-  s = __fadd_rn(s, __fadd_rn(err, t));
-}
-
+// row sum S + s carries about 2^-48 of sum |a_ij x_j| (pair_fma, pair_add).
+//
 // One group of G lanes per block row (rows in the level's kernel layout, as the
 // FP64 operator kernel); each lane takes U blocks per step; x gathers are two
 // 16-byte loads (hi and lo of the node).
@@ -1929,7 +1908,8 @@ void precondition_device<float>(amg_handle* h, const double* r, double* z) {
 
 void apply_pair(amg_handle* h, const float* xp, double* y) {
   const Level& lv = *h->L[0];
-  if (!lv.val2.p) fail(AMG_ERR_INVALID, "the FP32-pair operator needs an FP32 SPD handle with outer_pair");
+  if (!lv.val2.p)
+    fail(AMG_ERR_INVALID, "the FP32-pair operator needs an FP32 SPD handle with outer_pair");
   switch (lv.group_pair) {
     case 4: launch_apply_pair<4>(lv, xp, y, h->stream); break;
     case 8: launch_apply_pair<8>(lv, xp, y, h->stream); break;

@@ -44,4 +44,31 @@ __device__ __forceinline__ void st3(double* p, int j, double a, double b, double
                : "memory");
 }
 
+// FP32-pair arithmetic of the Krylov operator: (S, s) += a x with a = (a.x, a.y)
+// = hi + lo and x = xh + xl.  The product a.x xh is exact as the rounded product
+// p plus its error fma(a.x, xh, -p); the cross terms a.x xl + a.y xh join the
+// error, a.y xl (about 2^-48 of the product) is dropped; p is added to S with
+// TwoSum (Knuth) and the sum's error with the product's error to s.  The _rn
+// intrinsics keep the compiler from contracting any of these into an FMA.
+__device__ __forceinline__ void pair_fma(float& S, float& s, float2 a, float xh, float xl) {
+  const float p = __fmul_rn(a.x, xh);
+  float e = fmaf(a.x, xh, -p);
+  e = fmaf(a.x, xl, e);
+  e = fmaf(a.y, xh, e);
+  const float t = __fadd_rn(S, p);
+  const float bp = __fsub_rn(t, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  S = t;
+  s = __fadd_rn(s, __fadd_rn(err, e));
+}
+
+// (S, s) += (T, t) for the reduction across the lanes of a row
+__device__ __forceinline__ void pair_add(float& S, float& s, float T, float t) {
+  const float u = __fadd_rn(S, T);
+  const float bp = __fsub_rn(u, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(u, bp)), __fsub_rn(T, bp));
+  S = u;
+  s = __fadd_rn(s, __fadd_rn(err, t));
+}
+
 }  // namespace amgp2

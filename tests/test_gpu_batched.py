@@ -43,16 +43,18 @@ def _rhs(prob, k, rng):
     return out
 
 
-@pytest.mark.parametrize("precision,k,tile", [(0, 5, -1), (1, 5, -1), (1, 16, -1), (1, 1, -1),
-                                             (1, 5, 0), (1, 5, 1), (1, 5, 2), (1, 5, 3),
-                                             (0, 3, 1), (0, 3, 3)])
-def test_batched_matches_single_and_direct(precision, k, tile):
-    """tile -1: the SpMM tile chosen per level by timing; 0..3: each tile forced."""
+@pytest.mark.parametrize("precision,k,tile,pair", [
+    (0, 5, -1, 1), (1, 5, -1, 1), (1, 16, -1, 1), (1, 1, -1, 1), (1, 5, 0, 1), (1, 5, 1, 1),
+    (1, 5, 2, 1), (1, 5, 3, 1), (0, 3, 1, 1), (0, 3, 3, 1), (1, 5, -1, 0), (1, 16, 3, 0)])
+def test_batched_matches_single_and_direct(precision, k, tile, pair):
+    """tile -1: the SpMM tile chosen per level by timing; 0..3: each tile forced.
+    pair: with the FP32 cycle, the operator products in FP32 pairs (1) or FP64 (0)."""
     probs = _problems()
     rng = np.random.default_rng(7)
     handles, Bs, Xs, rhs = [], [], [], []
     for p in probs:
-        h = B().setup_problem(p, B().default_options(precision=precision, batch_tile=tile))
+        h = B().setup_problem(p, B().default_options(precision=precision, batch_tile=tile,
+                                                     outer_pair=pair))
         r = _rhs(p, k, rng)
         if k >= 3:
             r[2] = 0.0                       # a zero right-hand side converges at once
