@@ -265,7 +265,8 @@ int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t
     AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (ferr) {
       AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
-      fail(AMG_ERR_TIMEOUT, "a bounded device wait (grid barrier) timed out during the solve");
+      fail(AMG_ERR_TIMEOUT, "a bounded device wait (grid barrier or mbarrier) timed out during "
+                            "the solve");
     }
     float ms = 0.f;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -500,6 +501,12 @@ int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
     launch_from_padded(lv.x64, x, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
+    int ferr = 0;
+    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ferr) {
+      AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
+      fail(AMG_ERR_TIMEOUT, "an mbarrier wait of the one-launch colour sweep timed out");
+    }
     return AMG_OK;
   });
 }

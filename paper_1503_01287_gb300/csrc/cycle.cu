@@ -699,32 +699,42 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
                               (const T*)P.dinv, P.wt));
 }
 
-// Multicolour Gauss-Seidel sweep of one small level as ONE launch of a
-// thread-block cluster.  Every CTA keeps in shared memory the level's whole
+// Multicolour Gauss-Seidel sweep of one small level as ONE launch: a single CTA,
+// or a thread-block cluster.  Every CTA keeps in shared memory the level's whole
 // iterate x and right-hand side b (4 values a node) and the row ids and block
-// offsets of the colour-ordered rows; the colours run in sweep order with a
-// cluster barrier between them, and a row's new value is stored into the x copy
-// of every CTA of the cluster (distributed shared memory).  After a barrier a
-// row update therefore reads global memory only for its block columns and values
-// and D_i^{-1}, at addresses known from shared memory: one L2 round trip, which
-// each group of G lanes starts for its next row before the barrier it must
-// wait at (between the barrier's arrive and wait, so that neither waits for the
-// other).  Rows of one colour share no block, so the updates of a colour never
-// read a value written in the same colour (the row's own x_i is read before its
-// own update).
+// offsets of the colour-ordered rows, so a row update reads global memory only
+// for its block columns and values and D_i^{-1}, at addresses known from shared
+// memory; each group of G lanes loads its next row's operands before it waits
+// for the colour it must follow.  The colours run in sweep order.
+//   single CTA: the new value of a row goes to shared memory; __syncthreads
+//   between the colours.
+//   cluster: the new value of a row goes to the x copy of every CTA of the
+//   cluster by st.async (distributed shared memory), which counts its bytes on
+//   the receiving CTA's mbarrier of that step of the sweep (one mbarrier a
+//   colour, each completing one phase); a warp starts a colour once every row
+//   of the previous colour has arrived.  That also orders the reads: a row's
+//   value is sent after its owner has read every x_j of the row, so a value of
+//   colour q + 1 can reach a CTA only after all reads of colour q have been
+//   done.  No cluster barrier or memory fence is needed between the colours.
+// Rows of one colour share no block, so the updates of a colour never read a
+// value written in the same colour (the row's own x_i is read before its own
+// update).  Every mbarrier wait is bounded: after kMbarSpins polls the CTA sets
+// *err and stops waiting.
 constexpr int kGsClThreads = 512;
 constexpr int kGsClMaxColours = 127;
 constexpr int kGsClSmemBytes = 200 * 1024;
+constexpr unsigned kMbarSpins = 1u << 18;
 
 struct GsColours {
   int ptr[kGsClMaxColours + 1];   // stored rows of colour c: ptr[c] .. ptr[c+1]
 };
 
-// shared memory of the one-cluster sweep: x and b (4 n values each), the row id
-// and the first block of every stored row (n + 1 offsets)
+// shared memory of the one-launch sweep: an mbarrier a colour (1 KB), x and b
+// (4 n values each), the row id and the first block of every stored row
+constexpr int kGsClBarBytes = 8 * (kGsClMaxColours + 1);
 template <typename T>
 constexpr int64_t gs_cl_smem(int64_t n) {
-  return 8 * n * (int64_t)sizeof(T) + 4 * n + 4 * (n + 1);
+  return kGsClBarBytes + 8 * n * (int64_t)sizeof(T) + 4 * n + 4 * (n + 1);
 }
 
 __device__ __forceinline__ void lds3(const float* p, int j, float& a, float& b, float& c) {
@@ -737,11 +747,59 @@ __device__ __forceinline__ void lds3(const double* p, int j, double& a, double& 
   c = p[4 * j + 2];
 }
 
-__device__ __forceinline__ void cluster_arrive_release() {
-  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cluster_wait_acquire() {
-  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+// the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// waits for the completion of the mbarrier phase of parity `par`; false after
+// kMbarSpins polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par) {
+  for (unsigned spins = 0; spins < kMbarSpins; ++spins) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(par)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// a node's new value (x, y, z, 0) into the shared memory of a cluster CTA,
+// counted on that CTA's mbarrier
+__device__ __forceinline__ void st_async_node(uint32_t dst, uint32_t bar, float a, float b,
+                                              float c) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, "
+      "[%5];" ::"r"(dst),
+      "f"(a), "f"(b), "f"(c), "f"(0.f), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void st_async_node(uint32_t dst, uint32_t bar, double a, double b,
+                                              double c) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+          dst),
+      "d"(a), "d"(b), "r"(bar)
+      : "memory");
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+          dst + 16),
+      "d"(c), "d"(0.0), "r"(bar)
+      : "memory");
 }
 
 // blocks carried per lane (register budget of a 512-thread CTA: 128 a thread)
@@ -750,29 +808,34 @@ constexpr int gs_cl_unroll() {
   return (sizeof(T) == 8 || sizeof(V) == 2 || G >= 16) ? 2 : 3;
 }
 
-// ONE: a single CTA (no cluster): plain shared-memory stores and __syncthreads
-// between the colours, whose bar.sync orders shared memory without the
-// memory fence that a cluster-scope release takes
 template <typename T, int G, int U, typename V, bool ONE>
 __global__ void __launch_bounds__(kGsClThreads, 1)
     k_gs_cluster(int n, int ncolours, const GsColours cp, int post, int x_zero,
                  const int* __restrict__ rows, const int* __restrict__ rowptr,
                  const int* __restrict__ col, const V* __restrict__ val, int64_t nnzb, T* x,
                  const T* __restrict__ b, const T* __restrict__ dinv,
-                 const double* __restrict__ wt) {
+                 const double* __restrict__ wt, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char gs_smem[];
-  T* xs = reinterpret_cast<T*>(gs_smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gs_smem);
+  T* xs = reinterpret_cast<T*>(gs_smem + kGsClBarBytes);
   T* bs = xs + 4 * (int64_t)n;
   int* rows_s = reinterpret_cast<int*>(bs + 4 * (int64_t)n);
   int* rp_s = rows_s + n;
   const int cs = ONE ? 1 : (int)cg::this_cluster().num_blocks();
   const int rank = ONE ? 0 : (int)cg::this_cluster().block_rank();
   constexpr int RPW = 32 / G;
+  constexpr uint32_t kNodeBytes = 4 * sizeof(T);
   const int lane = threadIdx.x & 31, sub = lane / G, gl = lane & (G - 1);
   const int warp = (rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
   const int nwarps = (cs * (int)blockDim.x) >> 5;
   const int stride = nwarps * RPW;
   const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
+  auto colour_of = [&](int q) { return post ? ncolours - 1 - q : q; };
+  auto colour_bytes = [&](int q) {
+    const int c = colour_of(q);
+    return (uint32_t)(cp.ptr[c + 1] - cp.ptr[c]) * kNodeBytes;
+  };
+  const uint32_t bar0 = smem_addr(bars), xs0 = smem_addr(xs);
 
   for (int k = threadIdx.x; k < 4 * n; k += blockDim.x) {
     xs[k] = x_zero ? T(0) : x[k];
@@ -780,9 +843,19 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) rows_s[k] = __ldg(rows + k);
   for (int k = threadIdx.x; k <= n; k += blockDim.x) rp_s[k] = __ldg(rowptr + k);
-  // every copy is complete before any CTA stores into another's
-  if constexpr (ONE) __syncthreads();
-  else cg::this_cluster().sync();
+  if constexpr (ONE) {
+    __syncthreads();
+  } else {
+    // mbarrier q counts step q of the sweep: one arrival (its expect_tx) and the
+    // bytes of every row of the colour
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < ncolours; ++q) mbar_init(bar0 + 8 * q);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (int q = 0; q < ncolours; ++q) mbar_expect(bar0 + 8 * q, colour_bytes(q));
+    }
+    // every copy and mbarrier is ready before any CTA stores into another
+    cg::this_cluster().sync();
+  }
 
   // operands of this group's next row
   int pi = 0, pa = 0, pe = 0;
@@ -813,15 +886,16 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
       ld3(dp, 2, pd[6], pd[7], pd[8]);
     }
   };
-  auto colour_of = [&](int q) { return post ? ncolours - 1 - q : q; };
 
   {
     const int c = colour_of(0);
     load_row(cp.ptr[c] + warp * RPW + sub, cp.ptr[c + 1]);
   }
+  bool ok = true;
   for (int q = 0; q < ncolours; ++q) {
     const int c = colour_of(q);
     const int a = cp.ptr[c], e = cp.ptr[c + 1];
+    const uint32_t bar = bar0 + 8 * q;
     for (int base = a + warp * RPW; base < e; base += stride) {
       const bool active = base + sub < e;
       const int i = pi, ka = pa, ke = pe;
@@ -868,7 +942,7 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
         n2 = xi2 + om * (pd[6] * r0 + pd[7] * r1 + pd[8] * r2);
       }
       // the group's first lane holds the new value: every lane of the group
-      // takes it and stores it into the copies of ranks gl, gl + G, ...
+      // takes it (a cluster sends it to ranks gl, gl + G, ...)
       n0 = __shfl_sync(0xffffffffu, n0, sub * G);
       n1 = __shfl_sync(0xffffffffu, n1, sub * G);
       n2 = __shfl_sync(0xffffffffu, n2, sub * G);
@@ -882,35 +956,31 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
             xs[4 * (int64_t)i + 2] = n2;
           }
         } else {
-          for (int r = gl; r < cs; r += G) {
-            T* dst = cg::this_cluster().map_shared_rank(xs, (unsigned)r) + 4 * (int64_t)i;
-            dst[0] = n0;
-            dst[1] = n1;
-            dst[2] = n2;
-          }
+          for (int r = gl; r < cs; r += G)
+            st_async_node(cluster_addr(xs0 + 4 * (uint32_t)i * (uint32_t)sizeof(T), r),
+                          cluster_addr(bar, r), n0, n1, n2);
         }
       }
     }
+    // the next colour's first-row operands, before waiting for this colour
+    if (q + 1 < ncolours) {
+      const int cn = colour_of(q + 1);
+      load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
+    }
     if constexpr (ONE) {
-      if (q + 1 < ncolours) {
-        const int cn = colour_of(q + 1);
-        load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
-      }
       __syncthreads();
     } else {
-      // the barrier in two halves: the arrive releases this colour's stores; the
-      // next colour's first-row operands are loaded between the halves
-      cluster_arrive_release();
-      if (q + 1 < ncolours) {
-        const int cn = colour_of(q + 1);
-        load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
+      // all of colour q has arrived (the one phase of mbarrier q)
+      if (ok && !mbar_wait(bar, 0u)) {
+        atomicOr(err, 1);
+        ok = false;
       }
-      cluster_wait_acquire();
     }
   }
   // every copy now holds the swept iterate: each CTA writes its share
   for (int k = rank * (int)blockDim.x + (int)threadIdx.x; k < 4 * n; k += cs * (int)blockDim.x)
     x[k] = xs[k];
+  if constexpr (!ONE) cg::this_cluster().sync();   // no CTA leaves while others may store
 }
 
 // The largest cluster of `cs` CTAs with `smem` bytes each that can be resident
@@ -958,7 +1028,7 @@ int gs_cluster_fits(int cs, int smem) {
 
 template <typename T, int G, typename V>
 void launch_gs_cluster_g(const Level& lv, int cs, bool post, bool x_zero, const V* val, T* x,
-                         const T* b, const T* dinv, cudaStream_t s) {
+                         const T* b, const T* dinv, int* err, cudaStream_t s) {
   constexpr int U = gs_cl_unroll<T, G, V>();
   // the shared-memory and cluster-size attributes were set by gs_cluster_fits
   // when the level's cluster size was chosen
@@ -967,7 +1037,7 @@ void launch_gs_cluster_g(const Level& lv, int cs, bool post, bool x_zero, const 
   if (cs == 1) {
     k_gs_cluster<T, G, U, V, true><<<1, kGsClThreads, (size_t)gs_cl_smem<T>(lv.n), s>>>(
         lv.n, lv.ncolours, cp, (int)post, (int)x_zero, lv.k_rows(), lv.k_rowptr(), lv.k_col(),
-        val, lv.nnzb, x, b, dinv, (const double*)lv.wt);
+        val, lv.nnzb, x, b, dinv, (const double*)lv.wt, err);
     return;
   }
   auto kern = k_gs_cluster<T, G, U, V, false>;
@@ -985,17 +1055,17 @@ void launch_gs_cluster_g(const Level& lv, int cs, bool post, bool x_zero, const 
   cfg.numAttrs = 1;
   AMG_CUDA(cudaLaunchKernelEx(&cfg, kern, lv.n, lv.ncolours, cp, (int)post, (int)x_zero,
                               lv.k_rows(), lv.k_rowptr(), lv.k_col(), val, lv.nnzb, x, b, dinv,
-                              (const double*)lv.wt));
+                              (const double*)lv.wt, err));
 }
 
 template <typename T, typename V>
 void launch_gs_cluster_v(const Level& lv, int cs, int G, bool post, bool x_zero, const V* val,
-                         T* x, const T* b, const T* dinv, cudaStream_t s) {
+                         T* x, const T* b, const T* dinv, int* err, cudaStream_t s) {
   switch (G) {
-    case 4: launch_gs_cluster_g<T, 4, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
-    case 8: launch_gs_cluster_g<T, 8, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
-    case 16: launch_gs_cluster_g<T, 16, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
-    default: launch_gs_cluster_g<T, 32, V>(lv, cs, post, x_zero, val, x, b, dinv, s); break;
+    case 4: launch_gs_cluster_g<T, 4, V>(lv, cs, post, x_zero, val, x, b, dinv, err, s); break;
+    case 8: launch_gs_cluster_g<T, 8, V>(lv, cs, post, x_zero, val, x, b, dinv, err, s); break;
+    case 16: launch_gs_cluster_g<T, 16, V>(lv, cs, post, x_zero, val, x, b, dinv, err, s); break;
+    default: launch_gs_cluster_g<T, 32, V>(lv, cs, post, x_zero, val, x, b, dinv, err, s); break;
   }
 }
 
@@ -1425,13 +1495,14 @@ struct Emit {
       if (lv.val16.p) {
         launch_gs_cluster_v<float, __nv_bfloat16>(
             lv, lv.gs_cl, lv.gs_cl_g, post, x_zero,
-            reinterpret_cast<const __nv_bfloat16*>(lv.val16.p), x, b, dinv, h->stream);
+            reinterpret_cast<const __nv_bfloat16*>(lv.val16.p), x, b, dinv, h->flag.p,
+            h->stream);
         h->launches++;
         return;
       }
     }
     launch_gs_cluster_v<T, T>(lv, lv.gs_cl, lv.gs_cl_g, post, x_zero, LvVec<T>::val(lv), x, b,
-                              dinv, h->stream);
+                              dinv, h->flag.p, h->stream);
     h->launches++;
   }
   void zero(T* a, int64_t n) {
@@ -2059,6 +2130,11 @@ void autotune_levels(amg_handle* h) {
     }
     lv.gs_cl = cs_best;
     lv.gs_cl_g = g_best;
+  }
+  {
+    int ferr = 0;
+    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ferr) fail(AMG_ERR_TIMEOUT, "an mbarrier wait of the one-launch colour sweep timed out");
   }
   // cluster sub-cycle: the largest cluster that fits (16, else 8 CTAs), then the
   // fastest start level among 1..L (or none)

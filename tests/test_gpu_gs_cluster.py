@@ -1,5 +1,6 @@
-"""The multicolour Gauss-Seidel sweep of a small level as one thread-block-cluster
-launch (iterate in shared memory, one cluster barrier per colour), through the C ABI.
+"""The multicolour Gauss-Seidel sweep of a small level as one launch (a CTA, or a
+thread-block cluster whose CTAs exchange new values by st.async counted on an
+mbarrier a colour; x, b and the row offsets in shared memory), through the C ABI.
 
 The sweep computes what the one-launch-per-colour chain computes (Sec. 3.3, the
 block Gauss-Seidel smoother in colour order, colours descending after the coarse
