@@ -802,10 +802,11 @@ __device__ __forceinline__ void st_async_node(uint32_t dst, uint32_t bar, double
       : "memory");
 }
 
-// blocks carried per lane (register budget of a 512-thread CTA: 128 a thread)
+// blocks carried per lane in each of the two operand sets (register budget of
+// a 512-thread CTA: 128 a thread)
 template <typename T, int G, typename V>
 constexpr int gs_cl_unroll() {
-  return (sizeof(T) == 8 || sizeof(V) == 2 || G >= 16) ? 2 : 3;
+  return sizeof(T) == 8 ? 1 : 2;
 }
 
 template <typename T, int G, int U, typename V, bool ONE>
@@ -837,12 +838,23 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
   };
   const uint32_t bar0 = smem_addr(bars), xs0 = smem_addr(xs);
 
-  for (int k = threadIdx.x; k < 4 * n; k += blockDim.x) {
-    xs[k] = x_zero ? T(0) : x[k];
-    bs[k] = __ldg(b + k);
+  {
+    // x and b as 16-byte words (a node is one or two), several loads in flight
+    const int nw = n * 4 * (int)sizeof(T) / 16;
+    uint4* xw = reinterpret_cast<uint4*>(xs);
+    uint4* bw = reinterpret_cast<uint4*>(bs);
+    const uint4* xg = reinterpret_cast<const uint4*>(x);
+    const uint4* bg = reinterpret_cast<const uint4*>(b);
+#pragma unroll 4
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) {
+      xw[k] = x_zero ? make_uint4(0u, 0u, 0u, 0u) : xg[k];
+      bw[k] = __ldg(bg + k);
+    }
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n; k += blockDim.x) rows_s[k] = __ldg(rows + k);
+#pragma unroll 4
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) rp_s[k] = __ldg(rowptr + k);
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) rows_s[k] = __ldg(rows + k);
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) rp_s[k] = __ldg(rowptr + k);
   if constexpr (ONE) {
     __syncthreads();
   } else {
@@ -857,57 +869,64 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
     cg::this_cluster().sync();
   }
 
-  // operands of this group's next row
-  int pi = 0, pa = 0, pe = 0;
-  int pj[U];
-  T pv[U][9];
-  T pd[9];
-  auto load_row = [&](int g, int end) {
-    pa = pe = 0;
+  // operands of a row: node, block range, the first U blocks' columns and
+  // values, D_i^{-1}.  Two sets: the first rows of the next two colours are
+  // loaded while the current one runs.
+  struct RowOps {
+    int i, a, e;
+    int j[U];
+    T v[U][9];
+    T d[9];
+  };
+  auto load_row = [&](RowOps& o, int g, int end) {
+    o.a = o.e = 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) pj[u] = -1;
+    for (int u = 0; u < U; ++u) o.j[u] = -1;
     if (g >= end) return;
-    pi = rows_s[g];
-    pa = rp_s[g];
-    pe = rp_s[g + 1];
+    o.i = rows_s[g];
+    o.a = rp_s[g];
+    o.e = rp_s[g + 1];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int k = pa + gl + u * G;
-      if (k < pe) {
-        pj[u] = __ldg(col + k);
+      const int k = o.a + gl + u * G;
+      if (k < o.e) {
+        o.j[u] = __ldg(col + k);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) pv[u][q] = ldg_v<T>(val + q * nnzb + k);
+        for (int q = 0; q < 9; ++q) o.v[u][q] = ldg_v<T>(val + q * nnzb + k);
       }
     }
     if (gl == 0) {
-      const T* dp = dinv + 12 * (int64_t)pi;
-      ld3(dp, 0, pd[0], pd[1], pd[2]);
-      ld3(dp, 1, pd[3], pd[4], pd[5]);
-      ld3(dp, 2, pd[6], pd[7], pd[8]);
+      const T* dp = dinv + 12 * (int64_t)o.i;
+      ld3(dp, 0, o.d[0], o.d[1], o.d[2]);
+      ld3(dp, 1, o.d[3], o.d[4], o.d[5]);
+      ld3(dp, 2, o.d[6], o.d[7], o.d[8]);
     }
   };
+  auto first_row = [&](RowOps& o, int q) {
+    if (q >= ncolours) return;
+    const int c = colour_of(q);
+    load_row(o, cp.ptr[c] + warp * RPW + sub, cp.ptr[c + 1]);
+  };
 
-  {
-    const int c = colour_of(0);
-    load_row(cp.ptr[c] + warp * RPW + sub, cp.ptr[c + 1]);
-  }
   bool ok = true;
-  for (int q = 0; q < ncolours; ++q) {
+  // step q of the sweep from the operands in `o` (its first row); `o` then
+  // takes the first row of step q + 2
+  auto step = [&](int q, RowOps& o) {
     const int c = colour_of(q);
     const int a = cp.ptr[c], e = cp.ptr[c + 1];
     const uint32_t bar = bar0 + 8 * q;
     for (int base = a + warp * RPW; base < e; base += stride) {
       const bool active = base + sub < e;
-      const int i = pi, ka = pa, ke = pe;
+      const int i = o.i, ka = o.a, ke = o.e;
       T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (pj[u] < 0) continue;
+        if (o.j[u] < 0) continue;
         T x0, x1, x2;
-        lds3(xs, pj[u], x0, x1, x2);
-        s0 = fma(pv[u][0], x0, s0); s0 = fma(pv[u][1], x1, s0); s0 = fma(pv[u][2], x2, s0);
-        s1 = fma(pv[u][3], x0, s1); s1 = fma(pv[u][4], x1, s1); s1 = fma(pv[u][5], x2, s1);
-        s2 = fma(pv[u][6], x0, s2); s2 = fma(pv[u][7], x1, s2); s2 = fma(pv[u][8], x2, s2);
+        lds3(xs, o.j[u], x0, x1, x2);
+        s0 = fma(o.v[u][0], x0, s0); s0 = fma(o.v[u][1], x1, s0); s0 = fma(o.v[u][2], x2, s0);
+        s1 = fma(o.v[u][3], x0, s1); s1 = fma(o.v[u][4], x1, s1); s1 = fma(o.v[u][5], x2, s1);
+        s2 = fma(o.v[u][6], x0, s2); s2 = fma(o.v[u][7], x1, s2); s2 = fma(o.v[u][8], x2, s2);
       }
       // blocks beyond the U carried ones
       for (int k = ka + gl + U * G; k < ke; k += G) {
@@ -926,10 +945,10 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
         s2 = fma(ldg_v<T>(vv + 8 * nnzb), x2, s2);
       }
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      for (int off = G / 2; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
       T n0 = T(0), n1 = T(0), n2 = T(0);
       if (active && gl == 0) {
@@ -937,9 +956,9 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
         lds3(xs, i, xi0, xi1, xi2);
         lds3(bs, i, b0, b1, b2);
         const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
-        n0 = xi0 + om * (pd[0] * r0 + pd[1] * r1 + pd[2] * r2);
-        n1 = xi1 + om * (pd[3] * r0 + pd[4] * r1 + pd[5] * r2);
-        n2 = xi2 + om * (pd[6] * r0 + pd[7] * r1 + pd[8] * r2);
+        n0 = xi0 + om * (o.d[0] * r0 + o.d[1] * r1 + o.d[2] * r2);
+        n1 = xi1 + om * (o.d[3] * r0 + o.d[4] * r1 + o.d[5] * r2);
+        n2 = xi2 + om * (o.d[6] * r0 + o.d[7] * r1 + o.d[8] * r2);
       }
       // the group's first lane holds the new value: every lane of the group
       // takes it (a cluster sends it to ranks gl, gl + G, ...)
@@ -947,7 +966,7 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
       n1 = __shfl_sync(0xffffffffu, n1, sub * G);
       n2 = __shfl_sync(0xffffffffu, n2, sub * G);
       // the next row's operands in this colour
-      if (base + stride < e) load_row(base + stride + sub, e);
+      if (base + stride < e) load_row(o, base + stride + sub, e);
       if (active) {
         if constexpr (ONE) {
           if (gl == 0) {
@@ -962,11 +981,8 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
         }
       }
     }
-    // the next colour's first-row operands, before waiting for this colour
-    if (q + 1 < ncolours) {
-      const int cn = colour_of(q + 1);
-      load_row(cp.ptr[cn] + warp * RPW + sub, cp.ptr[cn + 1]);
-    }
+    // the first row of step q + 2, before waiting for this colour
+    first_row(o, q + 2);
     if constexpr (ONE) {
       __syncthreads();
     } else {
@@ -976,6 +992,13 @@ __global__ void __launch_bounds__(kGsClThreads, 1)
         ok = false;
       }
     }
+  };
+  RowOps A, B;
+  first_row(A, 0);
+  first_row(B, 1);
+  for (int q = 0; q < ncolours; q += 2) {
+    step(q, A);
+    if (q + 1 < ncolours) step(q + 1, B);
   }
   // every copy now holds the swept iterate: each CTA writes its share
   for (int k = rank * (int)blockDim.x + (int)threadIdx.x; k < 4 * n; k += cs * (int)blockDim.x)
