@@ -401,7 +401,8 @@ def run_profile(args):
         # under a profiler would choose differently), without graph replay so that a
         # profiler sees every kernel
         opts = B.default_options(precision=prec, cycle_kernel=args.cycle_kernel,
-                                 cluster_from=args.cluster_from, use_graphs=0)
+                                 cluster_from=args.cluster_from, use_graphs=0,
+                                 gs_cluster=args.gs_cluster, outer_pair=args.outer_pair)
         h = B.setup_problem(prob, opts, stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)

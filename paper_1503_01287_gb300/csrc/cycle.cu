@@ -2154,6 +2154,33 @@ void autotune_levels(amg_handle* h) {
     lv.gs_cl = cs_best;
     lv.gs_cl_g = g_best;
   }
+  // A one-launch sweep chosen above by timing the sweep alone is kept only if
+  // the whole preconditioner application is faster with it: between the
+  // per-colour and row kernels of the cycle it can cost more than alone.
+  if (h->opt.gs_cluster < 0) {
+    DBuf<double> r, z;
+    const int64_t n4 = h->L[0]->dofs4();
+    r.alloc(n4);
+    z.alloc(n4);
+    AMG_CUDA(cudaMemsetAsync(r.p, 0, r.bytes(), s));
+    auto precond_ms = [&]() {
+      for (int rep = 0; rep < 6; ++rep) {
+        if (rep == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) precondition_device<float>(h, r, z);
+        else precondition_device<double>(h, r, z);
+      }
+      return elapsed();
+    };
+    for (size_t l = 0; l < h->L.size(); ++l) {
+      Level& lv = *h->L[l];
+      if (lv.gs_cl <= 0) continue;
+      const float t_on = precond_ms();
+      const int keep = lv.gs_cl;
+      lv.gs_cl = 0;
+      const float t_off = precond_ms();
+      if (t_on < 0.99f * t_off) lv.gs_cl = keep;
+    }
+  }
   {
     int ferr = 0;
     AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
