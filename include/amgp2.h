@@ -177,7 +177,9 @@ typedef struct amg_options {
                                arithmetic -- every FP64 value and direction entry
                                held as two floats hi + lo, each product formed
                                exactly with an FMA, sums compensated (TwoSum),
-                               about 2^-48 relative; 0 in FP64.  The residual
+                               about 2^-48 relative while the values and the
+                               direction's entries lie between about 1e-30 and
+                               1e38 in magnitude; 0 in FP64.  The residual
                                reported at exit is always recomputed in FP64     */
   int32_t pad2;
 } amg_options;
