@@ -174,8 +174,8 @@ __global__ void k_axpy(int64_t n, double alpha, const double* __restrict__ a, do
     b[k] = fma(alpha, a[k], b[k]);
 }
 
-__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                      double* __restrict__ c) {
+// c = a - b; c may be b (element-wise, in place)
+__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* b, double* c) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     c[k] = a[k] - b[k];

@@ -1660,12 +1660,6 @@ __global__ void k_vk_ws(int np, const int* __restrict__ brow, const double* __re
   }
 }
 
-__global__ void k_fill_int(int* a, int v, int64_t n) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    a[k] = v;
-}
-
 __global__ void k_iota(int* a, int n) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
     a[k] = k;
