@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -131,6 +132,27 @@ def cpu_threads():
         return 1
 
 
+def host_cpu():
+    """The host's CPU model (lscpu, else /proc/cpuinfo, else the architecture) and core
+    count, recorded beside the oracle timings."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                model = line.split(":", 1)[1].strip()
+                break
+        else:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.split(":")[0].strip().lower() in ("model name", "cpu model"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -146,7 +168,7 @@ def run_reference(args, rank, world):
         "config": {"workload": f"elasticity {args.n}^3 P2 (oracle sample {n_sample}^3)",
                    "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cpu_threads(),
-                         "kind": "oracle",
+                         "kind": "oracle", "host": host_cpu(),
                          "sample": f"FP64 AMG-PCG solve phase of elasticity {n_sample}^3 "
                                    f"({ndof} DOF, {its} iterations), setup excluded"},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
@@ -327,7 +349,7 @@ def run_gpu(args, rank, world):
                 k: float(np.linalg.norm(v - xo) / np.linalg.norm(xo))
                 for k, v in gpu_x_ref.items()}}
         cpu = {"value": ndof_s / times[0], "unit": "DOF/s", "cores": cpu_threads(),
-               "kind": "oracle",
+               "kind": "oracle", "host": host_cpu(),
                "sample": f"FP64 AMG-PCG solve phase of elasticity {args.ref_n}^3 "
                          f"({ndof_s} DOF, {its} iterations), setup excluded"}
 
