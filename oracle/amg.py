@@ -15,8 +15,12 @@ against the paper, not to be fast:
                       weight on all 3 components; R = P^T.
   Galerkin            A_{l+1} = P^T A_l P (Sec. 3.2.1/3.2.2), pattern kept
                       structurally (entries that cancel numerically stay).
-  smoothers           Sec. 3.3: damped 3x3-block Jacobi, multicolour symmetric
-                      3x3-block Gauss-Seidel (first-fit colouring in index order).
+  smoothers           Sec. 3.3: damped 3x3-block Jacobi, multicolour 3x3-block
+                      Gauss-Seidel (first-fit colouring in index order).  The
+                      post-smoothing sweeps run the colours in reverse order
+                      inside a Krylov method (a symmetric preconditioner for CG)
+                      and in the pre-smoothing order for the stand-alone AMG
+                      iteration (Options.post_order).
   cycle               Algorithm 1 (nu = 1: V-cycle, nu = 2: W-cycle).
   Krylov              PCG, flexible CG, right-preconditioned FGMRES(m).
 
@@ -222,6 +226,11 @@ class Options:
     ws: float = 1.0
     wc: float = 1.0
     wp: float = 1.0
+    # colour order of the post-smoothing sweeps (Gauss-Seidel, Vanka): "reverse"
+    # (descending: with the ascending pre-smoothing the cycle is a symmetric
+    # preconditioner, as CG needs) or "same" (ascending, as pre-smoothing: the
+    # stand-alone AMG iteration of Sec. 4.2, Tables 4 and 8)
+    post_order: str = "reverse"
 
 
 @dataclass
@@ -402,7 +411,7 @@ def smooth(h: Hierarchy, l: int, x, b, post: bool):
         return sd.smooth(h, l, x, b, post)
     if o.smoother == "jacobi":
         return jacobi_sweep(lv, x, b, o.omega * o.ws)
-    return gs_sweep(lv, x, b, reverse=post, ws=o.ws)
+    return gs_sweep(lv, x, b, reverse=post and o.post_order == "reverse", ws=o.ws)
 
 
 def operator(h: Hierarchy, l: int):
@@ -580,8 +589,31 @@ def solve(prob, opts: Options | None = None, tol: float = 1e-8, h: Hierarchy | N
     b = prob.rhs()
     if h.saddle:
         from . import saddle as sd
-        return sd.solve(h, prob, b, tol, maxit), h
+        return sd.solve(h, prob, b, tol, maxit, method), h
     K = operator(h, 0)
     M = lambda r: precondition(h, r)   # noqa: E731
+    if method == "amg":
+        return amg_iteration(K, M, b, tol, maxit=maxit), h
     flexible = method == "fcg"
     return pcg(K, M, b, tol, maxit=maxit, flexible=flexible), h
+
+
+def amg_iteration(apply_A, apply_M, b, tol, maxit=1000):
+    """The stand-alone AMG solver (Sec. 4.2): x_{k+1} = x_k + M^{-1}(b - A x_k) from
+    x_0 = 0, one preconditioner application (`cycles` cycles of Algorithm 1) per
+    iteration, stopping when ||b - A x_k|| / ||b|| <= tol."""
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    hist = [1.0]
+    if nb == 0.0:
+        return SolveResult(x, 0, True, hist, 0.0)
+    r = b.copy()
+    it = 0
+    while it < maxit:
+        x = x + apply_M(r)
+        r = b - apply_A(x)
+        it += 1
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            return SolveResult(x, it, True, hist, hist[-1])
+    return SolveResult(x, it, False, hist, hist[-1])

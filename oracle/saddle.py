@@ -201,7 +201,7 @@ def smooth_vanka(h, l, x, b, post):
     nu = 3 * lv.n
     x = x.copy()
     order = range(vk["ncolours"])
-    if post:
+    if post and h.opts.post_order == "reverse":
         order = reversed(list(order))
     for c in order:
         r = b - apply_K(lv, x)
@@ -284,11 +284,17 @@ def pressure_projector(h):
     return project
 
 
-def solve(h, prob, b, tol, maxit):
+def solve(h, prob, b, tol, maxit, method=None):
+    """FGMRES(50) (Sec. 4.4), or with method = "amg" the stand-alone AMG iteration."""
     lv0 = h.levels[0]
     project = pressure_projector(h)
-    res = amg.fgmres(lambda v: apply_K(lv0, v), lambda r: amg.precondition(h, r), b, tol,
-                     restart=50, maxit=maxit, project=project)
+    K = lambda v: apply_K(lv0, v)                            # noqa: E731
+    if method == "amg":
+        M = lambda r: (project or (lambda v: v))(amg.precondition(h, r))   # noqa: E731
+        res = amg.amg_iteration(K, M, b, tol, maxit=maxit)
+    else:
+        res = amg.fgmres(K, lambda r: amg.precondition(h, r), b, tol,
+                         restart=50, maxit=maxit, project=project)
     if project is not None:
         res.x = project(res.x)
     return res
