@@ -181,7 +181,14 @@ typedef struct amg_options {
                                direction's entries lie between about 1e-30 and
                                1e38 in magnitude; 0 in FP64.  The residual
                                reported at exit is always recomputed in FP64     */
-  int32_t pad2;
+  int32_t post_order;       /* colour order of the post-smoothing sweeps of the
+                               Gauss-Seidel and Vanka smoothers: -1 (default)
+                               the pre-smoothing (ascending) order for the
+                               stand-alone AMG iteration (krylov =
+                               AMG_KRYLOV_NONE; Sec. 4.2, Tables 4 and 8) and
+                               the reverse (descending) order for the Krylov
+                               methods, which keeps the preconditioner
+                               symmetric for CG; 0 reverse; 1 same           */
 } amg_options;
 
 #define AMG_MAX_LEVELS 8
@@ -352,16 +359,19 @@ int amg_level_copy(const amg_handle* h, int32_t level, int32_t item, void* host_
 
 /* One application of the preconditioner, z = M^{-1} r (opt->cycles cycles of
  * Algorithm 1 from zero), in the precision chosen at setup.  r and z are device
- * pointers of 3*n_nodes + n_pres doubles.  Synchronises the stream. */
+ * pointers of 3*n_nodes + n_pres doubles.  Synchronises the stream; returns
+ * AMG_ERR_TIMEOUT if a bounded device wait of the cycle gave up. */
 int amg_apply_preconditioner(amg_handle* h, const double* r, double* z);
 
 /*
  * amg_apply_preconditioner_noalloc -- the same z = M^{-1} r as
- * amg_apply_preconditioner, for callers that must not allocate device memory
- * during the call: work issued while a stream is captured into a CUDA graph in
- * global mode (cudaMalloc is refused there), code whose framework allocator has
- * already reserved the device memory, and latency-bound loops that cannot take
- * the device-wide synchronisation an allocation may bring.  The paper has no
+ * amg_apply_preconditioner, for callers that cannot let a library call allocate
+ * device memory: applications whose framework allocator (a caching allocator, a
+ * memory pool sized at start-up) already holds nearly all of the device memory,
+ * so that a cudaMalloc inside the call fails or forces the framework to give
+ * memory back; and loops with a latency budget, where cudaMalloc and cudaFree may
+ * synchronise the whole device.  amg_apply_preconditioner allocates its two
+ * staging vectors on its first call; this variant never does.  The paper has no
  * counterpart; this is a property of the library interface.
  *   r, z   device pointers of 3*n_nodes + n_pres doubles (the caller owns them).
  * The input and output are staged in one static device array of the library
@@ -374,7 +384,8 @@ int amg_apply_preconditioner(amg_handle* h, const double* r, double* z);
  * capture.  All calls share the array: calls whose GPU work overlaps (several
  * handles, streams or threads at once) race on it and must be serialised by the
  * caller.  The array keeps the last call's contents; both staged vectors are
- * rewritten completely by every call.  Synchronises the handle's stream.
+ * rewritten completely by every call.  Synchronises the handle's stream and
+ * returns AMG_ERR_TIMEOUT if a bounded device wait of the cycle gave up.
  */
 int amg_apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
 

@@ -72,7 +72,7 @@ class AmgOptions(C.Structure):
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
                 ("omega", C.c_double), ("omega_p", C.c_double),
                 ("batch_tile", C.c_int32), ("gs_cluster", C.c_int32),
-                ("outer_pair", C.c_int32), ("pad2", C.c_int32)]
+                ("outer_pair", C.c_int32), ("post_order", C.c_int32)]
 
 
 class AmgStats(C.Structure):

@@ -287,6 +287,10 @@ int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stat
 
 // noalloc.cu: the preconditioner application with static staging vectors
 void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
+// After the handle's stream has been synchronised: reads the device error word
+// that bounded waits (grid barrier, mbarrier) set when they give up, clears it
+// and fails with AMG_ERR_TIMEOUT naming `what` if it was set.
+void check_wait_flag(amg_handle* h, const char* what);
 
 // learned.cu: statistics of the hierarchy, weights, selection with fallback
 constexpr double kProbeTol = 1e-8;   // the probe solves run to the stopping tolerance of the workloads

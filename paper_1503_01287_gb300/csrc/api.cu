@@ -96,7 +96,7 @@ void amg_default_options(amg_options* o) {
   o->batch_tile = -1;
   o->gs_cluster = -1;
   o->outer_pair = 1;
-  o->pad2 = 0;
+  o->post_order = -1;     // resolved from the Krylov method in amg_setup
 }
 
 int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,
@@ -143,8 +143,12 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
         (h->opt.gs_cluster > 0 && (h->opt.gs_cluster & (h->opt.gs_cluster - 1))))
       fail(AMG_ERR_INVALID, "gs_cluster must be -1, 0, 1, 2, 4, 8 or 16");
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
-        h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1)
+        h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1 ||
+        h->opt.post_order < -1 || h->opt.post_order > 1)
       fail(AMG_ERR_INVALID, "option out of range");
+    // post-smoothing colour order: the stand-alone iteration sweeps the colours in the
+    // pre-smoothing order, a Krylov method gets the symmetric (reversed) order
+    if (h->opt.post_order < 0) h->opt.post_order = h->opt.krylov == AMG_KRYLOV_NONE ? 1 : 0;
     h->kind = kind;
     h->saddle = saddle;
     if (stream) {
@@ -261,13 +265,7 @@ int amg_solve(amg_handle* h, const double* b, double* x, double rel_tol, int32_t
     }
     AMG_CUDA(cudaEventRecord(e1, h->stream));
     AMG_CUDA(cudaEventSynchronize(e1));
-    int ferr = 0;
-    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (ferr) {
-      AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
-      fail(AMG_ERR_TIMEOUT, "a bounded device wait (grid barrier or mbarrier) timed out during "
-                            "the solve");
-    }
+    check_wait_flag(h, "the solve");
     float ms = 0.f;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
@@ -319,6 +317,19 @@ __global__ void k_planes_to_aos(const double* __restrict__ planes, int nv, int64
        k += (int64_t)gridDim.x * blockDim.x)
     for (int e = 0; e < nv; ++e) aos[nv * k + e] = planes[e * nnz + k];
 }
+
+}  // namespace
+
+void check_wait_flag(amg_handle* h, const char* what) {
+  int ferr = 0;
+  AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!ferr) return;
+  AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
+  fail(AMG_ERR_TIMEOUT, std::string("a bounded device wait (grid barrier or mbarrier) gave up "
+                                    "during ") + what + "; the result is not valid");
+}
+
+namespace {
 
 void copy_out(amg_handle* h, const void* src, size_t bytes, void* dst, int64_t cap) {
   if ((int64_t)bytes > cap) fail(AMG_ERR_INVALID, "destination too small");
@@ -444,6 +455,7 @@ int amg_apply_preconditioner(amg_handle* h, const double* r, double* z) {
     launch_from_padded(h->kz, z, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
+    check_wait_flag(h, "the preconditioner application");
     return AMG_OK;
   });
 }
@@ -501,12 +513,7 @@ int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
     launch_from_padded(lv.x64, x, lv.n, lv.np, h->stream, h);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(h->stream));
-    int ferr = 0;
-    AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (ferr) {
-      AMG_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
-      fail(AMG_ERR_TIMEOUT, "an mbarrier wait of the one-launch colour sweep timed out");
-    }
+    check_wait_flag(h, "the smoothing sweep");
     return AMG_OK;
   });
 }

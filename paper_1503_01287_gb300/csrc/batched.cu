@@ -429,12 +429,11 @@ constexpr int kTiles = 4;   // tile t: S = 1 + (t & 1), U = (t & 2) ? 4 : 2
 
 // One colour of the multicolour Gauss-Seidel sweep for all right-hand sides,
 // launched with programmatic dependent launch: the row's ids, the column indices
-// and values of its first U blocks of this lane group, b and D^{-1} are loaded
-// before griddepcontrol.wait (none of them is written by the previous colour's
-// kernel or by anything it overlaps: they are setup data, or b, written before the
-// sweep's first colour by a kernel that does not overlap), so this prologue runs
-// under the previous colour; after the wait only the x gathers and the update
-// remain.  Tile as in k_rows_m.
+// and values of its first U blocks of this lane group and D^{-1} (setup data that
+// no cycle kernel writes) are loaded before griddepcontrol.wait, so this prologue
+// runs under the previous kernel; b, the relaxation multiplier and the x gathers
+// come after the wait, which is where the previous kernel's writes become
+// visible.  Tile as in k_rows_m.
 template <typename T, int S, int U>
 __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restrict__ rows,
                                                   const int* __restrict__ rowptr,
@@ -444,7 +443,6 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
                                                   const T* __restrict__ dinv,
                                                   const double* __restrict__ wt) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / (K * S);
   const int q = (threadIdx.x / K) % S;
   const int r = threadIdx.x % K;
@@ -470,15 +468,18 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
       }
     }
     if (q == 0) {
-      ld3(b, i * K + r, b0, b1, b2);
       const T* dp = dinv + 12 * (int64_t)i;
       ld3(dp, 0, d[0], d[1], d[2]);
       ld3(dp, 1, d[3], d[4], d[5]);
       ld3(dp, 2, d[6], d[7], d[8]);
     }
   }
+  // the right-hand side and the multiplier may be written by the previous kernel
+  // (the restriction before a sweep's first colour): read only after the wait
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (!active) return;
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
+  if (q == 0) ld3(b, i * K + r, b0, b1, b2);
   T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -680,7 +681,7 @@ void cycle_m(amg_handle* h, int l, T* x, const T* b, bool x_is_zero) {
                                                           MV<T>::pval(lv), MV<T>::x(bn), x,
                                                           lv.wt);
   h->launches++;
-  for (int k = 0; k < h->opt.m_post; ++k) smooth_m<T>(h, l, x, b, true);
+  for (int k = 0; k < h->opt.m_post; ++k) smooth_m<T>(h, l, x, b, h->opt.post_order != 1);
 }
 
 // z = M^{-1} r for all right-hand sides (FP64 [node][K][4] in and out)

@@ -592,11 +592,12 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
 }
 
 // Multicolour Gauss-Seidel for one colour, launched with programmatic dependent
-// launch: everything the row update reads except x (row ids, block columns and
-// values, b_i, D_i^{-1}) is loaded before griddepcontrol.wait, so this prologue
-// overlaps the previous colour's kernel; after the wait only the x gathers and
-// the update remain.  Neither the previous colour's kernel nor any operation
-// it overlaps writes those operands (it writes x of its own rows only).
+// launch: the operands that setup wrote and no cycle kernel writes (row ids,
+// block columns and values, D_i^{-1}) are loaded before griddepcontrol.wait, so
+// this prologue overlaps the previous kernel; b_i, the relaxation multiplier and
+// the x gathers come after the wait, since only then are the previous kernel's
+// writes guaranteed visible (the first colour of a sweep follows the
+// restriction that writes b).
 // One group of G lanes per stored row; each lane prefetches up to U blocks.
 template <typename T, int G, int U, typename V = T>
 __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict__ rows,
@@ -607,7 +608,6 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
                                                 const T* __restrict__ dinv,
                                                 const double* __restrict__ wt) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int gl = threadIdx.x & (G - 1);
   const bool active = g < nrows;
@@ -632,7 +632,6 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
       }
     }
     if (gl == 0) {
-      ld3(b, i, b0, b1, b2);
       const T* dp = dinv + 12 * (int64_t)i;
       ld3(dp, 0, d[0], d[1], d[2]);
       ld3(dp, 1, d[3], d[4], d[5]);
@@ -640,10 +639,14 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
     }
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
   T s0 = T(0), s1 = T(0), s2 = T(0);
   T xi0 = T(0), xi1 = T(0), xi2 = T(0);
   if (active) {
-    if (gl == 0) VL<true>::node(x, i, xi0, xi1, xi2);
+    if (gl == 0) {
+      ld3(b, i, b0, b1, b2);
+      VL<true>::node(x, i, xi0, xi1, xi2);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (j[u] < 0) continue;
@@ -1670,9 +1673,10 @@ void e_smooth_bs(Emit<T>& e, amg_handle* h, int l, T* x, const T* b) {
   e.vec(1, lv.np, nullptr, dp, nullptr, T(1), x + n4);      // p += dp
 }
 
-// One smoothing sweep (Sec. 3.3).  SPD: symmetric multicolour block GS (colours
-// ascending before the coarse correction, descending after it) or damped block
-// Jacobi.  Saddle: segregated Gauss-Seidel, Eq. (uzsm).
+// One smoothing sweep (Sec. 3.3).  SPD: multicolour block GS (colours ascending,
+// or descending when `post` is set: the post-smoothing order of the symmetric
+// cycle) or damped block Jacobi.  Saddle: segregated Gauss-Seidel, Eq. (uzsm),
+// Braess-Sarazin or Vanka (patch colours in the same order as GS).
 template <typename T>
 void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
               bool x_is_zero) {
@@ -1797,7 +1801,10 @@ void cycle_rec(Emit<T>& e, amg_handle* h, int l, T* x, const T* b, bool x_is_zer
   e_restrict<T>(e, h, l, r, bc);
   coarse_calls<T>(e, h, l + 1, xc, bc);
   e_prolong<T>(e, h, l, xc, x);
-  for (int k = 0; k < o.m_post; ++k) e_smooth<T>(e, h, lv, x, b, true, false);
+  // post-smoothing: colours descending (symmetric cycle) or, with post_order = 1,
+  // ascending as in pre-smoothing
+  const bool reverse = o.post_order != 1;
+  for (int k = 0; k < o.m_post; ++k) e_smooth<T>(e, h, lv, x, b, reverse, false);
 }
 
 template <typename T>

@@ -2,13 +2,13 @@
 // amg_apply_preconditioner without any device allocation inside the call.
 //
 // amg_apply_preconditioner stages its input and output vectors in buffers the
-// handle allocates on first use.  Some callers cannot let a call allocate:
-// code that issues work while a CUDA stream is being captured into a graph in
-// global capture mode (cudaMalloc is refused there), applications whose
-// framework allocator has already reserved the device memory, and latency-
-// bound loops that cannot afford the device-wide synchronisation an allocation
-// may cause.  This variant stages the two vectors in one file-scope static
-// device array instead, so after amg_setup no call allocates anything.
+// handle allocates on its first call.  Some callers cannot let a library call
+// allocate: applications whose framework allocator (a caching allocator, or a
+// pool sized at start-up) already holds nearly all of the device memory, where
+// a cudaMalloc inside the call fails or forces the framework to release memory,
+// and loops with a latency budget, where cudaMalloc and cudaFree may
+// synchronise the whole device.  This variant stages the two vectors in one
+// file-scope static device array instead, so after amg_setup no call allocates.
 #include <cstdio>
 #include <mutex>
 
@@ -70,6 +70,7 @@ void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z) {
   launch_from_padded(sz, z, lv.n, lv.np, h->stream, h);
   AMG_LAUNCH_CHECK();
   AMG_CUDA(cudaStreamSynchronize(h->stream));
+  check_wait_flag(h, "the preconditioner application");
 }
 
 }  // namespace amgp2

@@ -286,19 +286,43 @@ def test_pcg_fp64_matches_oracle(opts, okw):
     assert np.all(x.reshape(-1, 3)[d] == 0.0)
 
 
-def test_standalone_amg_matches_oracle():
-    prob = fp.vector_laplace_problem(6, seed=2)
-    h = gpu(prob, krylov=B().AMG_KRYLOV_NONE)
+@pytest.mark.parametrize("kind,opts", [
+    ("laplace", {}), ("elasticity", {}), ("elasticity", {"cycle_kernel": 2}),
+    ("elasticity", {"cluster_from": 1}), ("elasticity", {"m_pre": 2, "m_post": 2}),
+    ("laplace", {"post_order": 0}), ("mixed", {}),
+])
+def test_standalone_amg_matches_oracle(kind, opts):
+    """The stand-alone AMG iteration (Sec. 4.2): by default its post-smoothing sweeps
+    the colours in the pre-smoothing order (post_order 0 forces the reversed order)."""
+    prob = {"laplace": lambda: fp.vector_laplace_problem(6, seed=2),
+            "elasticity": lambda: fp.elasticity_problem(6, seed=4),
+            "mixed": lambda: fp.mixed_elasticity_problem(4, nu=0.45, seed=5)}[kind]()
+    h = gpu(prob, krylov=B().AMG_KRYLOV_NONE, max_iterations=400, **opts)
     st, x = _solve(h, prob, 1e-8)
-    oh = amg.build_hierarchy(prob, oracle_opts(prob))
-    b = prob.rhs()
-    xo = np.zeros_like(b)
-    its = 0
-    while np.linalg.norm(b - oh.levels[0].A @ xo) > 1e-8 * np.linalg.norm(b) and its < 500:
-        xo = xo + amg.precondition(oh, b - oh.levels[0].A @ xo)
-        its += 1
-    assert st.converged and abs(st.iterations - its) <= 1, (st.iterations, its)
-    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+    okw = {k: v for k, v in opts.items() if k in ("m_pre", "m_post")}
+    order = "reverse" if opts.get("post_order") == 0 else "same"
+    ref, _ = amg.solve(prob, oracle_opts(prob, post_order=order, **okw), tol=1e-8,
+                       method="amg", maxit=400)
+    assert st.converged and ref.converged
+    assert abs(st.iterations - ref.iterations) <= 1, (st.iterations, ref.iterations)
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("opts", [{}, {"cycle_kernel": 2}, {"cluster_from": 1},
+                                  {"gs_cluster": 1}, {"nu": 2, "m_pre": 2, "m_post": 2}])
+def test_preconditioner_same_post_order_matches_oracle(opts):
+    """One cycle with post_order = 1 (post-smoothing colours ascending) in every cycle
+    variant, entry by entry against the oracle."""
+    prob = fp.elasticity_problem(7, seed=9)
+    h = gpu(prob, post_order=1, **opts)
+    okw = {k: v for k, v in opts.items() if k in ("nu", "m_pre", "m_post")}
+    oh = amg.build_hierarchy(prob, oracle_opts(prob, post_order="same", **okw))
+    r = np.random.default_rng(8).standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(cuda(r), z)
+    want = amg.precondition(oh, r)
+    got = z.cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-10 * np.abs(want).max())
 
 
 @pytest.mark.parametrize("cluster_from,cycle_kernel", [(0, 1), (1, 1), (2, 1), (0, 2)])

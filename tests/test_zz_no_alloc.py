@@ -1,13 +1,20 @@
-"""The allocation-free preconditioner entry point, for callers that cannot allocate
-device memory during a call (stream capture in global mode, frameworks whose
-allocator already owns the device memory, latency-bound loops).
+"""The allocation-free preconditioner entry point.
 
-amg_apply_preconditioner_noalloc must give the result of amg_apply_preconditioner
-on two consecutive calls (its static staging array keeps the previous call's
-contents, which must not leak into the next result), and must refuse problems
-larger than its staging array.  This file is collected last so that a run that
-stops at the first failure has already run every other test; it also passes on
-its own in a fresh process.
+amg_apply_preconditioner_noalloc serves callers that cannot let a library call
+allocate device memory: applications whose framework allocator already holds
+nearly all of the device memory, and loops with a latency budget in which
+cudaMalloc / cudaFree may synchronise the whole device.  It stages its vectors
+in a static device array of the library instead of buffers of the handle.
+
+It must give the result of amg_apply_preconditioner on two consecutive calls
+(the static array keeps the previous call's contents, which must not leak into
+the next result), in both FP64 cycle variants (per-operation launches and the
+persistent cycle kernel, which copies through the level's own vectors) and for
+the saddle layout with its pressure block; its repeated calls must leave the
+device's free memory unchanged; and it must refuse problems larger than its
+array.  This file is collected last so that a run that stops at the first
+failure has already run every other test; it also passes on its own in a fresh
+process.
 """
 import numpy as np
 import pytest
@@ -31,11 +38,21 @@ def _binding():
     return binding
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_noalloc_matches_allocating_entry_point(precision):
+PROBLEMS = {
+    "elasticity": lambda: fp.elasticity_problem(8, seed=2),
+    "mixed": lambda: fp.mixed_elasticity_problem(4, nu=0.49, seed=5),
+    "stokes": lambda: fp.stokes_lid_problem(4),
+}
+
+
+@pytest.mark.parametrize("kind,precision,cycle_kernel", [
+    ("elasticity", 0, 1), ("elasticity", 0, 2), ("elasticity", 1, 1), ("elasticity", 1, 2),
+    ("mixed", 0, 1), ("mixed", 1, 2), ("stokes", 0, 2),
+])
+def test_noalloc_matches_allocating_entry_point(kind, precision, cycle_kernel):
     B = _binding()
-    prob = fp.elasticity_problem(8, seed=2)
-    h = B.setup_problem(prob, B.default_options(precision=precision))
+    prob = PROBLEMS[kind]()
+    h = B.setup_problem(prob, B.default_options(precision=precision, cycle_kernel=cycle_kernel))
     rng = np.random.default_rng(11)
     for call in range(2):            # two calls in a row share the static array
         r = torch.from_numpy(rng.standard_normal(prob.n_dof)).cuda()
@@ -46,6 +63,36 @@ def test_noalloc_matches_allocating_entry_point(precision):
         zr, zn = z_ref.cpu().numpy(), z.cpu().numpy()
         assert np.all(np.isfinite(zn)), call
         assert np.linalg.norm(zn - zr) <= 1e-12 * np.linalg.norm(zr), call
+    h.free()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    """20^3 elasticity: each staged vector holds 4 * 68,921 doubles (2.2 MB), more
+    than the granularity at which cudaMemGetInfo reports free memory.  Repeated
+    calls must not change it; the allocating entry point's first call, which
+    allocates its two staging vectors, must (a check that the measurement sees
+    allocations of this size)."""
+    B = _binding()
+    prob = fp.elasticity_problem(20, seed=3)
+    h = B.setup_problem(prob, B.default_options(precision=1))
+    rng = np.random.default_rng(12)
+    rs = [torch.from_numpy(rng.standard_normal(prob.n_dof)).cuda() for _ in range(3)]
+    zs = [torch.zeros_like(rs[0]) for _ in range(3)]
+    z_ref = torch.zeros_like(rs[0])
+    h.apply_preconditioner_noalloc(rs[0], zs[0])   # first call: looks up the array's address
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for r, z in zip(rs, zs):
+        h.apply_preconditioner_noalloc(r, z)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    h.apply_preconditioner(rs[2], z_ref)           # allocates 2 x (4 n_nodes) doubles
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free0 - free2 >= 2 * 4 * prob.n_nodes * 8 * 0.9, (free0, free2)
+    zr, zn = z_ref.cpu().numpy(), zs[2].cpu().numpy()
+    assert np.linalg.norm(zn - zr) <= 1e-12 * np.linalg.norm(zr)
     h.free()
 
 
