@@ -323,17 +323,22 @@ def build_hierarchy(prob, opts: Options | None = None) -> Hierarchy:
 # ----------------------------------------------------------------------------------------
 
 PIVOT_RTOL = 1e-13
+PIVOT_TIE = 1e-9
 
 
-def complete_pivot_lu(K: np.ndarray, rtol: float = PIVOT_RTOL):
+def complete_pivot_lu(K: np.ndarray, rtol: float = PIVOT_RTOL, tie: float = PIVOT_TIE):
     """Gaussian elimination with complete pivoting, stopped at the numerical rank.
 
-    Step k picks the entry of largest magnitude in the remaining block (first in
-    row-major order among equals), swaps it to (k, k) and eliminates below it.
-    Elimination stops when that magnitude is <= rtol * max|K|; the unknowns of
-    the remaining columns are then set to zero, which gives one solution of a
-    consistent singular system (e.g. a Stokes matrix with its constant-pressure
-    mode) and the exact solution of a nonsingular one.
+    Step k takes the largest magnitude M of the remaining block; the pivot is the
+    first entry in row-major order of that block whose magnitude is >= (1 - tie) M
+    (entries within a relative `tie` of the largest count as equal, so that
+    rounding differences in the matrix do not change the pivot sequence of
+    matrices with exactly tied entries, such as the Galerkin coarse matrices of a
+    structured mesh); it is swapped to (k, k) and eliminated below.  Elimination
+    stops when M <= rtol * max|K|; the unknowns of the remaining columns are then
+    set to zero, which gives one solution of a consistent singular system (e.g. a
+    Stokes matrix with its constant-pressure mode) and the exact solution of a
+    nonsingular one.
     Returns (LU, row_perm, col_perm, rank).
     """
     A = np.array(K, dtype=np.float64)
@@ -344,10 +349,11 @@ def complete_pivot_lu(K: np.ndarray, rtol: float = PIVOT_RTOL):
     rank = 0
     for k in range(n):
         sub = np.abs(A[k:, k:])
-        flat = int(np.argmax(sub))
-        i, j = divmod(flat, n - k)
-        if sub[i, j] <= rtol * scale:
+        big = sub.max()
+        if big <= rtol * scale:
             break
+        flat = int(np.argmax(sub.ravel() >= (1.0 - tie) * big))
+        i, j = divmod(flat, n - k)
         i += k
         j += k
         A[[k, i], :] = A[[i, k], :]

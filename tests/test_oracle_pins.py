@@ -323,6 +323,36 @@ def test_complete_pivot_lu_solves():
     assert np.abs(S @ xs - bs).max() <= 1e-10 * np.abs(bs).max()
 
 
+def test_complete_pivot_ties_are_broken_by_position():
+    """Entries within the tie window count as equal: a matrix with exactly tied
+    entries and the same matrix perturbed by a few ulps give one pivot sequence
+    (the first tied entry in row-major order), and so one generalised inverse of a
+    singular matrix.  Pinned by hand on a matrix whose pivots are known: every
+    entry of the all-ones 4 x 4 block ties, so the first pivot is (0, 0)."""
+    J = np.ones((4, 4))
+    rng = np.random.default_rng(4)
+    noisy = J * (1.0 + 4e-16 * rng.choice([-1.0, 1.0], size=(4, 4)))
+    for M in (J, noisy):
+        LU, rp, cp, rank = amg.complete_pivot_lu(M)
+        assert rank == 1 and rp[0] == 0 and cp[0] == 0
+    # a singular symmetric matrix with tied entries, exact and perturbed
+    Q = np.array([[2.0, -1.0, 0.0, -1.0], [-1.0, 2.0, -1.0, 0.0],
+                  [0.0, -1.0, 2.0, -1.0], [-1.0, 0.0, -1.0, 2.0]])  # ring Laplacian, rank 3
+    Qn = Q * (1.0 + 2e-16 * rng.standard_normal((4, 4)))
+    f1, f2 = amg.complete_pivot_lu(Q), amg.complete_pivot_lu(Qn)
+    assert f1[3] == f2[3] == 3
+    assert np.array_equal(f1[1], f2[1]) and np.array_equal(f1[2], f2[2])
+    b = Q @ rng.standard_normal(4)
+    x1, x2 = amg.complete_pivot_solve(f1, b), amg.complete_pivot_solve(f2, b)
+    assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
+    assert np.abs(Q @ x1 - b).max() <= 1e-12 * np.abs(b).max()
+    # without the window a 2-ulp bump of Q[2, 2] moves the first pivot there
+    Qb = Q.copy()
+    Qb[2, 2] = np.nextafter(np.nextafter(2.0, 3.0), 3.0)
+    assert amg.complete_pivot_lu(Qb, tie=0.0)[1][0] == 2
+    assert amg.complete_pivot_lu(Qb)[1][0] == 0
+
+
 def test_pcg_solution_matches_sparse_direct():
     prob = fp.elasticity_problem(4, seed=1)
     res, _ = amg.solve(prob, tol=1e-12)
