@@ -103,33 +103,61 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- reference arm
 
-def oracle_sample(n_sample: int, steps: int, warmup: int):
-    """Time the CPU oracle's solve phase on the same workload at n_sample^3."""
+ORACLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                     "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_child(args):
+    """Runs in a child process whose BLAS / OpenMP pools are limited to one thread by
+    the environment (set before numpy is imported there).  The oracle's setup is
+    untimed; then either one full FP64 AMG-PCG solve (--oracle-iters 0; its solution
+    is saved for the error against the GPU's), or --oracle-warmup + --oracle-steps
+    runs of exactly --oracle-iters PCG iterations each (a bounded sample) plus one
+    untimed full solve for the iteration count that scales a sample to a solve.
+    Prints one JSON line; cpu_over_wall = process CPU time / wall time of the timed
+    runs (about 1 for one busy core)."""
     from fem_inputs import elasticity_problem
     from oracle import amg
-    prob = elasticity_problem(n_sample, seed=1)
+    prob = elasticity_problem(args.n, seed=1)
     h = amg.build_hierarchy(prob)
-    times = []
-    its = None
-    res = None
-    for k in range(warmup + steps):
-        t0 = time.perf_counter()
+    out = {"n": args.n, "dofs": prob.n_dof}
+    if args.oracle_iters <= 0:
+        c0, t0 = time.process_time(), time.perf_counter()
         res, _ = amg.solve(prob, tol=TOL, h=h)
-        dt = time.perf_counter() - t0
-        its = res.iterations
-        if k >= warmup:
-            times.append(dt)
-    oracle_sample.last_x = res.x
-    return prob.n_dof, times, its
+        wall = time.perf_counter() - t0
+        out.update(solve_s=wall, iterations=res.iterations, converged=bool(res.converged),
+                   cpu_over_wall=(time.process_time() - c0) / wall,
+                   true_rel_residual=res.true_rel_residual)
+        if args.oracle_out:
+            np.save(args.oracle_out, res.x)
+    else:
+        full, _ = amg.solve(prob, tol=TOL, h=h)
+        times, cpu = [], 0.0
+        for k in range(args.oracle_warmup + args.oracle_steps):
+            c0, t0 = time.process_time(), time.perf_counter()
+            amg.solve(prob, tol=0.0, h=h, maxit=args.oracle_iters)
+            dt = time.perf_counter() - t0
+            if k >= args.oracle_warmup:
+                times.append(dt)
+                cpu += time.process_time() - c0
+        out.update(iterations=full.iterations, sample_iters=args.oracle_iters,
+                   sample_s=times, cpu_over_wall=cpu / sum(times),
+                   solve_s=float(np.mean(times)) * full.iterations / args.oracle_iters)
+    print(json.dumps(out), flush=True)
 
 
-def cpu_threads():
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] + [1])
-    except Exception:
-        return 1
+def run_oracle_child(n, iters=0, steps=1, warmup=0, out=None):
+    """The oracle leg in a single-threaded child process (see oracle_child)."""
+    env = dict(os.environ)
+    for k in ORACLE_THREAD_ENV:
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--n", str(n),
+           "--oracle-iters", str(iters), "--oracle-steps", str(steps),
+           "--oracle-warmup", str(warmup)]
+    if out:
+        cmd += ["--oracle-out", out]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def host_cpu():
@@ -154,23 +182,30 @@ def host_cpu():
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm, on the benchmarked workload: after its untimed
+    setup, each step runs --ref-iters FP64 AMG-PCG iterations of the n^3 solve from
+    x = 0 (a bounded sample), scaled to a whole solve by the oracle's own iteration
+    count to the tolerance."""
     if rank != 0:
         return
-    n_sample = args.ref_n
-    ndof, times, its = oracle_sample(n_sample, max(1, args.steps), max(0, min(args.warmup, 1)))
-    t = float(np.mean(times))
-    value = ndof / t
+    o = run_oracle_child(args.n, iters=args.ref_iters, steps=max(1, args.steps),
+                         warmup=max(0, min(args.warmup, 1)))
+    t = o["solve_s"]
+    value = o["dofs"] / t
     line = {
         "metric": metric_name(args.n), "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"elasticity {args.n}^3 P2 (oracle sample {n_sample}^3)",
+        "config": {"workload": f"elasticity {args.n}^3 P2 ({o['dofs']} DOF), CPU oracle",
                    "tol": TOL},
-        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cpu_threads(),
-                         "kind": "oracle", "host": host_cpu(),
-                         "sample": f"FP64 AMG-PCG solve phase of elasticity {n_sample}^3 "
-                                   f"({ndof} DOF, {its} iterations), setup excluded"},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1,
+                         "cpu_over_wall": o["cpu_over_wall"], "kind": "oracle",
+                         "host": host_cpu(), "threads": "BLAS/OpenMP pools set to 1 thread",
+                         "sample": f"FP64 AMG-PCG on elasticity {args.n}^3 ({o['dofs']} DOF), "
+                                   f"setup excluded: {o['sample_iters']} iterations per step, "
+                                   f"scaled to the {o['iterations']} iterations of a solve to "
+                                   f"{TOL:g}"},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -203,7 +238,8 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
                                                      outer_pair=args.outer_pair,
-                                                     gs_cluster=args.gs_cluster), stream=sptr)
+                                                     gs_cluster=args.gs_cluster,
+                                                     gs_flow=args.gs_flow), stream=sptr)
     setup_chosen_ms = 1e3 * (time.perf_counter() - t0)
     # the learned weights: selection by the trained network, measured fallback included
     learned = None
@@ -217,6 +253,15 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     plain = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64), stream=sptr)
     setup_plain_ms = 1e3 * (time.perf_counter() - t0)
+    # the chosen configuration with the Krylov operator in FP64 instructions
+    # (outer_pair = 0) and the same weights, to audit the FP32-pair operator
+    alt = None
+    if args.outer_pair:
+        alt = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32, outer_pair=0,
+                                                      gs_cluster=args.gs_cluster,
+                                                      gs_flow=args.gs_flow), stream=sptr)
+        if learned is not None:
+            alt.set_weights(*learned["weights"])
 
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
@@ -260,14 +305,23 @@ def run_gpu(args, rank, world):
     sampler.start()
     ms, stats = timed(chosen, args.steps, args.warmup)
     clocks = sampler.stop()
+    x_sol = {"chosen": x.cpu().numpy()}
     ms_e2e, stats_e2e = timed(chosen, args.steps, max(1, args.warmup // 2), host=True)
+    alt_res = None
+    if alt is not None:
+        ms_alt, stats_alt = timed(alt, max(1, args.steps // 2), 1)
+        x_sol["chosen_fp64_operator"] = x.cpu().numpy()
+        alt_res = {"value": world * ndof / (ms_alt * 1e-3), "ms_per_step": ms_alt,
+                   "iterations": stats_alt[-1]["iterations"],
+                   "note": "the chosen solve with outer_pair = 0: the Krylov operator "
+                           "products in FP64 instructions instead of FP32 pairs"}
     ms_plain, stats_plain = timed(plain, max(1, args.steps // 2), 1)
+    x_sol["plain_fp64"] = x.cpu().numpy()
 
-    # correctness of what was timed: recomputed residual of the last solution
+    # correctness of what was timed: recomputed residual of the chosen solution
     A = prob.a_scipy().tocsr()
-    xv = x.cpu().numpy()
     bv = prob.rhs()
-    true_rel = float(np.linalg.norm(bv - A @ xv) / np.linalg.norm(bv))
+    true_rel = float(np.linalg.norm(bv - A @ x_sol["chosen"]) / np.linalg.norm(bv))
 
     # dominant kernel: the FP32 multicolour GS sweep on level 0 (all colours)
     info0 = chosen.level_info(0)
@@ -299,7 +353,6 @@ def run_gpu(args, rank, world):
     # iteration counts versus mesh size (the paper's mesh-independence study), after the
     # timed region: the same workload family at 4^3, 8^3, 16^3 and the timed size
     mesh = None
-    gpu_x_ref = {}
     if rank == 0 and not args.no_mesh:
         mesh = {"n": [], "dofs": [], "chosen_iterations": [], "chosen_ms": [],
                 "plain_fp64_iterations": [], "plain_fp64_ms": [],
@@ -318,8 +371,6 @@ def run_gpu(args, rank, world):
                 st = hh.solve(bb, xx, TOL, device_ptrs=True)
                 mesh[key + "_iterations"].append(st.iterations)
                 mesh[key + "_ms"].append(st.solve_ms)
-                if n == args.ref_n:
-                    gpu_x_ref[key] = xx.cpu().numpy()
                 hh.free()
         mesh["n"].append(args.n)
         mesh["dofs"].append(ndof)
@@ -329,29 +380,34 @@ def run_gpu(args, rank, world):
         mesh["plain_fp64_ms"].append(ms_plain)
     peak, peak_kind = peaks()
     achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
-    # DRAM bytes of one level-0 sweep from the committed ncu summary of this kernel
-    # (32^3 only; cold-cache per launch, see the summary)
+    flow0 = stats[-1]["level_gs_flow"][0]
+    # DRAM bytes of one level-0 sweep (ncu, dram__bytes_read.sum + dram__bytes_write.sum
+    # over the colour launches of one sweep) from the data file beside the ncu summary
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "gs_colour_sweep_elasticity_n32.md")
+    prof = os.path.join(ROOT, "profiles", "gs_colour_sweep_elasticity_n32.json")
     if args.n == 32 and os.path.exists(prof):
-        for ln in open(prof):
-            if ln.startswith("dram_bytes_per_sweep:"):
-                traffic = int(ln.split(":")[1])
+        traffic = json.load(open(prof)).get("dram_bytes_per_sweep")
 
     cpu = None
     err_vs_oracle = None
     if rank == 0 and not args.no_cpu:
-        ndof_s, times, its = oracle_sample(args.ref_n, 1, 0)
-        xo = oracle_sample.last_x
-        if gpu_x_ref:
-            # the GPU solutions of the same system (mesh study) against the FP64 oracle's
-            err_vs_oracle = {"n": args.ref_n, "relative_l2": {
-                k: float(np.linalg.norm(v - xo) / np.linalg.norm(xo))
-                for k, v in gpu_x_ref.items()}}
-        cpu = {"value": ndof_s / times[0], "unit": "DOF/s", "cores": cpu_threads(),
-               "kind": "oracle", "host": host_cpu(),
-               "sample": f"FP64 AMG-PCG solve phase of elasticity {args.ref_n}^3 "
-                         f"({ndof_s} DOF, {its} iterations), setup excluded"}
+        # the FP64 oracle's solution of the same n^3 system, one single-threaded child
+        # process: its solve time is the CPU baseline, its x the reference solution
+        out = os.path.join(os.environ.get("BENCH_OUT_DIR", os.path.join(ROOT, "bench_out")),
+                           f"oracle_x_n{args.n}.npy")
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        o = run_oracle_child(args.n, out=out)
+        xo = np.load(out)
+        err_vs_oracle = {"n": args.n, "oracle_iterations": o["iterations"],
+                         "oracle_true_rel_residual": o["true_rel_residual"],
+                         "relative_l2": {k: float(np.linalg.norm(v - xo) / np.linalg.norm(xo))
+                                         for k, v in x_sol.items()}}
+        cpu = {"value": o["dofs"] / o["solve_s"], "unit": "DOF/s", "cores": 1,
+               "cpu_over_wall": o["cpu_over_wall"], "kind": "oracle", "host": host_cpu(),
+               "threads": "BLAS/OpenMP pools set to 1 thread",
+               "sample": f"one FP64 AMG-PCG solve of the benchmarked elasticity {args.n}^3 "
+                         f"system ({o['dofs']} DOF, {o['iterations']} iterations to "
+                         f"{TOL:g}), setup excluded"}
 
     value = world * ndof / (ms * 1e-3)
     launches = int(sum(s["kernel_launches"] for s in stats))
@@ -378,17 +434,22 @@ def run_gpu(args, rank, world):
                    "colours": stats[-1]["level_colours"],
                    "lanes_per_row": stats[-1]["level_group"],
                    "gs_cluster_ctas": stats[-1]["level_gs_cluster"],
+                   "gs_flow_lanes": stats[-1]["level_gs_flow"],
                    "cluster_from": stats[-1]["cluster_from"],
                    "cycle_kernel": stats[-1]["cycle_kernel"]},
         "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                        "iterations": stats_plain[-1]["iterations"]},
+        "chosen_fp64_operator": alt_res,
         "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_gs_pdl<float,G,U> multicolour Gauss-Seidel (unit: one "
-                               f"level-0 sweep = {sweep_launches} colour launches)",
+                     "kernel": (f"k_gs_flow<float,{flow0},U> multicolour Gauss-Seidel, one "
+                                "dataflow launch per sweep (unit: one level-0 sweep)")
+                               if flow0 else
+                               ("k_gs_pdl<float,G,U> multicolour Gauss-Seidel (unit: one "
+                                f"level-0 sweep = {sweep_launches} colour launches)"),
                      "unit_bytes": gs_bytes, "ms_per_unit": sweep_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs"},
         "kernels": {"spmv_fp64_level0": {"ms": spmv_ms, "bytes": spmv_bytes,
@@ -404,6 +465,8 @@ def run_gpu(args, rank, world):
         print(json.dumps(line), flush=True)
     chosen.free()
     plain.free()
+    if alt is not None:
+        alt.free()
 
 
 def run_profile(args):
@@ -424,7 +487,8 @@ def run_profile(args):
         # profiler sees every kernel
         opts = B.default_options(precision=prec, cycle_kernel=args.cycle_kernel,
                                  cluster_from=args.cluster_from, use_graphs=0,
-                                 gs_cluster=args.gs_cluster, outer_pair=args.outer_pair)
+                                 gs_cluster=args.gs_cluster, outer_pair=args.outer_pair,
+                                 gs_flow=args.gs_flow)
         h = B.setup_problem(prob, opts, stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)
@@ -683,7 +747,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--ref-n", type=int, default=16)
+    ap.add_argument("--ref-iters", type=int, default=4,
+                    help="reference arm: oracle PCG iterations per step (bounded sample)")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-iters", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-warmup", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="chosen solve without the learned-weights selection")
@@ -706,9 +776,13 @@ def main():
                     help="elasticity, batched: Krylov operator in FP32 pairs (1) or FP64 (0)")
     ap.add_argument("--gs-cluster", type=int, default=-1,
                     help="elasticity: one-cluster colour sweeps (-1 timed, 0 off, k CTAs)")
+    ap.add_argument("--gs-flow", type=int, default=-1, choices=[-1, 0, 1],
+                    help="elasticity: one-launch dataflow colour sweeps (-1 timed, 0 off, 1 on)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.oracle_child:
+        return oracle_child(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.profile:

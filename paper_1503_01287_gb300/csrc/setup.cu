@@ -749,10 +749,18 @@ __global__ void k_dense_BC(int np, int n3, const int* __restrict__ brow,
   }
 }
 
+// Entries within this relative window of the largest remaining magnitude count
+// as tied pivots, broken by row-major position: exact ties of a structured
+// coarse matrix then resolve the same way whatever rounding the Galerkin
+// products left in them.
+constexpr double kPivotTie = 1e-9;
+
 // Gaussian elimination with complete pivoting in one CTA, stopped at the
-// numerical rank: step k takes the largest |entry| of the trailing block (first
-// in row-major order among equal magnitudes), swaps it to (k, k) and eliminates.
-// It stops when that magnitude is <= rtol * max|K|.
+// numerical rank (Algorithm 1, step 6: the coarsest direct solve): step k takes
+// the largest magnitude M of the trailing block, pivots on its first entry in
+// row-major order with magnitude >= (1 - kPivotTie) M, swaps it to (k, k) and
+// eliminates.  It stops when M <= rtol * max|K|.
+
 __global__ void k_cplu(int m, double* __restrict__ A, int* __restrict__ rp, int* __restrict__ cp,
                        double rtol, int* __restrict__ rank_out) {
   __shared__ double sv[1024];
@@ -775,26 +783,36 @@ __global__ void k_cplu(int m, double* __restrict__ A, int* __restrict__ rp, int*
   int rank = 0;
   for (int k = 0; k < m; ++k) {
     int w = m - k;
-    double bv = -1.0;
+    // the largest magnitude M of the remaining block ...
+    double bv = 0.0;
+    for (long long q = tid; q < (long long)w * w; q += nt) {
+      int i = (int)(q / w), j = (int)(q % w);
+      bv = fmax(bv, fabs(A[(int64_t)(k + i) * m + k + j]));
+    }
+    sv[tid] = bv;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) sv[tid] = fmax(sv[tid], sv[tid + s]);
+      __syncthreads();
+    }
+    const double big = sv[0];
+    __syncthreads();
+    // ... and the pivot: the first entry in row-major order whose magnitude is
+    // within the relative tie window of M (rounding noise does not reorder ties)
+    const double thr = (1.0 - kPivotTie) * big;
     long long bi = LLONG_MAX;
     for (long long q = tid; q < (long long)w * w; q += nt) {
       int i = (int)(q / w), j = (int)(q % w);
-      double v = fabs(A[(int64_t)(k + i) * m + k + j]);
-      if (v > bv || (v == bv && q < bi)) { bv = v; bi = q; }
+      if (fabs(A[(int64_t)(k + i) * m + k + j]) >= thr) { bi = q; break; }
     }
-    sv[tid] = bv;
     si[tid] = bi;
     __syncthreads();
     for (int s = nt / 2; s > 0; s >>= 1) {
-      if (tid < s) {
-        double v2 = sv[tid + s];
-        long long i2 = si[tid + s];
-        if (v2 > sv[tid] || (v2 == sv[tid] && i2 < si[tid])) { sv[tid] = v2; si[tid] = i2; }
-      }
+      if (tid < s) si[tid] = min(si[tid], si[tid + s]);
       __syncthreads();
     }
     if (tid == 0) {
-      if (!(sv[0] > rtol * scale)) stop = 1;
+      if (!(big > rtol * scale)) stop = 1;
       piv_r = k + (int)(si[0] / w);
       piv_c = k + (int)(si[0] % w);
     }
@@ -825,7 +843,9 @@ __global__ void k_cplu(int m, double* __restrict__ A, int* __restrict__ rp, int*
     int w1 = m - k - 1;
     for (long long q = tid; q < (long long)w1 * w1; q += nt) {
       int i = k + 1 + (int)(q / w1), j = k + 1 + (int)(q % w1);
-      A[(int64_t)i * m + j] -= A[(int64_t)i * m + k] * A[(int64_t)k * m + j];
+      // product rounded, then the difference (no fused multiply-add)
+      A[(int64_t)i * m + j] =
+          __dsub_rn(A[(int64_t)i * m + j], __dmul_rn(A[(int64_t)i * m + k], A[(int64_t)k * m + j]));
     }
     __syncthreads();
     rank = k + 1;
@@ -847,14 +867,16 @@ __global__ void k_cplu_inverse(int m, const double* __restrict__ LU, const int* 
   for (int k = 0; k < r; ++k) {
     double yk = y[k];
     if (yk != 0.0)
-      for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) y[i] -= LU[(int64_t)i * m + k] * yk;
+      for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x)
+        y[i] = __dsub_rn(y[i], __dmul_rn(LU[(int64_t)i * m + k], yk));
     __syncthreads();
   }
   for (int k = r - 1; k >= 0; --k) {
     if (threadIdx.x == 0) y[k] /= LU[(int64_t)k * m + k];
     __syncthreads();
     double yk = y[k];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] -= LU[(int64_t)i * m + k] * yk;
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+      y[i] = __dsub_rn(y[i], __dmul_rn(LU[(int64_t)i * m + k], yk));
     __syncthreads();
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x)

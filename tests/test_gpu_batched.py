@@ -84,3 +84,39 @@ def test_batched_matches_single_and_direct(precision, k, tile, pair):
         assert st.iterations >= s1.iterations - 1
         if precision == 0:
             assert np.linalg.norm(x0.cpu().numpy() - x[0]) <= 1e-7 * np.linalg.norm(x[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_matches_oracle_per_rhs(precision):
+    """Every right-hand side of the batch against the oracle's solve of the same
+    system and right-hand side at the same tolerance (FP64 cycle: PCG; FP32 cycle:
+    flexible CG, as the batched path runs per right-hand side).  A right-hand side
+    whose residual reaches the tolerance one iteration apart from the oracle's
+    (rounding decides the crossing) differs from it by one step of the iteration, so
+    the check is: the GPU solution's error against the converged solution (oracle,
+    1e-13) is at most twice the oracle's own error at 1e-8, plus 1e-12."""
+    from oracle import amg
+    probs = _problems()
+    k = 4
+    rng = np.random.default_rng(17)
+    handles, Bs, Xs, rhs = [], [], [], []
+    for p in probs:
+        h = B().setup_problem(p, B().default_options(precision=precision))
+        r = _rhs(p, k, rng)
+        handles.append(h)
+        rhs.append(r)
+        Bs.append(torch.from_numpy(r.ravel()).cuda())
+        Xs.append(torch.zeros(k * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
+    rc, stats = B().solve_batched(handles, Bs, Xs, k, 1e-8)
+    assert rc == 0
+    for p, r, X in zip(probs, rhs, Xs):
+        oh = amg.build_hierarchy(p)
+        x = X.cpu().numpy().reshape(k, -1)
+        for j in range(k):
+            K, M = amg.operator(oh, 0), (lambda v: amg.precondition(oh, v))
+            ref = amg.pcg(K, M, r[j], 1e-8, flexible=precision == 1)
+            conv = amg.pcg(K, M, r[j], 1e-13)
+            assert ref.converged and conv.converged
+            e_or = np.linalg.norm(ref.x - conv.x)
+            e_gpu = np.linalg.norm(x[j] - conv.x)
+            assert e_gpu <= 2 * e_or + 1e-12 * np.linalg.norm(conv.x), (p.name, j, e_gpu, e_or)

@@ -10,7 +10,6 @@ by 2e-5 relative to |A||x|.
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 from fem_inputs import problems as fp
 from oracle import amg
@@ -18,7 +17,7 @@ from oracle import amg
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-STATE = {amg.STATE_C: 1, amg.STATE_F: 2}
+from parity_helpers import STATE, check_hierarchy, coarse_check  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,75 +47,6 @@ def oracle_opts(prob, **kw):
 
 def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-
-
-def check_hierarchy(h, oh, vals_tol=1e-12, check_colour=True):
-    assert h.n_levels == len(oh.levels), (h.n_levels, [lv.n for lv in oh.levels])
-    for l, lv in enumerate(oh.levels):
-        info = h.level_info(l)
-        last = l == len(oh.levels) - 1
-        assert info.n_nodes == lv.n
-        assert np.array_equal(h.level_array(l, "a_rowptr"), lv.rowptr)
-        assert np.array_equal(h.level_array(l, "a_col"), lv.col)
-        assert np.array_equal(h.level_array(l, "tags"), lv.tags)
-        v = h.level_array(l, "a_val").reshape(-1, 3, 3)
-        assert np.abs(v - lv.val).max() <= vals_tol * np.abs(lv.val).max()
-        d = h.level_array(l, "dinv").reshape(-1, 3, 3)
-        assert np.abs(d - lv.dinv).max() <= 1e-10 * np.abs(lv.dinv).max()
-        if not last:
-            st = h.level_array(l, "cf_state")
-            assert np.array_equal(st, np.vectorize(STATE.get)(lv.state))
-            prow = h.level_array(l, "p_rowptr")
-            pcol = h.level_array(l, "p_col")
-            ps = lv.P_structure.tocsr()
-            ps.sort_indices()
-            assert np.array_equal(prow, ps.indptr) and np.array_equal(pcol, ps.indices)
-            rows = np.repeat(np.arange(lv.n), np.diff(prow))
-            want = np.asarray(lv.P[rows, pcol]).ravel()
-            assert np.array_equal(h.level_array(l, "p_val"), want)
-            if check_colour and not oh.saddle:
-                assert np.array_equal(h.level_array(l, "colour"), lv.colour)
-        if oh.saddle:
-            assert info.n_pres == lv.npres
-            nb = 3 * lv.n
-            bc = h.level_array(l, "b_col")
-            brow = h.level_array(l, "b_rowptr")
-            bv = h.level_array(l, "b_val").reshape(-1, 3)
-            Bg = sp.csr_matrix((bv.ravel(), (np.repeat(np.repeat(np.arange(lv.npres),
-                                                                  np.diff(brow)), 3),
-                                              (3 * bc[:, None] + np.arange(3)).ravel())),
-                               shape=(lv.npres, nb))
-            assert abs(Bg - lv.B).max() <= vals_tol * max(abs(lv.B).max(), 1e-300)
-            crow = h.level_array(l, "c_rowptr")
-            Cg = sp.csr_matrix((h.level_array(l, "c_val"), h.level_array(l, "c_col"), crow),
-                               shape=(lv.npres, lv.npres))
-            assert abs(Cg - lv.C).max() <= vals_tol * max(abs(lv.C).max(), 1e-300) + 1e-300
-            if not last:
-                assert np.array_equal(h.level_array(l, "pcf_state"),
-                                      np.vectorize(STATE.get)(lv.p_state))
-                hs = lv.H_structure.tocsr()
-                hs.sort_indices()
-                assert np.array_equal(h.level_array(l, "h_rowptr"), hs.indptr)
-                assert np.array_equal(h.level_array(l, "h_col"), hs.indices)
-
-
-def coarse_check(h, oh):
-    L = len(oh.levels) - 1
-    m = 3 * oh.levels[L].n + oh.levels[L].npres
-    X = h.level_array(L, "coarse_inv").reshape(m, m)
-    rng = np.random.default_rng(5)
-    bvec = rng.standard_normal(m)
-    if oh.saddle:
-        from oracle import saddle as sd
-        K = sd.coarse_matrix(oh.levels[L])
-    else:
-        K = oh.levels[L].A.toarray()
-    bvec = K @ bvec          # consistent right-hand side
-    want = amg.complete_pivot_solve(oh.coarse_factor[1], bvec)
-    got = X @ bvec
-    assert np.abs(K @ got - bvec).max() <= 1e-9 * np.abs(bvec).max()
-    if not oh.saddle:
-        assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
 
 
 # --------------------------------------------------------------------------- setup parity
@@ -215,26 +145,13 @@ def test_preconditioner_matches_oracle(kind, cluster_from, cycle_kernel):
     h = gpu(prob, cluster_from=cluster_from, cycle_kernel=cycle_kernel)
     oh = amg.build_hierarchy(prob, oracle_opts(prob))
     if kind == "stokes":
-        # The Galerkin Stokes coarsest matrix is singular; any solution of a consistent
-        # coarse system is valid (Algorithm 1, step 6) and two generalised inverses differ
-        # by null-space parts that do not cancel after prolongation.  The coarse inverse is
-        # checked on its own (coarse_check); here the oracle uses the GPU's, so that the
-        # rest of the cycle is compared exactly.
-        L = len(oh.levels) - 1
-        m = 3 * oh.levels[L].n + oh.levels[L].npres
-        X = h.level_array(L, "coarse_inv").reshape(m, m)
+        # the singular Galerkin Stokes coarsest matrix: the GPU's generalised inverse
+        # must give the oracle's own complete-pivot solution (same tie rule)
         coarse_check(h, oh)
-        oh.coarse_factor = ("given", None)
-        orig = amg.coarse_solve
-        amg.coarse_solve = lambda hh, b: X @ b
-    try:
-        r = np.random.default_rng(3).standard_normal(prob.n_dof)
-        z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
-        h.apply_preconditioner(cuda(r), z)
-        want = amg.precondition(oh, r)
-    finally:
-        if kind == "stokes":
-            amg.coarse_solve = orig
+    r = np.random.default_rng(3).standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(cuda(r), z)
+    want = amg.precondition(oh, r)
     got = z.cpu().numpy()
     assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
 
@@ -296,7 +213,9 @@ def test_standalone_amg_matches_oracle(kind, opts):
     the colours in the pre-smoothing order (post_order 0 forces the reversed order)."""
     prob = {"laplace": lambda: fp.vector_laplace_problem(6, seed=2),
             "elasticity": lambda: fp.elasticity_problem(6, seed=4),
-            "mixed": lambda: fp.mixed_elasticity_problem(4, nu=0.45, seed=5)}[kind]()
+            # the stand-alone sGS iteration diverges on the random-traction mixed
+            # problems (in the oracle too); the Sec. 4.1 mixed setting converges
+            "mixed": lambda: fp.paper_setting_problem("mixed", 4)}[kind]()
     h = gpu(prob, krylov=B().AMG_KRYLOV_NONE, max_iterations=400, **opts)
     st, x = _solve(h, prob, 1e-8)
     okw = {k: v for k, v in opts.items() if k in ("m_pre", "m_post")}
@@ -330,13 +249,19 @@ def test_fp32_cycle_flexible_cg(cluster_from, cycle_kernel):
     prob = fp.elasticity_problem(10, seed=1)
     h = gpu(prob, precision=B().AMG_FP32, cluster_from=cluster_from, cycle_kernel=cycle_kernel)
     st, x = _solve(h, prob, 1e-8)
-    ref, _ = amg.solve(prob, tol=1e-12)
     assert st.converged and st.true_rel_residual <= 1.5e-8
-    # error against the FP64 oracle solution, bounded by the stopping rule
-    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
-    assert err <= 1e-5, err
-    ref8, _ = amg.solve(prob, tol=1e-8)
-    assert st.iterations <= ref8.iterations + 3
+    # against the FP64 oracle's flexible CG to the same tolerance: the FP32 cycle
+    # (with the FP32-pair operator) follows the FP64 iteration to about 1e-12 (4e-13
+    # to 7e-13 measured at 8^3-16^3) when both stop at the same iteration
+    ref8, _ = amg.solve(prob, tol=1e-8, method="fcg")
+    assert abs(st.iterations - ref8.iterations) <= 1, (st.iterations, ref8.iterations)
+    err = np.linalg.norm(x - ref8.x) / np.linalg.norm(ref8.x)
+    if st.iterations == ref8.iterations:
+        assert err <= 1e-10, err
+    else:      # one iteration apart: the difference is one step of the iteration
+        ref12, _ = amg.solve(prob, tol=1e-13)
+        e_or = np.linalg.norm(ref8.x - ref12.x)
+        assert np.linalg.norm(x - ref12.x) <= 2 * e_or + 1e-12 * np.linalg.norm(ref12.x)
 
 
 @pytest.mark.parametrize("kind", ["mixed", "stokes"])
@@ -395,6 +320,25 @@ def test_full_size_elasticity_32():
     A = prob.a_scipy().tocsr()
     b = prob.rhs()
     assert np.linalg.norm(b - A @ x) <= 1.5e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.slow
+def test_full_size_elasticity_32_solution_matches_oracle():
+    """The 32^3 elasticity workload solved by the oracle on the host (FP64 AMG-PCG,
+    1e-8) and on the GPU in the bench's two arms: the plain FP64 PCG within 1e-9 of
+    the oracle's solution, and the chosen FP32-cycle flexible CG with the FP32-pair
+    operator within 1e-9 as well (both follow the oracle's iteration, which stops
+    at the same count)."""
+    prob = fp.elasticity_problem(32, seed=1)
+    ref, _ = amg.solve(prob, tol=1e-8)
+    assert ref.converged
+    for precision in (B().AMG_FP64, B().AMG_FP32):
+        h = gpu(prob, precision=precision)
+        st, x = _solve(h, prob, 1e-8)
+        assert st.converged and abs(st.iterations - ref.iterations) <= 1
+        err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-9, (precision, err)
+        h.free()
 
 
 # --------------------------------------------------------------------------- errors
