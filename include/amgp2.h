@@ -189,6 +189,15 @@ typedef struct amg_options {
                                the reverse (descending) order for the Krylov
                                methods, which keeps the preconditioner
                                symmetric for CG; 0 reverse; 1 same           */
+  int32_t gs_flow;          /* multicolour Gauss-Seidel sweep of a coloured level
+                               as one cooperative launch in dataflow order (each
+                               row waits on per-node flags of the neighbours it
+                               reads new values from): -1 chosen per level by
+                               timing at setup (default), 0 never, 1 on every
+                               coloured level with the lanes per row of the
+                               one-launch-per-colour kernel (bitwise its
+                               results)                                       */
+  int32_t pad3;
 } amg_options;
 
 #define AMG_MAX_LEVELS 8
@@ -213,6 +222,8 @@ typedef struct amg_stats {
   int32_t cycle_kernel;     /* 1: one launch per operation, 2: persistent cycle */
   int32_t level_gs_cluster[AMG_MAX_LEVELS];  /* CTAs of the one-cluster sweep
                                (0: one launch per colour)                       */
+  int32_t level_gs_flow[AMG_MAX_LEVELS];     /* lanes per row of the one-launch
+                               dataflow sweep (0: not used on the level)        */
 } amg_stats;
 
 typedef struct amg_level_info {

@@ -72,7 +72,8 @@ class AmgOptions(C.Structure):
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
                 ("omega", C.c_double), ("omega_p", C.c_double),
                 ("batch_tile", C.c_int32), ("gs_cluster", C.c_int32),
-                ("outer_pair", C.c_int32), ("post_order", C.c_int32)]
+                ("outer_pair", C.c_int32), ("post_order", C.c_int32),
+                ("gs_flow", C.c_int32), ("pad3", C.c_int32)]
 
 
 class AmgStats(C.Structure):
@@ -86,7 +87,8 @@ class AmgStats(C.Structure):
                 ("level_colours", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_group", C.c_int32 * AMG_MAX_LEVELS),
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
-                ("level_gs_cluster", C.c_int32 * AMG_MAX_LEVELS)]
+                ("level_gs_cluster", C.c_int32 * AMG_MAX_LEVELS),
+                ("level_gs_flow", C.c_int32 * AMG_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -100,7 +102,8 @@ class AmgStats(C.Structure):
                 "level_colours": list(self.level_colours[:nl]),
                 "level_group": list(self.level_group[:nl]),
                 "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel,
-                "level_gs_cluster": list(self.level_gs_cluster[:nl])}
+                "level_gs_cluster": list(self.level_gs_cluster[:nl]),
+                "level_gs_flow": list(self.level_gs_flow[:nl])}
 
 
 class AmgLearned(C.Structure):

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamgp2.so")
-SOURCES = ["api.cu", "setup.cu", "cycle.cu", "krylov.cu", "batched.cu", "noalloc.cu", "learned.cu",
-           "mlp.cu"]
+SOURCES = ["api.cu", "setup.cu", "cycle.cu", "flow.cu", "krylov.cu", "batched.cu", "noalloc.cu",
+           "learned.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

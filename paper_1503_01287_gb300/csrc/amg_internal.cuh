@@ -114,6 +114,17 @@ struct Level {
   int gs_cl = 0;
   int gs_cl_g = 0;
   int gs_cl_bytes = 0;  // sizeof the arithmetic type the cluster size was chosen for
+  // the colour sweep as one cooperative launch in dataflow order (flow.cu):
+  // flow = lanes per block row (0: off); the column indices with their
+  // colour-order bits (stored order), [sweep number, finished CTAs], the tagged
+  // exchange array of new node values (8 words a node), and the row chunks of
+  // 32/flow rows that never cross a colour
+  DBuf<unsigned> fcol, fstate;
+  DBuf<unsigned long long> fxt;
+  DBuf<int> fchunk;
+  int flow = 0;
+  int flow_nchunks = 0;
+  int flow_grid32 = 0, flow_grid64 = 0;
   // learned weights of this level on the device: [0] relaxation multiplier,
   // [1] coarse-correction scale, [2] pressure-step multiplier (all 1: plain)
   double* wt = nullptr;
@@ -287,6 +298,14 @@ int solve_device(amg_handle* h, const double* b, double* x, double tol, amg_stat
 
 // noalloc.cu: the preconditioner application with static staging vectors
 void apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
+// one-launch dataflow colour sweep (flow.cu): its per-level data (false if the
+// level has no colours or the device has no cooperative launch), its chunks and
+// grid for G lanes per row (sets lv.flow = G), and the launch
+bool flow_prepare(amg_handle* h, Level& lv);
+void flow_set_group(amg_handle* h, Level& lv, int G);
+template <typename T>
+void launch_gs_flow(amg_handle* h, Level& lv, T* x, const T* b, const T* val, const T* dinv,
+                    bool reverse);
 // After the handle's stream has been synchronised: reads the device error word
 // that bounded waits (grid barrier, mbarrier) set when they give up, clears it
 // and fails with AMG_ERR_TIMEOUT naming `what` if it was set.

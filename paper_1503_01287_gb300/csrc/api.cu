@@ -97,6 +97,7 @@ void amg_default_options(amg_options* o) {
   o->gs_cluster = -1;
   o->outer_pair = 1;
   o->post_order = -1;     // resolved from the Krylov method in amg_setup
+  o->gs_flow = -1;
 }
 
 int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,
@@ -144,7 +145,8 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
       fail(AMG_ERR_INVALID, "gs_cluster must be -1, 0, 1, 2, 4, 8 or 16");
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
         h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1 ||
-        h->opt.post_order < -1 || h->opt.post_order > 1)
+        h->opt.post_order < -1 || h->opt.post_order > 1 || h->opt.gs_flow < -1 ||
+        h->opt.gs_flow > 1)
       fail(AMG_ERR_INVALID, "option out of range");
     // post-smoothing colour order: the stand-alone iteration sweeps the colours in the
     // pre-smoothing order, a Krylov method gets the symmetric (reversed) order
@@ -223,8 +225,12 @@ static void fill_stats(amg_handle* h, amg_stats* st) {
       st->level_colours[l] = h->L[l]->ncolours;
       st->level_group[l] = h->L[l]->group;
       st->level_gs_cluster[l] = h->L[l]->gs_cl;
+      // the dataflow sweep runs where neither the cluster sweep nor the
+      // persistent cycle takes the level's sweeps
+      st->level_gs_flow[l] = (h->use_full || h->L[l]->gs_cl > 0) ? 0 : h->L[l]->flow;
     } else {
       st->level_gs_cluster[l] = 0;
+      st->level_gs_flow[l] = 0;
       st->level_nodes[l] = st->level_pres[l] = st->level_colours[l] = 0;
       st->level_group[l] = 0;
       st->level_nnzb[l] = 0;

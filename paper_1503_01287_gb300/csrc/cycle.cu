@@ -1531,6 +1531,10 @@ struct Emit {
                               dinv, h->flag.p, h->stream);
     h->launches++;
   }
+  // a level's whole colour sweep as one dataflow launch (never recorded)
+  void gs_flow(Level& lv, T* x, const T* b, bool reverse) {
+    launch_gs_flow<T>(h, lv, x, b, LvVec<T>::val(lv), LvVec<T>::dinv(lv), reverse);
+  }
   void zero(T* a, int64_t n) {
     Phase P = blank(PH_ZERO);
     P.y = a; P.n = (int)n;
@@ -1687,6 +1691,11 @@ void e_smooth(Emit<T>& e, amg_handle* h, Level& lv, T* x, const T* b, bool post,
     return;
   }
   if (x_is_zero) e.zero(x, dofs);
+  if (!e.rec && lv.flow > 0 && !h->saddle && h->opt.smoother == AMG_SMOOTHER_GS &&
+      !(sizeof(T) == 4 && lv.val16.p)) {
+    e.gs_flow(lv, x, b, post);
+    return;
+  }
   const int G = group_for(lv);
   const T* val = LvVec<T>::val(lv);
   const T* dinv = LvVec<T>::dinv(lv);
@@ -2121,6 +2130,32 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group_gs = best;
+    auto sweep_ms = [&]() {
+      for (int r = 0; r < 7; ++r) {
+        if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) level_smooth<float>(h, (int)l, lv.x32.p, lv.b32.p, false, false);
+        else level_smooth<double>(h, (int)l, lv.x64.p, lv.b64.p, false, false);
+      }
+      return elapsed();
+    };
+    // the sweep as one dataflow launch: forced on with the chain's lanes per row
+    // (gs_flow = 1), or the fastest lanes per row if it beats the colour chain
+    lv.flow = 0;
+    if (h->opt.gs_flow != 0 && !(f32 && lv.val16.p) && flow_prepare(h, lv)) {
+      if (h->opt.gs_flow > 0) {
+        flow_set_group(h, lv, lv.group_gs);
+      } else {
+        float t_best = sweep_ms();
+        int g_best = 0;
+        for (int G : {4, 8, 16, 32}) {
+          flow_set_group(h, lv, G);
+          const float t = sweep_ms();
+          if (t < t_best) { t_best = t; g_best = G; }
+        }
+        if (g_best) flow_set_group(h, lv, g_best);
+        else lv.flow = 0;
+      }
+    }
     // the sweep as one cluster launch with the iterate in shared memory: the
     // forced cluster size, else the fastest (cluster size, lanes per row) if it
     // beats one launch per colour
@@ -2188,10 +2223,37 @@ void autotune_levels(amg_handle* h) {
       if (t_on < 0.99f * t_off) lv.gs_cl = keep;
     }
   }
+  // the same rule for the dataflow sweep, where it runs (no cluster sweep)
+  if (h->opt.gs_flow < 0) {
+    DBuf<double> r, z;
+    const int64_t n4 = h->L[0]->dofs4();
+    r.alloc(n4);
+    z.alloc(n4);
+    AMG_CUDA(cudaMemsetAsync(r.p, 0, r.bytes(), s));
+    auto precond_ms = [&]() {
+      for (int rep = 0; rep < 6; ++rep) {
+        if (rep == 2) AMG_CUDA(cudaEventRecord(e0, s));
+        if (f32) precondition_device<float>(h, r, z);
+        else precondition_device<double>(h, r, z);
+      }
+      return elapsed();
+    };
+    for (size_t l = 0; l < h->L.size(); ++l) {
+      Level& lv = *h->L[l];
+      if (lv.flow <= 0 || lv.gs_cl > 0) continue;
+      const float t_on = precond_ms();
+      const int keep = lv.flow;
+      lv.flow = 0;
+      const float t_off = precond_ms();
+      if (t_on < 0.99f * t_off) lv.flow = keep;
+    }
+  }
   {
     int ferr = 0;
     AMG_CUDA(cudaMemcpy(&ferr, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (ferr) fail(AMG_ERR_TIMEOUT, "an mbarrier wait of the one-launch colour sweep timed out");
+    if (ferr)
+      fail(AMG_ERR_TIMEOUT, "a bounded wait of a one-launch colour sweep (mbarrier or dataflow "
+                            "flag) timed out during setup tuning");
   }
   // cluster sub-cycle: the largest cluster that fits (16, else 8 CTAs), then the
   // fastest start level among 1..L (or none)
