@@ -239,7 +239,8 @@ def run_gpu(args, rank, world):
     chosen = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
                                                      outer_pair=args.outer_pair,
                                                      gs_cluster=args.gs_cluster,
-                                                     gs_flow=args.gs_flow), stream=sptr)
+                                                     gs_flow=args.gs_flow,
+                                                     gs_stream=args.gs_stream), stream=sptr)
     setup_chosen_ms = 1e3 * (time.perf_counter() - t0)
     # the learned weights: selection by the trained network, measured fallback included
     learned = None
@@ -259,7 +260,8 @@ def run_gpu(args, rank, world):
     if args.outer_pair:
         alt = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32, outer_pair=0,
                                                       gs_cluster=args.gs_cluster,
-                                                      gs_flow=args.gs_flow), stream=sptr)
+                                                      gs_flow=args.gs_flow,
+                                                     gs_stream=args.gs_stream), stream=sptr)
         if learned is not None:
             alt.set_weights(*learned["weights"])
 
@@ -381,6 +383,7 @@ def run_gpu(args, rank, world):
     peak, peak_kind = peaks()
     achieved = gs_bytes / (sweep_ms * 1e-3) / 1e9
     flow0 = stats[-1]["level_gs_flow"][0]
+    stream0 = stats[-1]["level_gs_stream"][0]
     # DRAM bytes of one level-0 sweep (ncu, dram__bytes_read.sum + dram__bytes_write.sum
     # over the colour launches of one sweep) from the data file beside the ncu summary
     traffic = None
@@ -435,6 +438,7 @@ def run_gpu(args, rank, world):
                    "lanes_per_row": stats[-1]["level_group"],
                    "gs_cluster_ctas": stats[-1]["level_gs_cluster"],
                    "gs_flow_lanes": stats[-1]["level_gs_flow"],
+                   "gs_stream_ctas_per_sm": stats[-1]["level_gs_stream"],
                    "cluster_from": stats[-1]["cluster_from"],
                    "cycle_kernel": stats[-1]["cycle_kernel"]},
         "plain_fp64": {"value": world * ndof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
@@ -448,6 +452,10 @@ def run_gpu(args, rank, world):
                      "kernel": (f"k_gs_flow<float,{flow0},U> multicolour Gauss-Seidel, one "
                                 "dataflow launch per sweep (unit: one level-0 sweep)")
                                if flow0 else
+                               (f"k_gs_stream<float,G,2> multicolour Gauss-Seidel, grid-stride "
+                                f"over {stream0} CTAs per SM (unit: one level-0 sweep = "
+                                f"{sweep_launches} colour launches)")
+                               if stream0 else
                                ("k_gs_pdl<float,G,U> multicolour Gauss-Seidel (unit: one "
                                 f"level-0 sweep = {sweep_launches} colour launches)"),
                      "unit_bytes": gs_bytes, "ms_per_unit": sweep_ms,
@@ -488,7 +496,7 @@ def run_profile(args):
         opts = B.default_options(precision=prec, cycle_kernel=args.cycle_kernel,
                                  cluster_from=args.cluster_from, use_graphs=0,
                                  gs_cluster=args.gs_cluster, outer_pair=args.outer_pair,
-                                 gs_flow=args.gs_flow)
+                                 gs_flow=args.gs_flow, gs_stream=args.gs_stream)
         h = B.setup_problem(prob, opts, stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": prec, **st.as_dict()}), flush=True)
@@ -778,6 +786,8 @@ def main():
                     help="elasticity: one-cluster colour sweeps (-1 timed, 0 off, k CTAs)")
     ap.add_argument("--gs-flow", type=int, default=-1, choices=[-1, 0, 1],
                     help="elasticity: one-launch dataflow colour sweeps (-1 timed, 0 off, 1 on)")
+    ap.add_argument("--gs-stream", type=int, default=-1,
+                    help="elasticity: grid-stride colour kernels (-1 timed, 0 off, k CTAs/SM)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

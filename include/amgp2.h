@@ -197,7 +197,14 @@ typedef struct amg_options {
                                coloured level with the lanes per row of the
                                one-launch-per-colour kernel (bitwise its
                                results)                                       */
-  int32_t pad3;
+  int32_t gs_stream;        /* one-launch-per-colour Gauss-Seidel kernels as
+                               grid-stride loops over a grid of k CTAs per SM,
+                               each warp loading its next rows' blocks while it
+                               updates the current ones: -1 k and the lanes per
+                               row chosen per level by timing at setup
+                               (default; 0 where one group of lanes per row is
+                               faster), 0 never, k = 1..8 forced (lanes per
+                               row as tuned for the chain)                     */
 } amg_options;
 
 #define AMG_MAX_LEVELS 8
@@ -224,6 +231,8 @@ typedef struct amg_stats {
                                (0: one launch per colour)                       */
   int32_t level_gs_flow[AMG_MAX_LEVELS];     /* lanes per row of the one-launch
                                dataflow sweep (0: not used on the level)        */
+  int32_t level_gs_stream[AMG_MAX_LEVELS];   /* CTAs per SM of the grid-stride
+                               colour kernel (0: one group of lanes per row)    */
 } amg_stats;
 
 typedef struct amg_level_info {

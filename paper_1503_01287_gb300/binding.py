@@ -73,7 +73,7 @@ class AmgOptions(C.Structure):
                 ("omega", C.c_double), ("omega_p", C.c_double),
                 ("batch_tile", C.c_int32), ("gs_cluster", C.c_int32),
                 ("outer_pair", C.c_int32), ("post_order", C.c_int32),
-                ("gs_flow", C.c_int32), ("pad3", C.c_int32)]
+                ("gs_flow", C.c_int32), ("gs_stream", C.c_int32)]
 
 
 class AmgStats(C.Structure):
@@ -88,7 +88,8 @@ class AmgStats(C.Structure):
                 ("level_group", C.c_int32 * AMG_MAX_LEVELS),
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
                 ("level_gs_cluster", C.c_int32 * AMG_MAX_LEVELS),
-                ("level_gs_flow", C.c_int32 * AMG_MAX_LEVELS)]
+                ("level_gs_flow", C.c_int32 * AMG_MAX_LEVELS),
+                ("level_gs_stream", C.c_int32 * AMG_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -103,7 +104,8 @@ class AmgStats(C.Structure):
                 "level_group": list(self.level_group[:nl]),
                 "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel,
                 "level_gs_cluster": list(self.level_gs_cluster[:nl]),
-                "level_gs_flow": list(self.level_gs_flow[:nl])}
+                "level_gs_flow": list(self.level_gs_flow[:nl]),
+                "level_gs_stream": list(self.level_gs_stream[:nl])}
 
 
 class AmgLearned(C.Structure):

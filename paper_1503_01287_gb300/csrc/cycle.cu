@@ -480,6 +480,9 @@ struct Phase {
   double omega;
   const double* wt;       // the level's learned weights (null: plain method)
   int vbf;                // PH_ROWS: values stored as BF16 (FP32 arithmetic)
+  int sctas;              // PH_ROWS, Gauss-Seidel: CTAs per SM of the streaming colour
+                          // kernel (0: one group of lanes per row, k_gs_pdl)
+  int xnc;                // PH_ROWS, Gauss-Seidel (k_gs_pdl): x through the L1 path
   const long long* off;   // PH_VANKA: offsets of the patch inverses
 };
 
@@ -599,7 +602,11 @@ __device__ __forceinline__ void exec_phase(const Phase& P, int tid, int nthr) {
 // writes guaranteed visible (the first colour of a sweep follows the
 // restriction that writes b).
 // One group of G lanes per stored row; each lane prefetches up to U blocks.
-template <typename T, int G, int U, typename V = T>
+// XNC: x is gathered through the read-only (L1-cached) path instead of L2 only.
+// Within one colour launch nothing that is gathered is written (rows of one
+// colour are not neighbours; a row reads its own x_i before writing it), and the
+// previous kernels' writes are visible after griddepcontrol.wait.
+template <typename T, int G, int U, typename V = T, bool XNC = false>
 __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict__ rows,
                                                 const int* __restrict__ rowptr,
                                                 const int* __restrict__ col,
@@ -645,13 +652,13 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
   if (active) {
     if (gl == 0) {
       ld3(b, i, b0, b1, b2);
-      VL<true>::node(x, i, xi0, xi1, xi2);
+      VL<!XNC>::node(x, i, xi0, xi1, xi2);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (j[u] < 0) continue;
       T x0, x1, x2;
-      VL<true>::node(x, j[u], x0, x1, x2);
+      VL<!XNC>::node(x, j[u], x0, x1, x2);
       s0 = fma(v[u][0], x0, s0); s0 = fma(v[u][1], x1, s0); s0 = fma(v[u][2], x2, s0);
       s1 = fma(v[u][3], x0, s1); s1 = fma(v[u][4], x1, s1); s1 = fma(v[u][5], x2, s1);
       s2 = fma(v[u][6], x0, s2); s2 = fma(v[u][7], x1, s2); s2 = fma(v[u][8], x2, s2);
@@ -660,7 +667,7 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
     for (int k = a + gl + U * G; k < e; k += G) {
       const int jj = ldg(col + k);
       T x0, x1, x2;
-      VL<true>::node(x, jj, x0, x1, x2);
+      VL<!XNC>::node(x, jj, x0, x1, x2);
       const V* vv = val + k;
       s0 = fma(ldg_v<T>(vv), x0, s0);
       s0 = fma(ldg_v<T>(vv + nnzb), x1, s0);
@@ -685,8 +692,8 @@ __global__ void __launch_bounds__(256) k_gs_pdl(int nrows, const int* __restrict
       xi1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2), xi2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
 }
 
-template <typename T, int G, typename V = T>
-void launch_gs_pdl(const Phase& P, cudaStream_t s) {
+template <typename T, int G, typename V, bool XNC>
+void launch_gs_pdl_x(const Phase& P, cudaStream_t s) {
   constexpr int U = (sizeof(T) == 8) ? (G >= 16 ? 2 : 3) : (G >= 16 ? 3 : 4);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(((int64_t)P.n * G + 255) / 256));
@@ -697,9 +704,15 @@ void launch_gs_pdl(const Phase& P, cudaStream_t s) {
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U, V>, P.n, P.rows, P.rowptr, P.col,
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_pdl<T, G, U, V, XNC>, P.n, P.rows, P.rowptr, P.col,
                               (const V*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
                               (const T*)P.dinv, P.wt));
+}
+
+template <typename T, int G, typename V = T>
+void launch_gs_pdl(const Phase& P, cudaStream_t s) {
+  if (P.xnc) launch_gs_pdl_x<T, G, V, true>(P, s);
+  else launch_gs_pdl_x<T, G, V, false>(P, s);
 }
 
 // Multicolour Gauss-Seidel sweep of one small level as ONE launch: a single CTA,
@@ -1295,8 +1308,170 @@ void launch_rows_mode(const Phase& P, int grid, cudaStream_t s) {
   }
 }
 
+// Multicolour Gauss-Seidel for one colour as a grid-stride kernel over a grid
+// of `sctas` CTAs per SM, launched with programmatic dependent launch.  Each warp
+// keeps two register sets of row operands (block columns, the values of U blocks
+// per lane, D_i^{-1}): the next row group's are loaded, straight from HBM and
+// without any dependence on x, while the current group gathers x and updates,
+// so the value stream does not stop at each group's x gathers, and the grid
+// leaves room on every SM for the next colour's kernel to start its prologue.
+// The loop runs in two halves with the sets' roles swapped (no register copy).
+// As in k_gs_pdl only setup constants are read before griddepcontrol.wait.
+template <typename T, int G, int U>
+struct GsSet {
+  int i, a, e;
+  int j[U];
+  T v[U][9];
+  T d[9];
+};
+
+template <typename T, int G, int U>
+__device__ __forceinline__ void gs_set_load(GsSet<T, G, U>& o, int g, int nrows,
+                                            const int* __restrict__ rows,
+                                            const int* __restrict__ rowptr,
+                                            const int* __restrict__ col,
+                                            const T* __restrict__ val, int64_t nnzb,
+                                            const T* __restrict__ dinv, int gl) {
+  o.a = o.e = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) o.j[u] = -1;
+  if (g >= nrows) return;
+  o.i = ldg(rows + g);
+  o.a = ldg(rowptr + g);
+  o.e = ldg(rowptr + g + 1);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int k = o.a + gl + u * G;
+    if (k < o.e) {
+      o.j[u] = __ldcs(col + k);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) o.v[u][q] = __ldcs(val + q * nnzb + k);
+    }
+  }
+  if (gl == 0) {
+    const T* dp = dinv + 12 * (int64_t)o.i;
+    ld3(dp, 0, o.d[0], o.d[1], o.d[2]);
+    ld3(dp, 1, o.d[3], o.d[4], o.d[5]);
+    ld3(dp, 2, o.d[6], o.d[7], o.d[8]);
+  }
+}
+
+template <typename T, int G, int U>
+__device__ __forceinline__ void gs_set_update(const GsSet<T, G, U>& o, bool active,
+                                              const int* __restrict__ col,
+                                              const T* __restrict__ val, int64_t nnzb, T* x,
+                                              const T* __restrict__ b, T om, int gl) {
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  T b0 = T(0), b1 = T(0), b2 = T(0), xi0 = T(0), xi1 = T(0), xi2 = T(0);
+  if (active) {
+    if (gl == 0) {
+      ld3(b, o.i, b0, b1, b2);
+      VL<true>::node(x, o.i, xi0, xi1, xi2);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (o.j[u] < 0) continue;
+      T x0, x1, x2;
+      VL<true>::node(x, o.j[u], x0, x1, x2);
+      s0 = fma(o.v[u][0], x0, s0); s0 = fma(o.v[u][1], x1, s0); s0 = fma(o.v[u][2], x2, s0);
+      s1 = fma(o.v[u][3], x0, s1); s1 = fma(o.v[u][4], x1, s1); s1 = fma(o.v[u][5], x2, s1);
+      s2 = fma(o.v[u][6], x0, s2); s2 = fma(o.v[u][7], x1, s2); s2 = fma(o.v[u][8], x2, s2);
+    }
+    for (int k = o.a + gl + U * G; k < o.e; k += G) {   // blocks beyond the set
+      const int jj = ldg(col + k);
+      T x0, x1, x2;
+      VL<true>::node(x, jj, x0, x1, x2);
+      const T* vv = val + k;
+      s0 = fma(ldg(vv), x0, s0);
+      s0 = fma(ldg(vv + nnzb), x1, s0);
+      s0 = fma(ldg(vv + 2 * nnzb), x2, s0);
+      s1 = fma(ldg(vv + 3 * nnzb), x0, s1);
+      s1 = fma(ldg(vv + 4 * nnzb), x1, s1);
+      s1 = fma(ldg(vv + 5 * nnzb), x2, s1);
+      s2 = fma(ldg(vv + 6 * nnzb), x0, s2);
+      s2 = fma(ldg(vv + 7 * nnzb), x1, s2);
+      s2 = fma(ldg(vv + 8 * nnzb), x2, s2);
+    }
+  }
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  }
+  if (!active || gl != 0) return;
+  const T r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+  const T* d = o.d;
+  st3(x, o.i, xi0 + om * (d[0] * r0 + d[1] * r1 + d[2] * r2),
+      xi1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2), xi2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
+}
+
+template <typename T, int G, int U>
+__global__ void __launch_bounds__(256) k_gs_stream(int nrows, const int* __restrict__ rows,
+                                                   const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col,
+                                                   const T* __restrict__ val, int64_t nnzb, T* x,
+                                                   const T* __restrict__ b,
+                                                   const T* __restrict__ dinv,
+                                                   const double* __restrict__ wt) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane & (G - 1);
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int step = (int)((gridDim.x * blockDim.x) >> 5) * R;
+  GsSet<T, G, U> A, Bs;
+  int g = warp * R + sub;
+  gs_set_load(A, g, nrows, rows, rowptr, col, val, nnzb, dinv, gl);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
+  // rows of one colour are not neighbours: the x gathers read only earlier
+  // colours' values (L2-coherent loads all the same, the kernel writes x)
+  for (int base = warp * R; base < nrows; base += 2 * step) {
+    gs_set_load(Bs, g + step, nrows, rows, rowptr, col, val, nnzb, dinv, gl);
+    gs_set_update(A, g < nrows, col, val, nnzb, x, b, om, gl);
+    if (base + step >= nrows) break;
+    gs_set_load(A, g + 2 * step, nrows, rows, rowptr, col, val, nnzb, dinv, gl);
+    gs_set_update(Bs, g + step < nrows, col, val, nnzb, x, b, om, gl);
+    g += 2 * step;
+  }
+}
+
+template <typename T, int G>
+void launch_gs_stream(const Phase& P, cudaStream_t s) {
+  constexpr int U = 2;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t want = ((int64_t)P.n * G + 255) / 256;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.sctas * sms)));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_stream<T, G, U>, P.n, P.rows, P.rowptr, P.col,
+                              (const T*)P.val, P.nnz, (T*)P.y, (const T*)P.b,
+                              (const T*)P.dinv, P.wt));
+}
+
 template <typename T, typename V>
 void launch_rows_v(const Phase& P, cudaStream_t s, bool pdl) {
+  if constexpr (std::is_same<T, V>::value) {
+    if (pdl && P.mode == kGS && P.rows && P.sctas > 0) {
+      switch (P.G) {
+        case 4: launch_gs_stream<T, 4>(P, s); return;
+        case 8: launch_gs_stream<T, 8>(P, s); return;
+        case 16: launch_gs_stream<T, 16>(P, s); return;
+        default: launch_gs_stream<T, 32>(P, s); return;
+      }
+    }
+  }
   if (pdl && P.mode == kGS && P.rows) {
     switch (P.G) {
       case 4: launch_gs_pdl<T, 4, V>(P, s); return;
@@ -1508,6 +1683,8 @@ struct Emit {
     P.mode = mode; P.G = G; P.n = nrows; P.rows = order ? order + first : nullptr;
     P.rowptr = lv.k_rowptr() + first; P.col = lv.k_col();
     P.val = val; P.nnz = lv.nnzb; P.x = x; P.b = b; P.y = y; P.dinv = dinv; P.omega = omega;
+    P.sctas = mode == kGS ? lv.gs_stream : 0;
+    P.xnc = mode == kGS ? lv.gs_xnc : 0;
     if (sizeof(T) == 4 && lv.val16.p && (const void*)val == (const void*)lv.val32.p) {
       P.val = lv.val16.p;   // BF16 storage of this level's values
       P.vbf = 1;
@@ -2130,6 +2307,22 @@ void autotune_levels(amg_handle* h) {
       if (ms < best_ms) { best_ms = ms; best = G; }
     }
     lv.group_gs = best;
+    lv.gs_stream = 0;
+    // the colour kernel's x gathers through L1 or L2 only: the faster
+    {
+      lv.gs_xnc = 0;
+      float t_l2 = 0.f, t_l1 = 0.f;
+      for (int xnc : {0, 1}) {
+        lv.gs_xnc = xnc;
+        for (int r = 0; r < 7; ++r) {
+          if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
+          if (f32) level_smooth<float>(h, (int)l, lv.x32.p, lv.b32.p, false, false);
+          else level_smooth<double>(h, (int)l, lv.x64.p, lv.b64.p, false, false);
+        }
+        (xnc ? t_l1 : t_l2) = elapsed();
+      }
+      lv.gs_xnc = t_l1 < t_l2 ? 1 : 0;
+    }
     auto sweep_ms = [&]() {
       for (int r = 0; r < 7; ++r) {
         if (r == 2) AMG_CUDA(cudaEventRecord(e0, s));
@@ -2138,6 +2331,26 @@ void autotune_levels(amg_handle* h) {
       }
       return elapsed();
     };
+    // the grid-stride colour kernel (register double buffering, a grid of a few
+    // CTAs per SM), for the cycle's precision: kept with its (CTAs per SM, lanes
+    // per row) if it beats one group of lanes per row
+    if (h->opt.gs_stream > 0) {
+      lv.gs_stream = h->opt.gs_stream;
+    } else if (h->opt.gs_stream < 0) {
+      float t_best = sweep_ms();
+      int c_best = 0, g_best = lv.group_gs;
+      const int g_keep = lv.group_gs;
+      for (int G : {8, 16, 32}) {
+        for (int cps : {1, 2, 3, 4}) {
+          lv.group_gs = G;
+          lv.gs_stream = cps;
+          const float t = sweep_ms();
+          if (t < t_best) { t_best = t; c_best = cps; g_best = G; }
+        }
+      }
+      lv.gs_stream = c_best;
+      lv.group_gs = c_best ? g_best : g_keep;
+    }
     // the sweep as one dataflow launch: forced on with the chain's lanes per row
     // (gs_flow = 1), or the fastest lanes per row if it beats the colour chain
     lv.flow = 0;
