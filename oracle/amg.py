@@ -222,10 +222,12 @@ class Options:
     separate: bool = True           # separated (new) vs non-separating graph
     omega_p: float = 0.125          # sGS pressure step
     # learned multipliers (1: the plain method): relaxation, coarse-grid
-    # correction scale, sGS pressure step
+    # correction scale, sGS pressure step; level_weights, if given, holds one
+    # (ws, wc, wp) per level and overrides the three
     ws: float = 1.0
     wc: float = 1.0
     wp: float = 1.0
+    level_weights: list = None
     # colour order of the post-smoothing sweeps (Gauss-Seidel, Vanka): "reverse"
     # (descending: with the ascending pre-smoothing the cycle is a symmetric
     # preconditioner, as CG needs) or "same" (ascending, as pre-smoothing: the
@@ -409,15 +411,24 @@ def gs_sweep(lv: Level, x, b, reverse: bool = False, ws: float = 1.0):
     return x
 
 
+def level_multipliers(o: Options, l: int):
+    """(ws, wc, wp) of level l: the per-level row if given, else the three globals."""
+    if o.level_weights is not None and l < len(o.level_weights):
+        ws, wc, wp = o.level_weights[l]
+        return float(ws), float(wc), float(wp)
+    return o.ws, o.wc, o.wp
+
+
 def smooth(h: Hierarchy, l: int, x, b, post: bool):
     lv = h.levels[l]
     o = h.opts
     if h.saddle:
         from . import saddle as sd
         return sd.smooth(h, l, x, b, post)
+    ws = level_multipliers(o, l)[0]
     if o.smoother == "jacobi":
-        return jacobi_sweep(lv, x, b, o.omega * o.ws)
-    return gs_sweep(lv, x, b, reverse=post and o.post_order == "reverse", ws=o.ws)
+        return jacobi_sweep(lv, x, b, o.omega * ws)
+    return gs_sweep(lv, x, b, reverse=post and o.post_order == "reverse", ws=ws)
 
 
 def operator(h: Hierarchy, l: int):
@@ -462,7 +473,7 @@ def amg_cycle(h: Hierarchy, l: int, x, b):
         xc = np.zeros_like(bc)
         for _ in range(o.nu):
             xc = amg_cycle(h, l + 1, xc, bc)
-    x = x + o.wc * prolong(h, l, xc)
+    x = x + level_multipliers(o, l)[1] * prolong(h, l, xc)
     for _ in range(o.m_post):
         x = smooth(h, l, x, b, post=True)
     return x

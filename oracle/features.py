@@ -15,6 +15,11 @@ The network sees [log10(unknowns) / 7, the five numbers of level 0, the five
 of level 1, the mean over pressure rows of C_kk / S_D,kk (saddle kinds, S_D the
 sGS scaling diag(C + B (D / omega)^-1 B^T)), 1 for saddle kinds].
 
+The per-level inputs (level_features) describe one non-coarsest level l and the
+level below it: [log10(unknowns of level l) / 7, the five numbers of level l,
+the first four of level l + 1, l / 4, the pressure mean of level l (saddle
+kinds with an sGS scaling), 1 for saddle kinds].
+
 These are definitions (there is no published formula: the learned part has no
 basis in the paper), written out node by node so that each can be read off.
 """
@@ -84,4 +89,25 @@ def features(h: amg.Hierarchy, saddle: bool) -> np.ndarray:
         keep = s > 0.0
         pres = float(np.mean(cd[keep] / s[keep])) if keep.any() else 0.0
     f += [pres, 1.0 if saddle else 0.0]
+    return np.array(f, dtype=np.float64)
+
+
+def _pressure_mean(lv) -> float:
+    if lv.npres <= 0 or "schur_diag" not in lv.extra:
+        return 0.0
+    s = lv.extra["schur_diag"]
+    cd = lv.C.diagonal()
+    keep = s > 0.0
+    return float(np.mean(cd[keep] / s[keep])) if keep.any() else 0.0
+
+
+def level_features(h: amg.Hierarchy, l: int, saddle: bool) -> np.ndarray:
+    """The 13 per-level inputs of non-coarsest level l (see the module text)."""
+    L = h.levels
+    lv = L[l]
+    dofs = 3 * lv.n + (lv.npres if saddle else 0)
+    f = [np.log10(dofs) / 7.0]
+    f += _level_stats(lv, l + 1 < len(L))
+    f += _level_stats(L[l + 1], l + 2 < len(L))[:4]
+    f += [l / 4.0, _pressure_mean(lv) if saddle else 0.0, 1.0 if saddle else 0.0]
     return np.array(f, dtype=np.float64)

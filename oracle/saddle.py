@@ -255,10 +255,11 @@ def smooth(h, l, x, b, post):
     u, p = x[:nu].copy(), x[nu:].copy()
     f, g = b[:nu], b[nu:]
     ru = f - lv.A @ u - lv.B.T @ p
-    u = u + o.omega * o.ws * amg.apply_dinv(lv.dinv, ru)
+    ws, _, wp = amg.level_multipliers(o, l)
+    u = u + o.omega * ws * amg.apply_dinv(lv.dinv, ru)
     sdg = lv.extra["schur_diag"]
     rp = lv.B @ u - lv.C @ p - g
-    p = p + o.omega_p * o.wp * np.divide(rp, sdg, out=np.zeros_like(rp), where=sdg != 0.0)
+    p = p + o.omega_p * wp * np.divide(rp, sdg, out=np.zeros_like(rp), where=sdg != 0.0)
     return np.concatenate([u, p])
 
 
