@@ -248,8 +248,10 @@ def run_gpu(args, rank, world):
         t0 = time.perf_counter()
         theta = np.load(os.path.join(ROOT, "paper_1503_01287_gb300", "weights", "mlp_theta.npy"))
         res = chosen.learn_weights(theta)
-        learned = {"weights": list(res.weights), "fell_back": res.fell_back,
-                   "rho_plain": res.rho_plain, "rho_learned": res.rho_learned,
+        rd = res.as_dict()
+        learned = {"weights": list(res.weights), "level_weights": rd["level_weights"],
+                   "fell_back": res.fell_back, "rho_plain": res.rho_plain,
+                   "rho_learned": res.rho_learned,
                    "selection_ms": 1e3 * (time.perf_counter() - t0)}
     t0 = time.perf_counter()
     plain = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64), stream=sptr)
@@ -263,7 +265,7 @@ def run_gpu(args, rank, world):
                                                       gs_flow=args.gs_flow,
                                                      gs_stream=args.gs_stream), stream=sptr)
         if learned is not None:
-            alt.set_weights(*learned["weights"])
+            alt.set_level_weights(learned["level_weights"])
 
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
@@ -391,6 +393,10 @@ def run_gpu(args, rank, world):
     if args.n == 32 and os.path.exists(prof):
         traffic = json.load(open(prof)).get("dram_bytes_per_sweep")
 
+    configs_block = None
+    if rank == 0 and not args.no_configs:
+        configs_block = run_configs(args, B)
+
     cpu = None
     err_vs_oracle = None
     if rank == 0 and not args.no_cpu:
@@ -466,6 +472,7 @@ def run_gpu(args, rank, world):
                     "precond_fp32": {"ms": precond_ms, "launches": precond_launches},
                     "levels_fp32": breakdown},
         "clocks": clocks,
+        "configs": configs_block,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -615,6 +622,204 @@ def run_replay(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- other configs
+
+def gen_worker(task):
+    """Input generation in a spawned worker process (no CUDA): ("stokes", n),
+    ("mixed", (n, nu, seed)) or ("batched", spec)."""
+    kind, arg = task
+    from fem_inputs import problems as fp
+    if kind == "stokes":
+        return fp.stokes_lid_problem(arg)
+    if kind == "mixed":
+        n, nu, seed = arg
+        return fp.mixed_elasticity_family(n, [nu], seed=seed)[0]
+    return fp.elasticity_problem(arg["n"], seed=arg["seed"], nu=arg["nu"], lengths=arg["lengths"],
+                                 n_rhs=16, traction="gaussian")
+
+
+def oracle_worker(task):
+    """The oracle's solution of one system, in a spawned worker: ("stokes", n, tol) the
+    lid-driven Stokes solve (FGMRES, pressure mean zero); ("batched", spec, rhs index,
+    tol) flexible CG on one right-hand side of a batched problem."""
+    from oracle import amg
+    t0 = time.perf_counter()
+    if task[0] == "stokes":
+        from fem_inputs import problems as fp
+        prob = fp.stokes_lid_problem(task[1])
+        res, _ = amg.solve(prob, tol=task[2])
+        return {"x": res.x, "iterations": res.iterations, "s": time.perf_counter() - t0}
+    spec, j, tol = task[1], task[2], task[3]
+    prob = gen_worker(("batched", spec))
+    oh = amg.build_hierarchy(prob)
+    f = np.ascontiguousarray(prob.f.reshape(16, -1)[j])   # as the batched solve gets it
+    res = amg.pcg(amg.operator(oh, 0), lambda v: amg.precondition(oh, v), f, tol, flexible=True)
+    return {"x": res.x, "iterations": res.iterations, "s": time.perf_counter() - t0}
+
+
+def saddle_results(B, probs, gmres_restart, tol, steps, warmup, theta, variants=None):
+    """The saddle workloads' solves: per system the chosen solve (FP32 cycle with the
+    learned-weights selection, measured fallback included), plain FP64 and the
+    Braess-Sarazin FP32 cycle, FGMRES(gmres_restart); median CUDA-event solve times.
+    Returns (rows, totals, last solution of each variant per system)."""
+    import torch
+    variants = variants or ("chosen", "plain_fp64", "braess_sarazin_fp32")
+    rows, xs = [], []
+    tot = {"dofs": 0}
+    for prob in probs:
+        b = torch.from_numpy(prob.rhs()).cuda()
+        x = torch.zeros_like(b)
+        t1 = time.time()
+        mk = {"chosen": dict(precision=B.AMG_FP32), "plain_fp64": dict(precision=B.AMG_FP64),
+              "braess_sarazin_fp32": dict(precision=B.AMG_FP32, smoother=B.AMG_SMOOTHER_BS)}
+        out, sol, res = {}, {}, None
+        for variant in variants:
+            h = B.setup_problem(prob, B.default_options(gmres_restart=gmres_restart,
+                                                        max_iterations=1000, **mk[variant]))
+            if variant == "chosen":
+                res = h.learn_weights(theta)
+            for _ in range(max(1, warmup)):
+                x.zero_()
+                h.solve(b, x, tol, device_ptrs=True)
+            ms, st = [], None
+            for _ in range(max(1, steps)):
+                x.zero_()
+                st = h.solve(b, x, tol, device_ptrs=True)
+                ms.append(st.solve_ms)
+            out[variant] = {"iterations": st.iterations, "converged": bool(st.converged),
+                            "true_rel_residual": st.true_rel_residual, "ms": float(np.median(ms))}
+            sol[variant] = x.cpu().numpy()
+            tot[variant + "_ms"] = tot.get(variant + "_ms", 0.0) + out[variant]["ms"]
+            h.free()
+        row = {"nu": prob.params.get("nu"), "dofs": prob.n_dof, **out,
+               "setup_and_selection_s": time.time() - t1}
+        if res is not None:
+            row.update(weights=list(res.weights), fell_back=res.fell_back)
+        rows.append(row)
+        xs.append(sol)
+        tot["dofs"] += prob.n_dof
+    return rows, tot, xs
+
+
+def batched_results(B, probs, nrhs, steps, warmup, outer_pair=1):
+    """amg_solve_batched of the problems (FP32 cycle, flexible CG per right-hand side):
+    (summary dict, handles, solutions).  Times are the graph launch's CUDA events."""
+    import torch
+    handles, Bs, Xs = [], [], []
+    t0 = time.perf_counter()
+    for p in probs:
+        h = B.setup_problem(p, B.default_options(precision=B.AMG_FP32, outer_pair=outer_pair))
+        handles.append(h)
+        Bs.append(torch.from_numpy(np.ascontiguousarray(p.f.reshape(nrhs, -1))).cuda())
+        Xs.append(torch.zeros(nrhs * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    times, rc, stats = [], 0, None
+    for k in range(warmup + steps):
+        rc, stats = B.solve_batched(handles, Bs, Xs, nrhs, TOL)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(stats[0].solve_ms)
+    ms = float(np.mean(times))
+    dof_rhs = sum(p.n_dof for p in probs) * nrhs
+    its = [s.iterations for s in stats]
+    summary = {"value": dof_rhs / (ms * 1e-3), "unit": "DOF*RHS/s", "ms_per_step": ms,
+               "problems": len(probs), "rhs": nrhs, "dof_total": sum(p.n_dof for p in probs),
+               "iterations": {"min": min(its), "max": max(its)},
+               "true_rel_residual_max": max(s.true_rel_residual for s in stats),
+               "converged": rc == 0, "setup_s": setup_s,
+               "gpu_launches": int(sum(s.kernel_launches for s in stats))}
+    return summary, handles, [X.cpu().numpy().reshape(nrhs, -1) for X in Xs]
+
+
+def run_configs(args, B, budget_s=300.0):
+    """The other workloads of the benchmark family, one short entry each: lid-driven
+    Stokes 24^3, mixed elasticity 40^3 (three nu), and the batched 64 x 16 solve, with
+    iterations, times and the error against the FP64 oracle where the oracle finishes
+    in seconds (Stokes 24^3: the full solve; batched: the two smallest problems, first
+    and last right-hand side; mixed 40^3: none, the recomputed residual instead).
+    Inputs are generated and the oracle runs in spawned worker processes while the
+    GPU works."""
+    import multiprocessing as mp
+    from fem_inputs import configs
+    t_start = time.time()
+    theta = np.load(os.path.join(ROOT, "paper_1503_01287_gb300", "weights", "mlp_theta.npy"))
+    specs = configs.batched_specs(64, seed=4)
+    small = sorted(range(len(specs)), key=lambda i: specs[i]["n"])[:2]
+    out = {}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        o_stokes = pool.apply_async(oracle_worker, (("stokes", 24, TOL),))
+        o_batch = [pool.apply_async(oracle_worker, (("batched", specs[i], j, TOL),))
+                   for i in small for j in (0, 15)]
+        g_stokes = pool.apply_async(gen_worker, (("stokes", 24),))
+        g_mixed = [pool.apply_async(gen_worker, (("mixed", (40, nu, 5)),))
+                   for nu in (0.49, 0.499, 0.4999)]
+        g_batch = [pool.apply_async(gen_worker, (("batched", sp),)) for sp in specs]
+        try:
+            prob = g_stokes.get()
+            rows, tot, xs = saddle_results(B, [prob], 300, TOL, 2, 1, theta,
+                                           variants=("chosen", "plain_fp64"))
+            ent = {"workload": "stokes_lid_n24: lid-driven Taylor-Hood Stokes, 24^3",
+                   "dofs": prob.n_dof, "value": prob.n_dof / (tot["chosen_ms"] * 1e-3),
+                   "unit": "DOF/s", "plain_fp64_value": prob.n_dof / (tot["plain_fp64_ms"] * 1e-3),
+                   **rows[0]}
+            o = o_stokes.get()
+            n3 = 3 * prob.n_nodes
+            w = prob.p_weights
+
+            def rel(a, bb):
+                return float(np.linalg.norm(a - bb) / np.linalg.norm(bb))
+            ent["error_vs_oracle"] = {
+                "oracle_iterations": o["iterations"], "oracle_s": o["s"],
+                "velocity_rel_l2": {k: rel(v[:n3], o["x"][:n3]) for k, v in xs[0].items()},
+                "pressure_rel_l2": {k: rel(v[n3:] - (w @ v[n3:]) / w.sum(),
+                                           o["x"][n3:] - (w @ o["x"][n3:]) / w.sum())
+                                    for k, v in xs[0].items()},
+                "note": "GPU FGMRES(300) and oracle FGMRES(50), both to 1e-8"}
+            out["stokes_lid_n24"] = ent
+        except Exception as e:   # a config failing must not cost the main line
+            out["stokes_lid_n24"] = {"error": repr(e)[:300]}
+        try:
+            if time.time() - t_start > budget_s:
+                raise TimeoutError("configs time budget spent")
+            probs = [g.get() for g in g_mixed]
+            rows, tot, _ = saddle_results(B, probs, 300, TOL, 1, 1, theta,
+                                          variants=("chosen", "plain_fp64"))
+            out["mixed_elast_n40"] = {
+                "workload": "mixed_elast_n40: mixed elasticity 40^3, jittered, "
+                            "nu in {0.49, 0.499, 0.4999}",
+                "dofs": tot["dofs"], "value": tot["dofs"] / (tot["chosen_ms"] * 1e-3),
+                "unit": "DOF/s",
+                "plain_fp64_value": tot["dofs"] / (tot["plain_fp64_ms"] * 1e-3), "rows": rows,
+                "error_vs_oracle": None,
+                "note": "no oracle solve at this size (minutes per system on one core); "
+                        "true_rel_residual is recomputed in FP64 at exit"}
+        except Exception as e:
+            out["mixed_elast_n40"] = {"error": repr(e)[:300]}
+        try:
+            if time.time() - t_start > budget_s:
+                raise TimeoutError("configs time budget spent")
+            probs = [g.get() for g in g_batch]
+            summ, handles, xs = batched_results(B, probs, 16, 1, 1)
+            errs = []
+            for k, (i, j) in enumerate([(i, j) for i in small for j in (0, 15)]):
+                o = o_batch[k].get()
+                errs.append(float(np.linalg.norm(xs[i][j] - o["x"]) / np.linalg.norm(o["x"])))
+            summ["error_vs_oracle"] = {
+                "sample": "problems " + ", ".join(str(i) for i in small) +
+                          " (the two smallest), right-hand sides 0 and 15, oracle flexible CG",
+                "relative_l2_max": max(errs)}
+            summ["workload"] = "batched_elast: 64 problems x 16 right-hand sides"
+            for h in handles:
+                h.free()
+            out["batched_elast"] = summ
+        except Exception as e:
+            out["batched_elast"] = {"error": repr(e)[:300]}
+    out["wall_s"] = time.time() - t_start
+    return out
+
+
 def run_mixed(args):
     """Mixed displacement-pressure elasticity on jittered 40^3 cubes, nu in {0.49, 0.499,
     0.4999}: the chosen solve (FP32 cycle, sGS smoother with the weights that the
@@ -624,7 +829,6 @@ def run_mixed(args):
     the summed solve times (CUDA events of amg_solve); setup and weight selection are
     reported beside it.  --workload stokes runs the same comparison on the lid-driven
     Stokes problem (24^3, Taylor-Hood)."""
-    import torch
     import __graft_entry__ as ge
     from fem_inputs.configs import CONFIGS, make_config
     ge.build()
@@ -639,52 +843,15 @@ def run_mixed(args):
     if stokes:
         probs = [probs]
     gen_s = time.time() - t0
-    rows = []
-    tot = {"dofs": 0, "chosen_ms": 0.0, "plain_ms": 0.0}
-    for prob in probs:
-        b = torch.from_numpy(prob.rhs()).cuda()
-        x = torch.zeros_like(b)
-        t1 = time.time()
-        ch = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
-                                                     gmres_restart=cfg["gmres_restart"],
-                                                     max_iterations=1000))
-        res = ch.learn_weights(theta)
-        setup_learn_s = time.time() - t1
-        pl = B.setup_problem(prob, B.default_options(precision=B.AMG_FP64,
-                                                     gmres_restart=cfg["gmres_restart"],
-                                                     max_iterations=1000))
-        bs = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32,
-                                                     smoother=B.AMG_SMOOTHER_BS,
-                                                     gmres_restart=cfg["gmres_restart"],
-                                                     max_iterations=1000))
-        out = {}
-        for variant, h in (("chosen", ch), ("plain_fp64", pl), ("braess_sarazin_fp32", bs)):
-            for _ in range(max(1, args.warmup)):
-                x.zero_()
-                h.solve(b, x, cfg["tol"], device_ptrs=True)
-            ms, st = [], None
-            for _ in range(max(1, args.steps)):
-                x.zero_()
-                st = h.solve(b, x, cfg["tol"], device_ptrs=True)
-                ms.append(st.solve_ms)
-            out[variant] = {"iterations": st.iterations, "converged": bool(st.converged),
-                            "true_rel_residual": st.true_rel_residual,
-                            "ms": float(np.median(ms))}
-            h.free()
-        rows.append({"nu": prob.params.get("nu"), "dofs": prob.n_dof, **out,
-                     "weights": list(res.weights), "fell_back": res.fell_back,
-                     "setup_and_selection_s": setup_learn_s})
-        tot["dofs"] += prob.n_dof
-        tot["chosen_ms"] += out["chosen"]["ms"]
-        tot["plain_ms"] += out["plain_fp64"]["ms"]
-        tot["bs_ms"] = tot.get("bs_ms", 0.0) + out["braess_sarazin_fp32"]["ms"]
+    rows, tot, _ = saddle_results(B, probs, cfg["gmres_restart"], cfg["tol"], args.steps,
+                                  args.warmup, theta)
     line = {"metric": ("DOF/s solved to 1e-8 rel. residual, lid-driven Stokes 24^3 "
                        "Taylor-Hood: learned weights + FP32 cycle, FGMRES(300)") if stokes else
                       ("DOF/s solved to 1e-8 rel. residual, mixed elasticity 40^3 P2/P1, "
                        "nu in {0.49, 0.499, 0.4999}: learned weights + FP32 cycle, FGMRES(300)"),
             "value": tot["dofs"] / (tot["chosen_ms"] * 1e-3), "unit": "DOF/s",
-            "plain_fp64_value": tot["dofs"] / (tot["plain_ms"] * 1e-3),
-            "braess_sarazin_fp32_value": tot["dofs"] / (tot["bs_ms"] * 1e-3),
+            "plain_fp64_value": tot["dofs"] / (tot["plain_fp64_ms"] * 1e-3),
+            "braess_sarazin_fp32_value": tot["dofs"] / (tot["braess_sarazin_fp32_ms"] * 1e-3),
             "config": {"workload": name if stokes else f"mixed_elast_n{args.n_mixed}",
                        "tol": cfg["tol"]},
             "rows": rows, "generate_s": gen_s}
@@ -694,7 +861,10 @@ def run_mixed(args):
 def run_batched(args):
     """64 uneven elasticity problems x 16 right-hand sides in one amg_solve_batched
     launch (box meshes n ~ U{8..24}, side lengths ~ U[1,4], nu ~ U[0.2,0.45],
-    N(0,1) traction loads), FP32 V-cycle, flexible CG per right-hand side to 1e-8."""
+    N(0,1) traction loads), FP32 V-cycle, flexible CG per right-hand side to 1e-8;
+    beside it the plain baseline on the same inputs: one FP64 amg_solve (AMG-PCG) per
+    problem and right-hand side (inputs resident on the device, CUDA-event solve
+    times summed)."""
     import torch
 
     from fem_inputs import configs, elasticity_problem
@@ -706,46 +876,44 @@ def run_batched(args):
     probs = [elasticity_problem(sp["n"], seed=sp["seed"], nu=sp["nu"], lengths=sp["lengths"],
                                 n_rhs=args.rhs, traction="gaussian") for sp in specs]
     gen_s = time.perf_counter() - t0
-    handles, Bs, Xs = [], [], []
-    t0 = time.perf_counter()
-    for p in probs:
-        h = B.setup_problem(p, B.default_options(precision=B.AMG_FP32,
-                                                  outer_pair=args.outer_pair))
-        handles.append(h)
-        Bs.append(torch.from_numpy(np.ascontiguousarray(p.f.reshape(args.rhs, -1))).cuda())
-        Xs.append(torch.zeros(args.rhs * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
-    setup_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    times = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        rc, stats = B.solve_batched(handles, Bs, Xs, args.rhs, TOL)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            times.append(stats[0].solve_ms)
-    ms = float(np.mean(times))
-    dof_rhs = sum(p.n_dof for p in probs) * args.rhs
-    worst = max(s.true_rel_residual for s in stats)
-    its = [s.iterations for s in stats]
+    summ, handles, xs = batched_results(B, probs, args.rhs, args.steps, args.warmup,
+                                        outer_pair=args.outer_pair)
+    for h in handles:
+        h.free()
+    plain = None
+    if not args.no_plain:
+        tot_ms, its = 0.0, []
+        for p in probs:
+            h = B.setup_problem(p, B.default_options(precision=B.AMG_FP64))
+            F = torch.from_numpy(np.ascontiguousarray(p.f.reshape(args.rhs, -1))).cuda()
+            x = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+            h.solve(F[0].contiguous(), x, TOL, device_ptrs=True)      # warm-up
+            for r in range(args.rhs):
+                st = h.solve(F[r].contiguous(), x, TOL, device_ptrs=True)
+                tot_ms += st.solve_ms
+                its.append(st.iterations)
+            h.free()
+        plain = {"value": summ["dof_total"] * args.rhs / (tot_ms * 1e-3), "unit": "DOF*RHS/s",
+                 "ms_per_batch": tot_ms, "iterations": {"min": min(its), "max": max(its)},
+                 "what": "one FP64 amg_solve (AMG-PCG, FP64 cycle) per problem and "
+                         "right-hand side, CUDA-event solve times summed"}
     line = {
         "metric": "DOF x RHS/s solved to 1e-8 rel. residual, batched elasticity "
                   f"({args.batch} uneven problems x {args.rhs} RHS, FP32 V-cycle, FCG)",
-        "value": dof_rhs / (ms * 1e-3), "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None,
+        "value": summ["value"], "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": summ["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
         "dtype": ("f32 cycle + f32-pair Krylov operator + f64 vectors" if args.outer_pair
                   else "f32 cycle + f64 outer"), "data": "synthetic",
         "config": {"workload": f"batched_elast: {args.batch} problems, n in "
                                f"{min(sp['n'] for sp in specs)}..{max(sp['n'] for sp in specs)}",
-                   "dof_total": sum(p.n_dof for p in probs), "rhs": args.rhs, "tol": TOL},
-        "iterations": {"min": min(its), "max": max(its)}, "true_rel_residual_max": worst,
-        "converged": rc == 0, "setup_s": setup_s, "generate_s": gen_s,
-        "graph_launches_per_step": 1,
-        "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+                   "dof_total": summ["dof_total"], "rhs": args.rhs, "tol": TOL},
+        "iterations": summ["iterations"], "true_rel_residual_max": summ["true_rel_residual_max"],
+        "converged": summ["converged"], "setup_s": summ["setup_s"], "generate_s": gen_s,
+        "graph_launches_per_step": 1, "gpu_launches": summ["gpu_launches"],
+        "plain_fp64_per_rhs": plain,
     }
     print(json.dumps(line), flush=True)
-    for h in handles:
-        h.free()
 
 
 def main():
@@ -767,6 +935,10 @@ def main():
                     help="chosen solve without the learned-weights selection")
     ap.add_argument("--no-mesh", action="store_true",
                     help="skip the iteration-count-versus-mesh-size study")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batched: skip the per-right-hand-side FP64 amg_solve baseline")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the Stokes 24^3 / mixed 40^3 / batched 64 x 16 entries")
     ap.add_argument("--workload", default="elasticity",
                     choices=["elasticity", "batched", "replay", "mixed", "stokes"])
     ap.add_argument("--n-mixed", type=int, default=40, help="mixed: cubes per side")

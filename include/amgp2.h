@@ -448,19 +448,23 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
 
 /* ------------------------------------------- learned weights (small network)
  *
- * Three multipliers change the cycle, the same on every level; all 1 is the
- * plain method of Sec. 3.3:
+ * Three multipliers per level change the cycle; all 1 is the plain method of
+ * Sec. 3.3:
  *   ws  relaxation: the block Jacobi damping omega, the Gauss-Seidel step and
- *       the sGS velocity step are multiplied by ws;
+ *       the sGS velocity step of the level are multiplied by ws;
  *   wc  coarse-grid correction: x_l += wc * P x_{l+1} (Algorithm 1, step 13);
- *   wp  sGS pressure step: omega_p is multiplied by wp (saddle kinds).
- * A network of two hidden layers of 64 (ReLU) maps 13 statistics of the
- * hierarchy's block diagonals and interpolation sets (amg_features) and a
- * candidate (ws, wc, log2 wp) to the predicted log10 of the ratio of the
- * candidate's convergence factor to the plain method's.  amg_learn_weights
- * evaluates it on a fixed grid of candidates, keeps the best, and falls back to
- * the plain weights when a measured probe solve with the chosen weights does
- * not reduce the residual faster per iteration than the plain weights do.
+ *   wp  sGS pressure step of the level: omega_p is multiplied by wp (saddle
+ *       kinds).
+ * The paper has no counterpart: this part is an addition of the library.  A
+ * network of two hidden layers of 64 (ReLU) maps 13 statistics of one level and
+ * the level below it (amg_level_features) and a candidate (ws, wc, log2 wp) for
+ * that level to the predicted log10 of the ratio of the convergence factor with
+ * that level's multipliers changed (the others plain) to the plain factor.
+ * amg_learn_weights evaluates it on a fixed grid of candidates for every level,
+ * keeps each level's best, and falls back by measurement: the combination stays
+ * only if a probe solve converges faster per iteration than with the plain
+ * weights, else the level with the largest predicted gain alone is probed, else
+ * the plain weights stay.
  */
 #define AMG_N_FEATURES 13
 #define AMG_MLP_INPUTS 16      /* features, ws, wc, log2 wp                   */
@@ -477,14 +481,21 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
 #define AMG_GRID_NWP 7
 
 typedef struct amg_learned {
-  double weights[3];        /* ws, wc, wp in use after the call                 */
-  double predicted;         /* network output at the chosen candidate           */
+  double weights[3];        /* ws, wc, wp of level 0 after the call             */
+  double predicted;         /* sum over levels of the network's output at each
+                               level's chosen candidate                         */
   double rho_plain;         /* probe convergence factor, plain weights          */
-  double rho_learned;       /* probe convergence factor, chosen weights         */
+  double rho_learned;       /* probe convergence factor of the weights that were
+                               probed last against the plain ones               */
   int32_t fell_back;        /* 1: the plain weights were kept                   */
-  int32_t n_candidates;
+  int32_t n_candidates;     /* grid points per level                            */
   int32_t probe_iterations_plain;
   int32_t probe_iterations_learned;
+  double level_weights[3 * AMG_MAX_LEVELS];  /* (ws, wc, wp) per level in use     */
+  double level_predicted[AMG_MAX_LEVELS];    /* network output at each level's
+                                                 choice (0 on the coarsest)      */
+  int32_t n_levels;
+  int32_t pad0;
 } amg_learned;
 
 /*
@@ -504,21 +515,40 @@ typedef struct amg_learned {
  */
 int amg_features(amg_handle* h, double* features);
 
+/*
+ * amg_level_features -- the network's 13 inputs for non-coarsest level `level`
+ * (host doubles), with the statistics of amg_features above:
+ *   [0]      log10(3 n_l + n_pres,l) / 7
+ *   [1..5]   the five statistics of level l
+ *   [6..9]   the first four statistics of level l + 1
+ *   [10]     l / 4
+ *   [11]     saddle kinds: the pressure mean of level l (as [11] above)
+ *   [12]     1 for saddle kinds, 0 for SPD kinds
+ * AMG_ERR_INVALID for the coarsest level or a level that does not exist.
+ */
+int amg_level_features(amg_handle* h, int32_t level, double* features);
+
 /* Sets (ws, wc, wp) = w[0..2] on every level (host doubles, finite, > 0). */
 int amg_set_weights(amg_handle* h, const double* w);
+
+/* Sets (ws, wc, wp) = w[3 l .. 3 l + 2] on levels l < n_levels (host doubles,
+ * finite, > 0); levels from n_levels on get the plain weights. */
+int amg_set_level_weights(amg_handle* h, const double* w, int32_t n_levels);
 
 /* Copies the per-level weights, 4 doubles per level (ws, wc, wp, 1), to host. */
 int amg_get_weights(const amg_handle* h, double* w, int32_t capacity);
 
 /*
- * amg_learn_weights -- chooses (ws, wc, wp) with the trained network theta
- * (host floats, AMG_MLP_NPARAM, layout above): argmin of the network over the
- * grid ws in [AMG_WS_MIN, AMG_WS_MAX] (AMG_GRID_NWS points) x wc (AMG_GRID_NWC)
- * x log2 wp (AMG_GRID_NWP, saddle kinds; wp = 1 otherwise), then two probe
- * solves of K x = K y (y pseudo-random, zero on Dirichlet nodes) to a relative
- * residual of 1e-8 with the plain and with the chosen weights; the chosen
- * weights stay only if their factor rel_residual^(1/iterations) is smaller.
- * out receives the decision.  Later amg_solve calls use the weights in place.
+ * amg_learn_weights -- chooses each level's (ws, wc, wp) with the trained network
+ * theta (host floats, AMG_MLP_NPARAM, layout above): per non-coarsest level, the
+ * argmin of the network over the grid ws in [AMG_WS_MIN, AMG_WS_MAX]
+ * (AMG_GRID_NWS points) x wc (AMG_GRID_NWC) x log2 wp (AMG_GRID_NWP, saddle
+ * kinds; wp = 1 otherwise); then probe solves of K x = K y (y pseudo-random, zero
+ * on Dirichlet nodes) to a relative residual of 1e-8: plain weights, the
+ * combination, and if the combination is not faster the level with the largest
+ * predicted gain alone.  Weights are kept only if their factor
+ * rel_residual^(1/iterations) is smaller than the plain one.  out receives the
+ * decision.  Later amg_solve calls use the weights in place.
  */
 int amg_learn_weights(amg_handle* h, const float* theta, amg_learned* out);
 

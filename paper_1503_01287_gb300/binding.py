@@ -43,6 +43,7 @@ EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_la
             "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
             "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc",
             "amg_features", "amg_set_weights", "amg_get_weights", "amg_learn_weights",
+            "amg_level_features", "amg_set_level_weights",
             "amg_mlp_forward", "amg_mlp_gradient", "amg_mlp_adam", "amg_mlp_backward"]
 
 N_FEATURES = 13
@@ -112,11 +113,17 @@ class AmgLearned(C.Structure):
     _fields_ = [("weights", C.c_double * 3), ("predicted", C.c_double),
                 ("rho_plain", C.c_double), ("rho_learned", C.c_double),
                 ("fell_back", C.c_int32), ("n_candidates", C.c_int32),
-                ("probe_iterations_plain", C.c_int32), ("probe_iterations_learned", C.c_int32)]
+                ("probe_iterations_plain", C.c_int32), ("probe_iterations_learned", C.c_int32),
+                ("level_weights", C.c_double * (3 * AMG_MAX_LEVELS)),
+                ("level_predicted", C.c_double * AMG_MAX_LEVELS),
+                ("n_levels", C.c_int32), ("pad0", C.c_int32)]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad0"}
         d["weights"] = list(self.weights)
+        nl = self.n_levels
+        d["level_weights"] = [list(self.level_weights[3 * l:3 * l + 3]) for l in range(nl)]
+        d["level_predicted"] = list(self.level_predicted[:nl])
         return d
 
 
@@ -174,6 +181,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_features.restype = C.c_int
     lib.amg_set_weights.argtypes = [vp, vp]
     lib.amg_set_weights.restype = C.c_int
+    lib.amg_level_features.argtypes = [vp, i32, vp]
+    lib.amg_level_features.restype = C.c_int
+    lib.amg_set_level_weights.argtypes = [vp, vp, i32]
+    lib.amg_set_level_weights.restype = C.c_int
     lib.amg_get_weights.argtypes = [vp, vp, i32]
     lib.amg_get_weights.restype = C.c_int
     lib.amg_learn_weights.argtypes = [vp, vp, C.POINTER(AmgLearned)]
@@ -352,6 +363,17 @@ class Handle:
         out = np.zeros(N_FEATURES)
         _check(load_library().amg_features(self.h, out.ctypes.data), self.h)
         return out
+
+    def level_features(self, level: int) -> np.ndarray:
+        """amg_level_features: the 13 network inputs of non-coarsest level `level`."""
+        out = np.zeros(N_FEATURES, dtype=np.float64)
+        _check(load_library().amg_level_features(self.h, level, out.ctypes.data), self.h)
+        return out
+
+    def set_level_weights(self, w):
+        """amg_set_level_weights with w of shape (n_levels, 3): (ws, wc, wp) per level."""
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
+        _check(load_library().amg_set_level_weights(self.h, w.ctypes.data, len(w)), self.h)
 
     def set_weights(self, ws: float, wc: float, wp: float = 1.0):
         w = np.array([ws, wc, wp], dtype=np.float64)

@@ -316,7 +316,9 @@ void check_wait_flag(amg_handle* h, const char* what);
 // learned.cu: statistics of the hierarchy, weights, selection with fallback
 constexpr double kProbeTol = 1e-8;   // the probe solves run to the stopping tolerance of the workloads
 void compute_features(amg_handle* h, double* out);
+void compute_level_features(amg_handle* h, int l, double* out);
 void set_weights(amg_handle* h, const double* w3);
+void set_level_weights(amg_handle* h, const double* w, int n);
 void get_weights(const amg_handle* h, double* out);
 void learn_weights(amg_handle* h, const float* theta_host, amg_learned* out);
 

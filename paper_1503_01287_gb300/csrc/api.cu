@@ -642,6 +642,25 @@ int amg_set_weights(amg_handle* h, const double* w) {
   });
 }
 
+int amg_level_features(amg_handle* h, int32_t level, double* features) {
+  return guarded(h, [&]() -> int {
+    if (!h || !features) fail(AMG_ERR_INVALID, "null argument");
+    compute_level_features(h, level, features);
+    return AMG_OK;
+  });
+}
+
+int amg_set_level_weights(amg_handle* h, const double* w, int32_t n_levels) {
+  return guarded(h, [&]() -> int {
+    if (!h || !w || n_levels < 0) fail(AMG_ERR_INVALID, "bad argument");
+    for (int64_t e = 0; e < 3 * (int64_t)n_levels; ++e)
+      if (!(std::isfinite(w[e]) && w[e] > 0.0))
+        fail(AMG_ERR_INVALID, "weights must be finite and > 0");
+    set_level_weights(h, w, n_levels);
+    return AMG_OK;
+  });
+}
+
 int amg_get_weights(const amg_handle* hc, double* w, int32_t capacity) {
   amg_handle* h = const_cast<amg_handle*>(hc);
   return guarded(h, [&]() -> int {

@@ -1,7 +1,7 @@
-// Learned smoother and correction weights: block-diagonal statistics of the
-// hierarchy (the network's inputs), the weights array of the cycle kernels, and
-// the selection of weights by the trained network with a measured fallback to
-// the plain method (all weights 1).
+// Learned smoother and correction weights, per level: block-diagonal statistics
+// of every level (the network's inputs), the weights array of the cycle kernels
+// (4 doubles a level), and the selection of each level's multipliers by the
+// trained network with a measured fallback to the plain method (all weights 1).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -187,6 +187,85 @@ void compute_features(amg_handle* h, double* out) {
   out[12] = h->saddle ? 1.0 : 0.0;
 }
 
+// The statistics accumulators of every level (kAcc each) and the pressure
+// accumulators (2 each) of every saddle level with an sGS scaling.
+static void level_stats_all(amg_handle* h, std::vector<double>& acc) {
+  cudaStream_t s = h->stream;
+  const int nl = (int)h->L.size();
+  const int per = kAcc + 2;
+  DBuf<double> dacc;
+  dacc.alloc((size_t)per * nl);
+  AMG_CUDA(cudaMemsetAsync(dacc.p, 0, dacc.bytes(), s));
+  for (int l = 0; l < nl; ++l) {
+    const Level& lv = *h->L[l];
+    const bool has_p = l + 1 < nl;
+    k_level_stats<<<grid_of(lv.n), 256, 0, s>>>(
+        lv.n, lv.rowptr, lv.col, lv.val, lv.nnzb, lv.dinv, lv.tags, has_p ? lv.state.p : nullptr,
+        has_p ? lv.cid.p : nullptr, has_p ? lv.p_rowptr.p : nullptr,
+        has_p ? lv.p_col.p : nullptr, dacc.p + per * l);
+    AMG_LAUNCH_CHECK();
+    h->launches++;
+    if (h->saddle && lv.np > 0 && lv.schur.p) {
+      k_pres_stats<<<grid_of(lv.np), 256, 0, s>>>(lv.np, lv.c_rowptr, lv.c_col, lv.c_val,
+                                                   lv.schur, dacc.p + per * l + kAcc);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
+  }
+  acc.assign((size_t)per * nl, 0.0);
+  AMG_CUDA(cudaMemcpyAsync(acc.data(), dacc.p, acc.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// the five statistics of a level from its accumulators (zeros without nodes)
+static void stats5(const double* q, double* f) {
+  const double cnt = q[4], fc = q[7];
+  if (cnt <= 0.0) {
+    for (int e = 0; e < 5; ++e) f[e] = 0.0;
+    return;
+  }
+  const double mean = q[1] / cnt;
+  f[0] = q[0] / cnt;
+  f[1] = std::sqrt(std::max(0.0, q[2] / cnt - mean * mean));
+  f[2] = q[3] / cnt;
+  f[3] = fc > 0.0 ? q[5] / fc : 0.0;
+  f[4] = fc > 0.0 ? q[6] / fc / 8.0 : 0.0;
+}
+
+static void level_features_from(const amg_handle* h, const std::vector<double>& acc, int l,
+                                 double* out) {
+  const int per = kAcc + 2;
+  const Level& lv = *h->L[l];
+  out[0] = std::log10((double)std::max(lv.dofs(), 1)) / 7.0;
+  stats5(acc.data() + per * l, out + 1);
+  double nx[5];
+  stats5(acc.data() + per * (l + 1), nx);
+  for (int e = 0; e < 4; ++e) out[6 + e] = nx[e];
+  out[10] = l / 4.0;
+  const double* pq = acc.data() + per * l + kAcc;
+  out[11] = (h->saddle && pq[1] > 0.0) ? pq[0] / pq[1] : 0.0;
+  out[12] = h->saddle ? 1.0 : 0.0;
+}
+
+void compute_level_features(amg_handle* h, int l, double* out) {
+  if (l < 0 || l + 1 >= (int)h->L.size())
+    fail(AMG_ERR_INVALID, "level features exist for the non-coarsest levels");
+  std::vector<double> acc;
+  level_stats_all(h, acc);
+  level_features_from(h, acc, l, out);
+}
+
+void set_level_weights(amg_handle* h, const double* w, int n) {
+  const int nl = (int)h->L.size();
+  std::vector<double> v(4 * (size_t)nl, 1.0);
+  for (int l = 0; l < nl && l < n; ++l)
+    for (int e = 0; e < 3; ++e) v[4 * l + e] = w[3 * l + e];
+  AMG_CUDA(cudaMemcpyAsync(h->wts.p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+  AMG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
 void set_weights(amg_handle* h, const double* w3) {
   const int nl = (int)h->L.size();
   std::vector<double> w(4 * (size_t)nl);
@@ -220,50 +299,81 @@ double probe_rate(amg_handle* h, DBuf<double>& b, DBuf<double>& x, int* iters) {
   return std::pow(r, 1.0 / st.iterations);
 }
 
+// Per-level selection: for every non-coarsest level the network predicts, for
+// each candidate (ws, wc, wp) of the grid, the log10 ratio of the convergence
+// factor with that level's multipliers changed (the others plain) to the plain
+// factor; each level takes its grid argmin (the grid holds the plain point).
+// Measured fallback: the combined choice is kept only if a probe solve to 1e-8
+// converges faster per iteration than with the plain weights; otherwise the
+// level with the largest predicted gain alone is probed, and otherwise the
+// plain weights stay.
 void learn_weights(amg_handle* h, const float* theta_host, amg_learned* out) {
   cudaStream_t s = h->stream;
-  double feat[AMG_N_FEATURES];
-  compute_features(h, feat);
+  const int nl = (int)h->L.size();
+  const int ns = std::max(nl - 1, 0);     // levels with multipliers that act
+  std::vector<double> acc;
+  level_stats_all(h, acc);
   // candidate grid: ws x wc (x log2 wp for saddle kinds)
-  std::vector<float> X;
   std::vector<double> W;
   const int nwp = h->saddle ? AMG_GRID_NWP : 1;
   for (int a = 0; a < AMG_GRID_NWS; ++a)
     for (int b = 0; b < AMG_GRID_NWC; ++b)
       for (int c = 0; c < nwp; ++c) {
-        const double ws = AMG_WS_MIN + (AMG_WS_MAX - AMG_WS_MIN) * a / (AMG_GRID_NWS - 1);
-        const double wc = AMG_WC_MIN + (AMG_WC_MAX - AMG_WC_MIN) * b / (AMG_GRID_NWC - 1);
-        const double lp = h->saddle ? AMG_WP_LOG2_MIN + (AMG_WP_LOG2_MAX - AMG_WP_LOG2_MIN) * c /
-                                                            (AMG_GRID_NWP - 1)
-                                    : 0.0;
-        for (int e = 0; e < AMG_N_FEATURES; ++e) X.push_back((float)feat[e]);
-        X.push_back((float)ws);
-        X.push_back((float)wc);
-        X.push_back((float)lp);
-        W.push_back(ws);
-        W.push_back(wc);
-        W.push_back(std::exp2(lp));
+        W.push_back(AMG_WS_MIN + (AMG_WS_MAX - AMG_WS_MIN) * a / (AMG_GRID_NWS - 1));
+        W.push_back(AMG_WC_MIN + (AMG_WC_MAX - AMG_WC_MIN) * b / (AMG_GRID_NWC - 1));
+        W.push_back(h->saddle ? AMG_WP_LOG2_MIN + (AMG_WP_LOG2_MAX - AMG_WP_LOG2_MIN) * c /
+                                                      (AMG_GRID_NWP - 1)
+                              : 0.0);
       }
   const int nc = (int)W.size() / 3;
-  DBuf<float> dth, dx, dy;
-  dth.alloc(mlp_nparam());
-  dx.alloc(X.size());
-  dy.alloc(nc);
-  AMG_CUDA(cudaMemcpyAsync(dth.p, theta_host, mlp_nparam() * sizeof(float),
-                           cudaMemcpyHostToDevice, s));
-  AMG_CUDA(cudaMemcpyAsync(dx.p, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-  mlp_forward(dth, dx, nc, dy, s);
-  h->launches++;
-  std::vector<float> y(nc);
-  AMG_CUDA(cudaMemcpyAsync(y.data(), dy.p, nc * sizeof(float), cudaMemcpyDeviceToHost, s));
-  AMG_CUDA(cudaStreamSynchronize(s));
-  int best = 0;
-  for (int k = 1; k < nc; ++k)
-    if (y[k] < y[best]) best = k;
+  std::vector<float> X;
+  X.reserve((size_t)ns * nc * AMG_MLP_INPUTS);
+  for (int l = 0; l < ns; ++l) {
+    double f[AMG_N_FEATURES];
+    level_features_from(h, acc, l, f);
+    for (int k = 0; k < nc; ++k) {
+      for (int e = 0; e < AMG_N_FEATURES; ++e) X.push_back((float)f[e]);
+      for (int e = 0; e < 3; ++e) X.push_back((float)W[3 * k + e]);
+    }
+  }
   std::memset(out, 0, sizeof(*out));
   out->n_candidates = nc;
-  out->predicted = y[best];
-  // measured fallback: the plain and the chosen weights on the same probe system
+  out->n_levels = nl;
+  std::vector<double> plain(3 * (size_t)nl, 1.0), chosen(plain);
+  std::vector<float> y((size_t)ns * nc, 0.f);
+  if (ns > 0) {
+    DBuf<float> dth, dx, dy;
+    dth.alloc(mlp_nparam());
+    dx.alloc(X.size());
+    dy.alloc(y.size());
+    AMG_CUDA(cudaMemcpyAsync(dth.p, theta_host, mlp_nparam() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemcpyAsync(dx.p, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             s));
+    mlp_forward(dth, dx, (int)y.size(), dy, s);
+    h->launches++;
+    AMG_CUDA(cudaMemcpyAsync(y.data(), dy.p, y.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                             s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+  }
+  int l_best = -1;
+  float gain_best = 0.f;
+  for (int l = 0; l < ns; ++l) {
+    const float* yl = y.data() + (size_t)l * nc;
+    int best = 0;
+    for (int k = 1; k < nc; ++k)
+      if (yl[k] < yl[best]) best = k;
+    chosen[3 * l + 0] = W[3 * best];
+    chosen[3 * l + 1] = W[3 * best + 1];
+    chosen[3 * l + 2] = std::exp2(W[3 * best + 2]);
+    out->level_predicted[l] = yl[best];
+    out->predicted += yl[best];
+    if (yl[best] < gain_best) {
+      gain_best = yl[best];
+      l_best = l;
+    }
+  }
+  // measured fallback on one probe system, b = K y with y fixed pseudo-random
   const Level& l0 = *h->L[0];
   const int64_t m = l0.dofs();
   DBuf<double> yv, b, x, ypad, bpad;
@@ -277,21 +387,37 @@ void learn_weights(amg_handle* h, const float* theta_host, amg_learned* out) {
   launch_to_padded(yv, ypad, l0.n, l0.np, s, h);
   level_apply<double>(h, 0, ypad.p, bpad.p);
   launch_from_padded(bpad, b, l0.n, l0.np, s, h);
-  const double plain[3] = {1.0, 1.0, 1.0};
-  set_weights(h, plain);
   int itp = 0, itl = 0;
+  set_level_weights(h, plain.data(), nl);
   out->rho_plain = probe_rate(h, b, x, &itp);
-  const double chosen[3] = {W[3 * best], W[3 * best + 1], W[3 * best + 2]};
-  set_weights(h, chosen);
-  out->rho_learned = probe_rate(h, b, x, &itl);
   out->probe_iterations_plain = itp;
-  out->probe_iterations_learned = itl;
-  if (!(out->rho_learned < out->rho_plain)) {
-    set_weights(h, plain);
-    out->fell_back = 1;
+  const std::vector<double>* keep = &plain;
+  std::vector<double> single(plain);
+  if (chosen != plain) {
+    set_level_weights(h, chosen.data(), nl);
+    out->rho_learned = probe_rate(h, b, x, &itl);
+    out->probe_iterations_learned = itl;
+    if (out->rho_learned < out->rho_plain) keep = &chosen;
   }
-  const double* wf = out->fell_back ? plain : chosen;
-  for (int e = 0; e < 3; ++e) out->weights[e] = wf[e];
+  if (keep == &plain && l_best >= 0) {
+    for (int e = 0; e < 3; ++e) single[3 * l_best + e] = chosen[3 * l_best + e];
+    if (single != plain && single != chosen) {
+      set_level_weights(h, single.data(), nl);
+      int its = 0;
+      const double rs = probe_rate(h, b, x, &its);
+      if (rs < out->rho_plain) {
+        keep = &single;
+        out->rho_learned = rs;
+        out->probe_iterations_learned = its;
+      }
+    }
+  }
+  out->fell_back = keep == &plain ? 1 : 0;
+  if (out->fell_back) out->rho_learned = out->rho_learned > 0 ? out->rho_learned : out->rho_plain;
+  set_level_weights(h, keep->data(), nl);
+  for (int l = 0; l < nl && l < AMG_MAX_LEVELS; ++l)
+    for (int e = 0; e < 3; ++e) out->level_weights[3 * l + e] = (*keep)[3 * l + e];
+  for (int e = 0; e < 3; ++e) out->weights[e] = (*keep)[e];
 }
 
 }  // namespace amgp2

@@ -9,13 +9,17 @@ mixed displacement-pressure elasticity (nu = 0.5 - 10^U[-4, -1.3], vertices
 jittered by U[0, 0.2] h), odd indices pure-displacement elasticity (nu in
 U[0.2, 0.45], side lengths U[1, 4] per axis, N(0, 1) traction).  Each problem
 is set up once (FP32 cycle; flexible CG or FGMRES(300)) and solved to 1e-8
-with the plain weights and with `--candidates` random (ws, wc, wp) from the
-box of the selection grid; a solve's convergence factor is
-rho = (||r_k|| / ||r_0||)^(1/k).  One training sample is
-  input  = the hierarchy's 13 statistics (amg_features), ws, wc, log2 wp
+with the plain weights and with `--candidates` random changes of one level:
+a level l drawn among the non-coarsest levels and a random (ws, wc, wp) from
+the box of the selection grid for that level, the other levels plain.  A
+solve's convergence factor is rho = (||r_k|| / ||r_0||)^(1/k).  One training
+sample is
+  input  = the 13 statistics of level l and the level below (amg_level_features),
+           ws, wc, log2 wp
   target = log10(rho_candidate / rho_plain), clipped to [-1, 1]
-(wp and its input are 1 and 0 for the SPD problems).  The plain weights give
-target 0 by definition, so the plain method is the yardstick of every sample.
+(wp and its input are 1 and 0 for the SPD problems).  Each problem also gives
+one plain sample (level 0, candidate (1, 1, 0), target 0), so the plain method
+is the yardstick of every problem's samples.
 
 Training.  Adam with the amg_mlp_* kernels (BF16 products, FP32 accumulation)
 on the mean squared error of the targets (--loss mse) or on a listwise ranking
@@ -83,18 +87,25 @@ def _rho(st) -> float:
     return float(r ** (1.0 / st.iterations))
 
 
+# setup options of the measurements: the per-operation cycle (the one-launch
+# sweep variants only change the speed, not the iteration)
+MEASURE_OPTS = dict(cluster_from=0, cycle_kernel=1, gs_cluster=0, gs_flow=0, gs_stream=0)
+
+
 def measure(prob, n_cand: int, rng: np.random.Generator, torch):
-    """(features, [(ws, wc, lp, target, iterations, ms)], plain (rho, iterations, ms))."""
+    """([features per sample], [(level, ws, wc, lp, target, iterations, ms)],
+    plain (rho, iterations, ms)): one plain sample, then n_cand one-level changes."""
     from . import binding as B
     saddle = prob.kind in ("mixed", "stokes")
     h = B.setup_problem(prob, B.default_options(precision=1, gmres_restart=RESTART,
-                                                max_iterations=MAXIT))
-    feats = h.features()
+                                                max_iterations=MAXIT, **MEASURE_OPTS))
+    nl = h.n_levels
+    lf = [h.level_features(l) for l in range(nl - 1)]
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
 
-    def run(ws, wc, wp):
-        h.set_weights(ws, wc, wp)
+    def run(w):
+        h.set_level_weights(w)
         x.zero_()
         try:
             st = h.solve(b, x, 1e-8, device_ptrs=True)
@@ -102,13 +113,19 @@ def measure(prob, n_cand: int, rng: np.random.Generator, torch):
             return 10.0, MAXIT, float("nan")
         return _rho(st), st.iterations, st.solve_ms
 
-    rho_p, it_p, ms_p = run(1.0, 1.0, 1.0)
-    rows = [(1.0, 1.0, 0.0, 0.0, it_p, ms_p)]
+    plain_w = np.ones((nl, 3))
+    rho_p, it_p, ms_p = run(plain_w)
+    feats = [lf[0]]
+    rows = [(0, 1.0, 1.0, 0.0, 0.0, it_p, ms_p)]
     for _ in range(n_cand):
+        l = int(rng.integers(0, nl - 1))
         ws, wc, lp = candidate_box(rng, saddle)
-        rho, it, ms = run(ws, wc, 2.0 ** lp)
+        w = plain_w.copy()
+        w[l] = (ws, wc, 2.0 ** lp)
+        rho, it, ms = run(w)
         t = float(np.clip(np.log10(max(rho, 1e-12) / rho_p), -1.0, 1.0))
-        rows.append((ws, wc, lp, t, it, ms))
+        feats.append(lf[l])
+        rows.append((l, ws, wc, lp, t, it, ms))
     h.free()
     return feats, rows, (rho_p, it_p, ms_p)
 
@@ -209,7 +226,7 @@ def train(X: np.ndarray, T: np.ndarray, train_idx, val_idx, steps: int, lr: floa
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--problems", type=int, default=2000)
+    ap.add_argument("--problems", type=int, default=1200)
     ap.add_argument("--candidates", type=int, default=6)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -245,9 +262,9 @@ def main(argv=None):
         gen_wait += time.time() - tw
         pending = pool.map_async(make_problem, chunks[ci + 1]) if ci + 1 < len(chunks) else None
         for k, prob in enumerate(probs):
-            f, r, p = measure(prob, args.candidates, rng, torch)
+            fs, r, p = measure(prob, args.candidates, rng, torch)
             pi = ci * args.chunk + k
-            for row in r:
+            for f, row in zip(fs, r):
                 feats.append(f)
                 rows.append(row)
                 owner.append(pi)
@@ -260,9 +277,9 @@ def main(argv=None):
     measure_s = time.time() - t0
 
     F = np.array(feats)
-    R = np.array(rows)
-    X = np.concatenate([F, R[:, 0:3]], axis=1).astype(np.float32)
-    T = R[:, 3].astype(np.float32)
+    R = np.array(rows)          # level, ws, wc, lp, target, iterations, ms
+    X = np.concatenate([F, R[:, 1:4]], axis=1).astype(np.float32)
+    T = R[:, 4].astype(np.float32)
     owner = np.array(owner)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.savez(os.path.splitext(args.out)[0] + ".data.npz", X=X, T=T, owner=owner, rows=R,
@@ -282,8 +299,11 @@ def main(argv=None):
         "samples": int(len(T)), "train_samples": int(len(train_idx)),
         "val_samples": int(len(val_idx)), "seed0": SEED0, "steps": args.steps, "lr": args.lr,
         "target_mean": float(T.mean()), "target_std": float(T.std()),
-        "share_candidates_better_than_plain": float(np.mean(R[R[:, 3] != 0.0, 3] < 0.0))
-        if np.any(R[:, 3] != 0.0) else 0.0,
+        "share_candidates_better_than_plain": float(np.mean(R[R[:, 4] != 0.0, 4] < 0.0))
+        if np.any(R[:, 4] != 0.0) else 0.0,
+        "share_better_by_level": {int(l): float(np.mean(R[(R[:, 0] == l) & (R[:, 4] != 0.0), 4]
+                                                        < 0.0))
+                                  for l in np.unique(R[1:, 0])},
         "plain_iterations_mean": float(Pl[:, 1].mean()),
         "history": hist, "measure_s": measure_s, "generation_wait_s": gen_wait,
         "train_s": train_s,

@@ -183,6 +183,43 @@ def test_features_match_oracle(kind):
     h.free()
 
 
+@pytest.mark.parametrize("kind", sorted(PROBLEMS))
+def test_level_features_match_oracle(kind):
+    prob, saddle = PROBLEMS[kind]()
+    h = B().setup_problem(prob, B().default_options())
+    oh = amg.build_hierarchy(prob)
+    assert h.n_levels == len(oh.levels)
+    for l in range(h.n_levels - 1):
+        got = h.level_features(l)
+        want = features.level_features(oh, l, saddle)
+        assert np.abs(got - want).max() <= 1e-10, (l, got, want)
+    with pytest.raises(B().AmgError):
+        h.level_features(h.n_levels - 1)
+    h.free()
+
+
+@pytest.mark.parametrize("kind", ["elasticity", "mixed"])
+def test_level_weighted_preconditioner_matches_oracle(kind):
+    """Different (ws, wc, wp) on every level: one preconditioner application against
+    the oracle's per-level multipliers."""
+    prob, saddle = PROBLEMS[kind]()
+    h = B().setup_problem(prob, B().default_options())
+    nl = h.n_levels
+    rng = np.random.default_rng(9)
+    w = np.column_stack([rng.uniform(0.7, 1.4, nl), rng.uniform(0.8, 1.6, nl),
+                         rng.uniform(0.6, 2.0, nl) if saddle else np.ones(nl)])
+    h.set_level_weights(w)
+    assert np.array_equal(h.weights()[:, :3], w)
+    o = amg.Options(smoother="sgs" if saddle else "gs", level_weights=[tuple(r) for r in w])
+    oh = amg.build_hierarchy(prob, o)
+    r = rng.standard_normal(prob.n_dof)
+    z = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    h.apply_preconditioner(torch.from_numpy(r).cuda(), z)
+    want = amg.precondition(oh, r)
+    assert np.linalg.norm(z.cpu().numpy() - want) <= 1e-10 * np.linalg.norm(want)
+    h.free()
+
+
 @pytest.mark.parametrize("kind,w", [("elasticity", (1.2, 1.4, 1.0)),
                                     ("laplace", (0.7, 1.8, 1.0)),
                                     ("mixed", (0.8, 1.3, 2.0))])
@@ -212,22 +249,41 @@ def _linear_in_ws(c):
     return mlp.pack(p).astype(np.float32)
 
 
-@pytest.mark.parametrize("kind", ["elasticity", "mixed"])
-def test_learn_weights_decision_and_fallback(kind):
+@pytest.mark.parametrize("kind,c", [("elasticity", 1.0), ("mixed", 1.0), ("elasticity", -1.0)])
+def test_learn_weights_decision_and_fallback(kind, c):
+    """A hand-built network c * ws: every level's argmin is the grid's smallest ws
+    (c > 0, no predicted gain) or largest ws (c < 0, predicted gain), first wc and
+    wp on ties.  The combination is probed against plain; with a predicted gain and
+    a combination that is not faster, the level with the largest gain (level 0:
+    equal outputs) is probed alone.  What stays must be what was measured faster."""
     prob, saddle = PROBLEMS[kind]()
     h = B().setup_problem(prob, B().default_options(precision=1))
-    res = h.learn_weights(_linear_in_ws(1.0))
+    nl = h.n_levels
+    res = h.learn_weights(_linear_in_ws(c))
     Bm = B()
+    assert res.n_levels == nl
     assert res.n_candidates == Bm.GRID[0] * Bm.GRID[1] * (Bm.GRID[2] if saddle else 1)
-    assert abs(res.predicted - bf16(Bm.WS_RANGE[0])) <= 1e-6    # the input is multiplied in BF16
-    chosen = [Bm.WS_RANGE[0], Bm.WC_RANGE[0], 2.0 ** Bm.WP_LOG2_RANGE[0] if saddle else 1.0]
-    assert 0.0 < res.rho_plain < 1.0 and res.rho_learned > 0.0
-    fell = res.rho_learned >= res.rho_plain
-    assert res.fell_back == int(fell)
-    want = [1.0, 1.0, 1.0] if fell else chosen
-    assert np.allclose(list(res.weights), want, rtol=0, atol=1e-12)
-    assert np.allclose(h.weights()[:, :3], np.tile(want, (h.n_levels, 1)), rtol=0, atol=1e-12)
-    # solves use the weights in place; plain weights give the plain iteration count
+    ws = Bm.WS_RANGE[0] if c > 0 else Bm.WS_RANGE[1]
+    chosen = [ws, Bm.WC_RANGE[0], 2.0 ** Bm.WP_LOG2_RANGE[0] if saddle else 1.0]
+    # each non-coarsest level predicts c * ws (the input is multiplied in BF16)
+    lp = list(res.level_predicted)[:nl]
+    assert all(abs(v - c * bf16(ws)) <= 1e-6 for v in lp[:nl - 1]) and lp[nl - 1] == 0.0
+    assert abs(res.predicted - (nl - 1) * c * bf16(ws)) <= 1e-5
+    assert 0.0 < res.rho_plain < 1.0
+    kept = np.array(list(res.level_weights)[:3 * nl]).reshape(nl, 3)
+    assert np.array_equal(kept, h.weights()[:, :3])
+    plain = np.ones((nl, 3))
+    combo = np.tile(chosen, (nl, 1))
+    combo[nl - 1] = 1.0                       # the coarsest level keeps the plain row
+    single = plain.copy()
+    single[0] = chosen
+    if res.fell_back:
+        assert np.array_equal(kept, plain)
+    else:
+        assert res.rho_learned < res.rho_plain
+        assert np.allclose(kept, combo, atol=1e-12) or (c < 0 and np.allclose(kept, single,
+                                                                               atol=1e-12))
+    assert np.allclose(list(res.weights), kept[0], atol=1e-12)
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
     st = h.solve(b, x, 1e-8, device_ptrs=True)
@@ -241,9 +297,12 @@ WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), ".
 
 def test_trained_network_gain_over_plain():
     """Held-out problems of the training distribution (seeds outside the training
-    range): the plain solve and the solve with the weights amg_learn_weights picks
-    with the trained network.  The measured fallback may cost at most a couple of
-    iterations against plain on any problem; the gain is what remains."""
+    range): the plain solve and the solve with the per-level weights
+    amg_learn_weights picks with the trained network.  Measured with the committed
+    network: 459 plain against 423 learned iterations in total (7.8 % fewer), the
+    choice kept on all 8 problems, none slower.  Asserted: at least 5 % fewer
+    iterations in total, the choice kept on at least half of the problems, and no
+    problem more than one iteration slower than plain."""
     import os
     if not os.path.exists(WEIGHTS):
         pytest.skip("no trained network in the package")
@@ -269,5 +328,6 @@ def test_trained_network_gain_over_plain():
     for r in rows:
         print(*r)
     for kind, ip, il, _, _ in rows:
-        assert il <= ip + 2, (kind, ip, il)
-    assert sum(r[2] for r in rows) <= sum(r[1] for r in rows)
+        assert il <= ip + 1, (kind, ip, il)
+    assert sum(r[2] for r in rows) <= 0.95 * sum(r[1] for r in rows)
+    assert sum(1 for r in rows if not r[3]) >= len(rows) // 2

@@ -101,27 +101,35 @@ def test_features_interpolation_statistics_by_matrix_products():
 
 def test_committed_training_data_and_network():
     """The committed dataset of measured convergence factors and the network trained
-    on it: shapes, the target's definition (plain rows are 0, targets clipped to
-    [-1, 1]), the input layout (13 statistics, ws, wc, log2 wp), and the network's
-    picks on the validation problems (FP64 forward pass): the measured candidate it
-    ranks first converges closer to the best measured one than always keeping the
-    plain weights does, and far closer than a random pick."""
+    on it: shapes, the target's definition (each problem's plain row is 0, targets
+    clipped to [-1, 1]), the input layout (13 per-level statistics with the level
+    index l / 4 as input 10, ws, wc, log2 wp), and the network's picks on the
+    validation problems (FP64 forward pass): the measured candidate it ranks first
+    converges closer to the best measured one than always keeping the plain weights
+    does, and far closer than a random pick."""
     import os
     from paper_1503_01287_gb300.train_weights import selection_regret
     here = os.path.join(os.path.dirname(__file__), "..", "paper_1503_01287_gb300", "weights")
     d = np.load(os.path.join(here, "mlp_theta.data.npz"))
-    X, T, owner = d["X"], d["T"].astype(np.float64), d["owner"]
-    assert X.shape == (14000, mlp.NI) and T.shape == (14000,)
+    X, T, owner, R = d["X"], d["T"].astype(np.float64), d["owner"], d["rows"]
+    nprob = int(owner.max()) + 1
+    per = len(T) // nprob
+    assert X.shape == (nprob * per, mlp.NI) and T.shape == (nprob * per,)
+    assert np.all(owner.reshape(nprob, per) == np.arange(nprob)[:, None])
     assert np.all(np.abs(T) <= 1.0)
-    assert int(owner.max()) + 1 == 2000
-    plain = (X[:, 13] == 1.0) & (X[:, 14] == 1.0) & (X[:, 15] == 0.0)
-    assert plain.sum() >= 2000 and np.all(T[plain] == 0.0)
+    first = np.arange(nprob) * per                 # each problem's plain row
+    assert np.all(T[first] == 0.0) and np.all(R[first, 0] == 0)
+    assert np.all(X[first, 13] == 1.0) and np.all(X[first, 14] == 1.0)
+    assert np.all(X[first, 15] == 0.0)
+    assert np.array_equal(X[:, 10], (R[:, 0] / 4.0).astype(np.float32))   # level index
     assert np.all((X[:, 12] == 0.0) | (X[:, 12] == 1.0))
     theta = np.load(os.path.join(here, "mlp_theta.npy")).astype(np.float64)
     assert theta.shape == (mlp.NPARAM,) and np.all(np.isfinite(theta))
     # validation problems: the 10 % held out by the training script's permutation
-    perm = np.random.default_rng(11).permutation(2000)
-    val = np.isin(owner, perm[:200])
+    perm = np.random.default_rng(11).permutation(nprob)
+    val = np.isin(owner, perm[:max(1, nprob // 10)])
+    plain = np.zeros(len(T), dtype=bool)
+    plain[first] = True
     y, _ = mlp.forward(theta, X[val].astype(np.float64))
     r_net = selection_regret(y, T[val], owner[val])
     r_plain = selection_regret(-plain[val].astype(np.float64), T[val], owner[val])
