@@ -416,10 +416,19 @@ int amg_apply_preconditioner_noalloc(amg_handle* h, const double* r, double* z);
 int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const double* x,
                     double* y);
 
-/* One smoothing sweep of level `level` on device vectors x (in/out) and b:
- * direction 0 = pre-smoothing order, 1 = post-smoothing order. */
+/* One smoothing sweep of level `level` (Sec. 3.3) on device vectors x (in/out)
+ * and b of 3*n_nodes + n_pres doubles, in FP64: direction 0 = colours (or Vanka
+ * patch colours) ascending, 1 = descending.  Synchronises the stream; returns
+ * AMG_ERR_TIMEOUT if a bounded device wait gave up. */
 int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
                      const double* b);
+
+/* The same sweep in `precision`: AMG_FP64 as amg_level_smooth, or AMG_FP32 on a
+ * handle set up with precision AMG_FP32: x and b are rounded to float and the
+ * sweep runs the FP32 cycle's kernels and launch variants (the ones its solves
+ * time) on the level's FP32 values; x is returned widened to double. */
+int amg_level_smooth_precision(amg_handle* h, int32_t level, int32_t direction,
+                               int32_t precision, double* x, const double* b);
 
 /* ------------------------------------------------------------ measurement */
 

@@ -40,7 +40,8 @@ KINDS = {"laplace": AMG_VECTOR_LAPLACE, "elasticity": AMG_ELASTICITY,
 
 EXPORTED = ["amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
             "amg_level_info_get", "amg_level_copy", "amg_apply_preconditioner",
-            "amg_level_apply", "amg_level_smooth", "amg_set_pressure_weights",
+            "amg_level_apply", "amg_level_smooth", "amg_level_smooth_precision",
+            "amg_set_pressure_weights",
             "amg_time_level_op", "amg_solve_batched", "amg_apply_preconditioner_noalloc",
             "amg_features", "amg_set_weights", "amg_get_weights", "amg_learn_weights",
             "amg_level_features", "amg_set_level_weights",
@@ -167,6 +168,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.amg_level_apply.restype = C.c_int
     lib.amg_level_smooth.argtypes = [vp, i32, i32, vp, vp]
     lib.amg_level_smooth.restype = C.c_int
+    lib.amg_level_smooth_precision.argtypes = [vp, i32, i32, i32, vp, vp]
+    lib.amg_level_smooth_precision.restype = C.c_int
     lib.amg_set_pressure_weights.argtypes = [vp, vp, i32]
     lib.amg_set_pressure_weights.restype = C.c_int
     lib.amg_time_level_op.argtypes = [vp, i32, i32, i32, i32, i32, C.POINTER(dbl),
@@ -354,9 +357,15 @@ class Handle:
                                                 C.byref(ms), C.byref(nl)), self.h)
         return ms.value, nl.value
 
-    def level_smooth(self, level: int, x_dev, b_dev, post: bool = False):
-        _check(load_library().amg_level_smooth(self.h, level, 1 if post else 0, _ptr(x_dev),
-                                               _ptr(b_dev)), self.h)
+    def level_smooth(self, level: int, x_dev, b_dev, post: bool = False,
+                     precision: int | None = None):
+        """One sweep (post: colours descending); precision None/AMG_FP64 or AMG_FP32."""
+        if precision is None:
+            _check(load_library().amg_level_smooth(self.h, level, 1 if post else 0,
+                                                   _ptr(x_dev), _ptr(b_dev)), self.h)
+        else:
+            _check(load_library().amg_level_smooth_precision(
+                self.h, level, 1 if post else 0, precision, _ptr(x_dev), _ptr(b_dev)), self.h)
 
     def features(self) -> np.ndarray:
         """The 13 statistics of the hierarchy that the weight network reads."""

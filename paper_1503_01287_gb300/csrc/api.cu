@@ -531,6 +531,31 @@ int amg_level_smooth(amg_handle* h, int32_t level, int32_t direction, double* x,
   });
 }
 
+int amg_level_smooth_precision(amg_handle* h, int32_t level, int32_t direction,
+                               int32_t precision, double* x, const double* b) {
+  if (precision == AMG_FP64) return amg_level_smooth(h, level, direction, x, b);
+  return guarded(h, [&]() -> int {
+    if (!h || !x || !b) fail(AMG_ERR_INVALID, "null argument");
+    if (precision != AMG_FP32) fail(AMG_ERR_INVALID, "precision must be AMG_FP64 or AMG_FP32");
+    if (level < 0 || level >= (int)h->L.size() - 1)
+      fail(AMG_ERR_INVALID, "no smoother on this level");
+    Level& lv = *h->L[level];
+    if (!lv.val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with precision FP32");
+    const int64_t n4 = lv.dofs4();
+    launch_to_padded(x, lv.x64, lv.n, lv.np, h->stream, h);
+    launch_to_padded(b, lv.b64, lv.n, lv.np, h->stream, h);
+    launch_to_float(lv.x64, lv.x32, n4, h->stream, h);
+    launch_to_float(lv.b64, lv.b32, n4, h->stream, h);
+    level_smooth<float>(h, level, lv.x32.p, lv.b32.p, direction != 0, false);
+    launch_to_double(lv.x32, lv.x64, n4, h->stream, h);
+    launch_from_padded(lv.x64, x, lv.n, lv.np, h->stream, h);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    check_wait_flag(h, "the smoothing sweep");
+    return AMG_OK;
+  });
+}
+
 int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precision, int32_t reps,
                       int32_t warmup, double* ms_per_rep, int32_t* launches_per_rep) {
   return guarded(h, [&]() -> int {

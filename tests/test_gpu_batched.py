@@ -120,3 +120,45 @@ def test_batched_matches_oracle_per_rhs(precision):
             e_or = np.linalg.norm(ref.x - conv.x)
             e_gpu = np.linalg.norm(x[j] - conv.x)
             assert e_gpu <= 2 * e_or + 1e-12 * np.linalg.norm(conv.x), (p.name, j, e_gpu, e_or)
+
+
+@pytest.mark.slow
+def test_batched_workload_sample_matches_oracle():
+    """Problems of the 64 x 16 batched workload at their full sizes: problem 20
+    (24^3 cubes, 1.5e5 nodes) and problem 11 (10^3 cubes, aspect ratio 3.3, the
+    slowest to converge), each with its 16 Gaussian traction loads, in one batched
+    FP32-cycle solve.  Every right-hand side's FP64 residual is recomputed; right-
+    hand sides of both problems are compared with the oracle's flexible CG, by the
+    criterion of the small-problem test (error against the converged solution at
+    most twice the oracle's own error at 1e-8)."""
+    from fem_inputs import configs
+    from oracle import amg
+    specs = configs.batched_specs(64, seed=4)
+    picks = [20, 11]
+    probs = [fp.elasticity_problem(specs[i]["n"], seed=specs[i]["seed"], nu=specs[i]["nu"],
+                                   lengths=specs[i]["lengths"], n_rhs=16, traction="gaussian")
+             for i in picks]
+    handles, Bs, Xs, F = [], [], [], []
+    for p in probs:
+        handles.append(B().setup_problem(p, B().default_options(precision=1)))
+        f = np.ascontiguousarray(p.f.reshape(16, -1))
+        F.append(f)
+        Bs.append(torch.from_numpy(f.ravel().copy()).cuda())
+        Xs.append(torch.zeros(16 * 3 * p.n_nodes, dtype=torch.float64, device="cuda"))
+    rc, stats = B().solve_batched(handles, Bs, Xs, 16, 1e-8)
+    assert rc == 0
+    for k, (p, f, X) in enumerate(zip(probs, F, Xs)):
+        A = p.a_scipy().tocsr()
+        x = X.cpu().numpy().reshape(16, -1)
+        for j in range(16):
+            assert np.linalg.norm(f[j] - A @ x[j]) <= 1.5e-8 * np.linalg.norm(f[j]), (k, j)
+        oh = amg.build_hierarchy(p)
+        K, M = amg.operator(oh, 0), (lambda v: amg.precondition(oh, v))
+        for j in ((0,) if k == 0 else (0, 15)):
+            ref = amg.pcg(K, M, f[j], 1e-8, flexible=True)
+            conv = amg.pcg(K, M, f[j], 1e-13)
+            e_or = np.linalg.norm(ref.x - conv.x)
+            e_gpu = np.linalg.norm(x[j] - conv.x)
+            assert e_gpu <= 2 * e_or + 1e-12 * np.linalg.norm(conv.x), (picks[k], j, e_gpu, e_or)
+    for h in handles:
+        h.free()
