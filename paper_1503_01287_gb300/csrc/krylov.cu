@@ -47,19 +47,54 @@ __global__ void k_dots(int64_t n, int nd, const double* a0, const double* b0, co
   }
 }
 
-// multi-dot against a basis: partial[blk*(m) + i] = sum_k V[i][k] * w[k], i < m
-__global__ void k_mdot(int64_t n, int m, const double* __restrict__ V, int64_t ldv,
-                       const double* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  for (int i = 0; i < m; ++i) {
-    const double* v = V + i * ldv;
-    double s = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x)
-      s = fma(v[k], w[k], s);
-    double t = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x * m + i] = t;
+// multi-dot against a basis, kMdotG basis vectors per block row (blockIdx.y): each
+// thread keeps kMdotG sums, so w is read once per kMdotG vectors and the block
+// reduction runs once per row instead of once per vector.
+// partial[blockIdx.x * m + i] = sum over block column blockIdx.x's indices of V_i[k] w[k]
+constexpr int kMdotG = 8;
+__global__ void __launch_bounds__(256) k_mdot(int64_t n, int m, const double* __restrict__ V,
+                                              int64_t ldv, const double* __restrict__ w,
+                                              double* __restrict__ partial) {
+  __shared__ double sh[kMdotG][32];
+  const int i0 = blockIdx.y * kMdotG;
+  const int gn = min(kMdotG, m - i0);
+  double acc[kMdotG];
+#pragma unroll
+  for (int g = 0; g < kMdotG; ++g) acc[g] = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double wk = w[k];
+#pragma unroll
+    for (int g = 0; g < kMdotG; ++g)
+      if (g < gn) acc[g] = fma(V[(int64_t)(i0 + g) * ldv + k], wk, acc[g]);
   }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < kMdotG; ++g) {
+    double v = acc[g];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[g][wid] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < gn) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
+    partial[blockIdx.x * (int64_t)m + i0 + threadIdx.x] = t;
+  }
+}
+
+// out[i] = sum over b < nblk of partial[b * m + i] in block order, one warp per i
+__global__ void k_mdot_final(const double* __restrict__ partial, int nblk, int m,
+                             double* __restrict__ out) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * m + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[i] = s;
 }
 
 // out[d] = sum_blk partial[blk*nd + d] in block order (deterministic)
@@ -139,24 +174,49 @@ __global__ void k_cg_dir_pair(int64_t n, double* __restrict__ p, const double* _
   }
 }
 
-// w -= sum_i c[i] V_i  (c on the device)
-__global__ void k_basis_sub(int64_t n, int m, const double* __restrict__ V, int64_t ldv,
-                            const double* __restrict__ c, double* __restrict__ w) {
+// w -= sum_i c[i] V_i (c on the device, staged in shared memory; the basis loads
+// of one index go out eight at a time, the sum keeps the order i = 0, 1, ...)
+__global__ void __launch_bounds__(256) k_basis_sub(int64_t n, int m, const double* __restrict__ V,
+                                                   int64_t ldv, const double* __restrict__ c,
+                                                   double* __restrict__ w) {
+  __shared__ double cs[kMaxDots];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double acc = w[k];
-    for (int i = 0; i < m; ++i) acc = fma(-c[i], V[i * ldv + k], acc);
+    int i = 0;
+    for (; i + 8 <= m; i += 8) {
+      double v[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) v[g] = V[(int64_t)(i + g) * ldv + k];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) acc = fma(-cs[i + g], v[g], acc);
+    }
+    for (; i < m; ++i) acc = fma(-cs[i], V[(int64_t)i * ldv + k], acc);
     w[k] = acc;
   }
 }
 
-// x += sum_i y[i] Z_i
-__global__ void k_basis_add(int64_t n, int m, const double* __restrict__ Z, int64_t ldz,
-                            const double* __restrict__ y, double* __restrict__ x) {
+// x += sum_i y[i] Z_i (the same access pattern)
+__global__ void __launch_bounds__(256) k_basis_add(int64_t n, int m, const double* __restrict__ Z,
+                                                   int64_t ldz, const double* __restrict__ y,
+                                                   double* __restrict__ x) {
+  __shared__ double ys[kMaxDots];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double acc = x[k];
-    for (int i = 0; i < m; ++i) acc = fma(y[i], Z[i * ldz + k], acc);
+    int i = 0;
+    for (; i + 8 <= m; i += 8) {
+      double v[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) v[g] = Z[(int64_t)(i + g) * ldz + k];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) acc = fma(ys[i + g], v[g], acc);
+    }
+    for (; i < m; ++i) acc = fma(ys[i], Z[(int64_t)i * ldz + k], acc);
     x[k] = acc;
   }
 }
@@ -441,16 +501,18 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   const double bnorm = std::sqrt(read_scalar(h, S_BB));
   if (bnorm == 0.0) { st->iterations = 0; return AMG_OK; }
   DBuf<double> hcol, ydev;
-  hcol.alloc(kMaxDots);
+  hcol.alloc(2 * kMaxDots);   // the two Gram-Schmidt passes' coefficients
   ydev.alloc(kMaxDots);
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hc(kMaxDots);
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hc(2 * kMaxDots);
   int it = 0;
   double rel = 1.0;
   bool conv = false;
-  auto mdot = [&](int cnt, const double* vec) {
-    int nb = gridr(n);
-    k_mdot<<<nb, 256, 0, s>>>(n, cnt, V, ld, vec, h->red);
-    k_final<<<1, 256, 0, s>>>(h->red, nb, cnt, hcol.p);
+  auto mdot = [&](int cnt, const double* vec, double* out) {
+    const int rows = (cnt + kMdotG - 1) / kMdotG;
+    const int cols = (int)std::max<int64_t>(
+        1, std::min<int64_t>(kReduceBlocks / rows, (n + 255) / 256));
+    k_mdot<<<dim3(cols, rows), 256, 0, s>>>(n, cnt, V, ld, vec, h->red);
+    k_mdot_final<<<(cnt + 7) / 8, 256, 0, s>>>(h->red, cols, cnt, out);
     h->launches += 2;
   };
   while (it < h->opt.max_iterations && !conv) {
@@ -474,16 +536,18 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
       apply_K(h, zj, w);
       // classical Gram-Schmidt, applied twice (CGS2)
       for (int pass = 0; pass < 2; ++pass) {
-        mdot(j + 1, w);
-        k_basis_sub<<<gridr(n), 256, 0, s>>>(n, j + 1, V, ld, hcol.p, w);
+        double* coef = hcol.p + pass * kMaxDots;
+        mdot(j + 1, w, coef);
+        k_basis_sub<<<gridr(n), 256, 0, s>>>(n, j + 1, V, ld, coef, w);
         h->launches++;
-        AMG_CUDA(cudaMemcpyAsync(hc.data(), hcol.p, (j + 1) * sizeof(double),
-                                 cudaMemcpyDeviceToHost, s));
-        AMG_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j; ++i) H[i * m + j] += hc[i];
       }
       c.dots(w, w, S_T0);
+      // both passes' coefficients come back with the norm: one synchronisation
+      AMG_CUDA(cudaMemcpyAsync(hc.data(), hcol.p, (kMaxDots + j + 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
       const double hn = std::sqrt(read_scalar(h, S_T0));
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i <= j; ++i) H[i * m + j] += hc[pass * kMaxDots + i];
       H[(j + 1) * m + j] = hn;
       if (hn != 0.0) {
         k_scale<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / hn, V + (int64_t)(j + 1) * ld);
