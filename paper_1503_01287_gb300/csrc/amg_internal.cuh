@@ -214,7 +214,8 @@ struct amg_handle {
   amgp2::DBuf<double> kb, kx, kr, kz, kp, kq, kw, kro;   // padded layout
   amgp2::DBuf<float> kpf;           // the CG direction in pair form (8 floats a node)
   amgp2::DBuf<double> ub, ux;                             // user layout staging
-  amgp2::DBuf<double> gm_V, gm_Z;  // FGMRES bases
+  amgp2::DBuf<double> gm_V, gm_Z;  // FGMRES bases (V holds FP32 pairs)
+  amgp2::DBuf<double> gm_wp;       // the FGMRES Krylov vector as FP32 pairs
   amgp2::DBuf<double> red;         // reduction partials
   amgp2::DBuf<double> scal;        // device scalars
   amgp2::DBuf<double> pmass;       // Stokes pressure weights

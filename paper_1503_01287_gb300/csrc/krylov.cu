@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "amg_internal.cuh"
+#include "vec.cuh"
 
 namespace amgp2 {
 
@@ -47,54 +48,336 @@ __global__ void k_dots(int64_t n, int nd, const double* a0, const double* b0, co
   }
 }
 
-// multi-dot against a basis, kMdotG basis vectors per block row (blockIdx.y): each
-// thread keeps kMdotG sums, so w is read once per kMdotG vectors and the block
-// reduction runs once per row instead of once per vector.
-// partial[blockIdx.x * m + i] = sum over block column blockIdx.x's indices of V_i[k] w[k]
-constexpr int kMdotG = 8;
-__global__ void __launch_bounds__(256) k_mdot(int64_t n, int m, const double* __restrict__ V,
-                                              int64_t ldv, const double* __restrict__ w,
-                                              double* __restrict__ partial) {
-  __shared__ double sh[kMdotG][32];
-  const int i0 = blockIdx.y * kMdotG;
-  const int gn = min(kMdotG, m - i0);
-  double acc[kMdotG];
+constexpr int kMdotG = 8;   // basis rows per block row of the multi-dot
+
+// out[d * ostride + i] = sum over b < nblk of partial[(b * m + i) * nv + d] in block
+// order, one warp per (i, d)
+__global__ void k_mdot_final(const double* __restrict__ partial, int nblk, int m, int nv,
+                             int ostride, double* __restrict__ out) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= m * nv) return;
+  const int i = t / nv, d = t - i * nv;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[((int64_t)b * m + i) * nv + d];
 #pragma unroll
-  for (int g = 0; g < kMdotG; ++g) acc[g] = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const double wk = w[k];
-#pragma unroll
-    for (int g = 0; g < kMdotG; ++g)
-      if (g < gn) acc[g] = fma(V[(int64_t)(i0 + g) * ldv + k], wk, acc[g]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[d * ostride + i] = s;
+}
+
+// The Gram-Schmidt sweep of flexible GMRES with delayed reorthogonalisation (DCGS2:
+// Swirydowicz, Langou, Ananthan, Yang and Thomas, Numer. Linear Algebra Appl. 28,
+// 2021).  Rows 0..m-1 of the basis are final; row m holds u, the pending vector
+// (orthogonalised once and normalised); w is the new Krylov vector K z.  One pass
+// over the basis gives p_i = V_i . u and q_i = V_i . w for i < m together with
+// u . u and u . w (row m is u itself).
+//
+// The basis, u and w are FP32 pairs (hi + lo, the FP64 value to about 2^-48) and all
+// of the sweep's arithmetic is FP32 (pair_fma: exact products and TwoSum), because
+// FP64 instructions issue at a small fraction of the FP32 rate on this GPU: with
+// four FP64 FMAs per basis entry and step the sweep was bound by them, far below
+// the memory bandwidth.  Only each warp's final sums are converted to FP64.
+//
+// The basis streams through shared memory: one thread of a CTA issues 1-D bulk
+// copies (cp.async.bulk, the TMA's linear mode) of kTile-entry pieces of the rows
+// into a ring of kStages stages, each completing on its own mbarrier; all threads
+// wait for a stage's phase, use it, and pass a __syncthreads before it is refilled.
+// The copies run ahead of the arithmetic by up to kStages stages, so the memory
+// latency is hidden without holding loads in registers.  Every wait is bounded: a
+// CTA that gives up waits (bounded) for its copies in flight, sets *err and returns.
+constexpr int kTile = 256;                 // entries of a row piece (2 KB of pairs) = CTA size
+constexpr int kPieces = 10;                // pieces a stage: up to 8 basis rows, u and w
+constexpr int kStages = 4;
+constexpr unsigned kBulkSpins = 1u << 20;
+constexpr int kStreamSmem = kStages * kPieces * kTile * (int)sizeof(float2);   // 80 KB
+
+__device__ __forceinline__ uint32_t sm_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared
+// memory, counted on mbarrier b
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          sm_addr(dst)),
+      "l"(src), "r"(bytes), "r"(sm_addr(b))
+      : "memory");
+}
+// waits for the completion of the phase of parity par; false after kBulkSpins polls
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t par) {
+  for (unsigned i = 0; i < kBulkSpins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(sm_addr(b)), "r"(par)
+        : "memory");
+    if (done) return true;
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int g = 0; g < kMdotG; ++g) {
-    double v = acc[g];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[g][wid] = v;
+  return false;
+}
+// after a wait gave up at load q: wait (bounded) for loads q .. q + kStages - 1 of nq
+// that may still be in flight, then flag the error
+__device__ void ring_drain(uint64_t* bar, int64_t q, int64_t nq, int* err) {
+  for (int64_t d = q; d < q + kStages && d < nq; ++d)
+    bar_wait(&bar[d % kStages], (uint32_t)((d / kStages) & 1));
+  atomicExch(err, 1);
+}
+__device__ __forceinline__ uint32_t piece_bytes(int64_t ld, int64_t k0) {
+  return (uint32_t)(min((int64_t)kTile, ld - k0) * (int64_t)sizeof(float2));
+}
+
+// partial[(blockIdx.x * rows + i) * 2 + {0, 1}] = sum over the tiles of block column
+// blockIdx.x of V_i[k] u[k] and V_i[k] w[k], kMdotG rows per block row (blockIdx.y).
+// Rows are ld entries apart; the entries from n to ld are padding (copied, not used).
+__global__ void __launch_bounds__(kTile) k_mdot2(int64_t n, int64_t ld, int rows,
+                                                 const float2* __restrict__ V,
+                                                 const float2* __restrict__ u,
+                                                 const float2* __restrict__ w,
+                                                 double* __restrict__ partial,
+                                                 int* __restrict__ err) {
+  extern __shared__ __align__(128) float2 ring[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ double sh[2 * kMdotG][kTile / 32];
+  const int i0 = blockIdx.y * kMdotG;
+  const int gn = min(kMdotG, rows - i0);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t nq = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto issue = [&](int st, int64_t q) {
+    const int64_t k0 = (blockIdx.x + q * gridDim.x) * kTile;
+    const uint32_t bytes = piece_bytes(ld, k0);
+    bar_expect(&bar[st], bytes * (gn + 2));
+    float2* dst = ring + (size_t)st * kPieces * kTile;
+    for (int g = 0; g < gn; ++g)
+      bulk_load(dst + g * kTile, V + (int64_t)(i0 + g) * ld + k0, bytes, &bar[st]);
+    bulk_load(dst + 8 * kTile, u + k0, bytes, &bar[st]);
+    bulk_load(dst + 9 * kTile, w + k0, bytes, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) bar_init(&bar[st]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if ((int)threadIdx.x < gn) {
+  if (threadIdx.x == 0)
+    for (int st = 0; st < kStages && st < nq; ++st) issue(st, st);
+  float Su[kMdotG], su[kMdotG], Sw[kMdotG], sw[kMdotG];
+#pragma unroll
+  for (int g = 0; g < kMdotG; ++g) Su[g] = su[g] = Sw[g] = sw[g] = 0.f;
+  for (int64_t q = 0; q < nq; ++q) {
+    const int st = (int)(q % kStages);
+    const bool ok = bar_wait(&bar[st], (uint32_t)((q / kStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) ring_drain(bar, q, nq, err);
+      return;
+    }
+    const float2* sg = ring + (size_t)st * kPieces * kTile;
+    const int64_t k = (blockIdx.x + q * gridDim.x) * kTile + threadIdx.x;
+    if (k < n) {
+      const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
+#pragma unroll
+      for (int g = 0; g < kMdotG; ++g) {
+        if (g < gn) {
+          const float2 v = sg[g * kTile + threadIdx.x];
+          pair_fma(Su[g], su[g], v, uk.x, uk.y);
+          pair_fma(Sw[g], sw[g], v, wk.x, wk.y);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + kStages < nq) issue(st, q + kStages);
+  }
+  // the sums of a warp in pair arithmetic, then in FP64 across the warps
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 2 * kMdotG; ++q) {
+    float S = q < kMdotG ? Su[q] : Sw[q - kMdotG];
+    float e = q < kMdotG ? su[q] : sw[q - kMdotG];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float T = __shfl_xor_sync(0xffffffffu, S, o), t = __shfl_xor_sync(0xffffffffu, e, o);
+      pair_add(S, e, T, t);
+    }
+    if (lane == 0) sh[q][wid] = (double)S + (double)e;
+  }
+  __syncthreads();
+  const int g = threadIdx.x >> 1, d = threadIdx.x & 1;
+  if (g < gn) {
     double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
-    partial[blockIdx.x * (int64_t)m + i0 + threadIdx.x] = t;
+    for (int q = 0; q < kTile / 32; ++q) t += sh[d * kMdotG + g][q];
+    partial[(blockIdx.x * (int64_t)rows + i0 + g) * 2 + d] = t;
   }
 }
 
-// out[i] = sum over b < nblk of partial[b * m + i] in block order, one warp per i
-__global__ void k_mdot_final(const double* __restrict__ partial, int nblk, int m,
-                             double* __restrict__ out) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// FP32 pair of an FP64 value (hi = fl32(d), lo = fl32(d - hi)) and back
+__device__ __forceinline__ float2 to_pair(double d) {
+  const float hi = __double2float_rn(d);
+  return make_float2(hi, __double2float_rn(d - (double)hi));
+}
+__device__ __forceinline__ double from_pair(float2 p) { return (double)p.x + (double)p.y; }
+// a leading sum S and a small error sum s as one normalised pair (FastTwoSum)
+__device__ __forceinline__ float2 norm_pair(float S, float s) {
+  const float hi = __fadd_rn(S, s);
+  return make_float2(hi, __fsub_rn(s, __fsub_rn(hi, S)));
+}
+
+// Coefficients of the update from the sweep's dots (coef: p at [0, kMaxDots), q at
+// [kMaxDots, 2 kMaxDots), u . u at p[m], u . w at q[m]):
+//   s = ||u - V p|| = sqrt(u . u - p . p)   (u - V p is orthogonal to V)
+//   h = v . w with v = (u - V p) / s, i.e. (u . w - p . q) / s
+// written to coef[2 kMaxDots + {0, 1, 2}] = s, h, 1/s.  One warp, fixed order.
+__global__ void k_dcgs2_coef(int m, double* __restrict__ coef) {
   const int lane = threadIdx.x & 31;
-  if (i >= m) return;
-  double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * m + i];
+  double pp = 0.0, pq = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    const double p = coef[i];
+    pp = fma(p, p, pp);
+    pq = fma(p, coef[kMaxDots + i], pq);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[i] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    pp += __shfl_xor_sync(0xffffffffu, pp, o);
+    pq += __shfl_xor_sync(0xffffffffu, pq, o);
+  }
+  if (threadIdx.x == 0) {
+    const double sn = sqrt(fmax(coef[m] - pp, 0.0));
+    coef[2 * kMaxDots] = sn;
+    coef[2 * kMaxDots + 1] = sn > 0.0 ? (coef[kMaxDots + m] - pq) / sn : 0.0;
+    coef[2 * kMaxDots + 2] = sn > 0.0 ? 1.0 / sn : 0.0;
+  }
+}
+
+// The update of the same step, one more pass over rows 0..m-1 (pair arithmetic):
+//   v  = (u - sum_i p_i V_i) / s         written over u (row m): final
+//   w' = w - sum_i q_i V_i - h v          written to wn (row m + 1): the next pending
+// vector before its normalisation; partial[blockIdx.x] = the block's sum of w'^2.
+// A CTA takes tiles of kTile entries (one a thread); a tile's rows stream through
+// the ring eight at a time, u and w with the first eight.
+__global__ void __launch_bounds__(kTile) k_dcgs2_update(int64_t n, int64_t ld, int m,
+                                                        const float2* __restrict__ V, float2* u,
+                                                        const float2* __restrict__ w, float2* wn,
+                                                        const double* __restrict__ coef,
+                                                        double* __restrict__ partial,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(128) float2 ring[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ float2 cp[kMaxDots], cq[kMaxDots];   // -p_i and -q_i as pairs
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    cp[i] = to_pair(-coef[i]);
+    cq[i] = to_pair(-coef[kMaxDots + i]);
+  }
+  const float2 hneg = to_pair(-coef[2 * kMaxDots + 1]);
+  const float2 inv_s = to_pair(coef[2 * kMaxDots + 2]);
+  const int nch = max(1, (m + 7) / 8);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t my = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nq = my * nch;
+  auto issue = [&](int st, int64_t q) {
+    const int64_t k0 = (blockIdx.x + (q / nch) * gridDim.x) * kTile;
+    const int c = (int)(q % nch);
+    const int r0 = 8 * c, rn = max(0, min(8, m - r0));
+    const uint32_t bytes = piece_bytes(ld, k0);
+    bar_expect(&bar[st], bytes * (rn + (c == 0 ? 2 : 0)));
+    float2* dst = ring + (size_t)st * kPieces * kTile;
+    for (int r = 0; r < rn; ++r)
+      bulk_load(dst + r * kTile, V + (int64_t)(r0 + r) * ld + k0, bytes, &bar[st]);
+    if (c == 0) {
+      bulk_load(dst + 8 * kTile, u + k0, bytes, &bar[st]);
+      bulk_load(dst + 9 * kTile, w + k0, bytes, &bar[st]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) bar_init(&bar[st]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int st = 0; st < kStages && st < nq; ++st) issue(st, st);
+  float Sv = 0.f, sv = 0.f, Sw = 0.f, sw = 0.f, Sn = 0.f, sn = 0.f;
+  for (int64_t q = 0; q < nq; ++q) {
+    const int st = (int)(q % kStages);
+    const bool ok = bar_wait(&bar[st], (uint32_t)((q / kStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) ring_drain(bar, q, nq, err);
+      return;
+    }
+    const float2* sg = ring + (size_t)st * kPieces * kTile;
+    const int c = (int)(q % nch);
+    if (c == 0) {
+      const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
+      Sv = uk.x; sv = uk.y; Sw = wk.x; sw = wk.y;
+    }
+    const int r0 = 8 * c, rn = min(8, m - r0);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (r < rn) {
+        const float2 v = sg[r * kTile + threadIdx.x];
+        pair_fma(Sv, sv, cp[r0 + r], v.x, v.y);
+        pair_fma(Sw, sw, cq[r0 + r], v.x, v.y);
+      }
+    }
+    const int64_t k = (blockIdx.x + (q / nch) * gridDim.x) * kTile + threadIdx.x;
+    if (c == nch - 1 && k < n) {
+      const float2 a = norm_pair(Sv, sv);
+      float P = 0.f, pl = 0.f;
+      pair_fma(P, pl, inv_s, a.x, a.y);
+      const float2 vk = norm_pair(P, pl);
+      u[k] = vk;
+      pair_fma(Sw, sw, hneg, vk.x, vk.y);
+      const float2 wk2 = norm_pair(Sw, sw);
+      wn[k] = wk2;
+      pair_fma(Sn, sn, wk2, wk2.x, wk2.y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + kStages < nq) issue(st, q + kStages);
+  }
+  const double t = block_sum((double)Sn + (double)sn, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// v *= 1 / sqrt(nrm2[0]) (0 if the norm is 0) in pair arithmetic, also written to v2 as
+// FP64 values: normalises the pending vector and stages it as the preconditioner's input
+__global__ void k_scale_norm(int64_t n, float2* __restrict__ v, double* __restrict__ v2,
+                             const double* __restrict__ nrm2) {
+  const double r = sqrt(fmax(nrm2[0], 0.0));
+  const float2 f = to_pair(r > 0.0 ? 1.0 / r : 0.0);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = v[k];
+    float P = 0.f, pl = 0.f;
+    pair_fma(P, pl, f, a.x, a.y);
+    const float2 t = norm_pair(P, pl);
+    v[k] = t;
+    v2[k] = from_pair(t);
+  }
+}
+
+// v = pairs of a * f, v2 = a * f in FP64 (the first basis vector r / ||r||)
+__global__ void k_pair_scaled(int64_t n, const double* __restrict__ a, double f,
+                              float2* __restrict__ v, double* __restrict__ v2) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double t = a[k] * f;
+    v[k] = to_pair(t);
+    v2[k] = t;
+  }
+}
+
+// b = pairs of a (the Krylov vector K z for the sweep)
+__global__ void k_to_pair(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = to_pair(a[k]);
 }
 
 // out[d] = sum_blk partial[blk*nd + d] in block order (deterministic)
@@ -174,31 +457,8 @@ __global__ void k_cg_dir_pair(int64_t n, double* __restrict__ p, const double* _
   }
 }
 
-// w -= sum_i c[i] V_i (c on the device, staged in shared memory; the basis loads
-// of one index go out eight at a time, the sum keeps the order i = 0, 1, ...)
-__global__ void __launch_bounds__(256) k_basis_sub(int64_t n, int m, const double* __restrict__ V,
-                                                   int64_t ldv, const double* __restrict__ c,
-                                                   double* __restrict__ w) {
-  __shared__ double cs[kMaxDots];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
-  __syncthreads();
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[k];
-    int i = 0;
-    for (; i + 8 <= m; i += 8) {
-      double v[8];
-#pragma unroll
-      for (int g = 0; g < 8; ++g) v[g] = V[(int64_t)(i + g) * ldv + k];
-#pragma unroll
-      for (int g = 0; g < 8; ++g) acc = fma(-cs[i + g], v[g], acc);
-    }
-    for (; i < m; ++i) acc = fma(-cs[i], V[(int64_t)i * ldv + k], acc);
-    w[k] = acc;
-  }
-}
-
-// x += sum_i y[i] Z_i (the same access pattern)
+// x += sum_i y[i] Z_i (y staged in shared memory; the basis loads of one index go
+// out eight at a time, the sum keeps the order i = 0, 1, ...)
 __global__ void __launch_bounds__(256) k_basis_add(int64_t n, int m, const double* __restrict__ Z,
                                                    int64_t ldz, const double* __restrict__ y,
                                                    double* __restrict__ x) {
@@ -219,13 +479,6 @@ __global__ void __launch_bounds__(256) k_basis_add(int64_t n, int m, const doubl
     for (; i < m; ++i) acc = fma(ys[i], Z[(int64_t)i * ldz + k], acc);
     x[k] = acc;
   }
-}
-
-__global__ void k_scale(int64_t n, const double* __restrict__ a, double alpha,
-                        double* __restrict__ b) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = alpha * a[k];
 }
 
 __global__ void k_axpy(int64_t n, double alpha, const double* __restrict__ a, double* __restrict__ b) {
@@ -491,95 +744,214 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   cudaStream_t s = c.s;
   const int64_t n = c.n;
   const int m = std::max(1, std::min(h->opt.gmres_restart, kMaxDots - 2));
-  double* V = h->gm_V;
+  // the basis V as FP32 pairs (8 bytes an entry, the FP64 layout's size); Z in FP64
+  float2* V = reinterpret_cast<float2*>(h->gm_V.p);
   double* Z = h->gm_Z;
-  // basis vectors start on 64-byte boundaries: node loads are 32-byte vector accesses
+  // basis vectors start on 64-byte boundaries
   const int64_t ld = (n + 7) / 8 * 8;
   double* w = h->kw;
+  float2* wp = reinterpret_cast<float2*>(h->gm_wp.p);   // w as pairs for the sweep
   AMG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   c.dots(b, b, S_BB);
   const double bnorm = std::sqrt(read_scalar(h, S_BB));
   if (bnorm == 0.0) { st->iterations = 0; return AMG_OK; }
-  DBuf<double> hcol, ydev;
-  hcol.alloc(2 * kMaxDots);   // the two Gram-Schmidt passes' coefficients
+  // coef (device, read back once a step): the sweep's dots with u at [0, kMaxDots),
+  // with w at [kMaxDots, 2 kMaxDots), then s, h, 1/s, ||w'||^2
+  constexpr int kS = 2 * kMaxDots;
+  DBuf<double> coef, ydev;
+  coef.alloc(kS + 8);
   ydev.alloc(kMaxDots);
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hc(2 * kMaxDots);
+  // H by columns: Hc[j * (m + 1) + i] = H(i, j); rotated in place once a column is final
+  std::vector<double> Hc((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hb(kS + 8), tmp(m + 1);
+  // the sweep's kernels: kTile threads a CTA, the ring in dynamic shared memory, two
+  // CTAs an SM
+  int dev = 0, sms = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  AMG_CUDA(cudaFuncSetAttribute(k_mdot2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kStreamSmem));
+  AMG_CUDA(cudaFuncSetAttribute(k_dcgs2_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kStreamSmem));
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * sms));
+  auto mdot2 = [&](int rows, const float2* u, const float2* wv) {
+    const int grows = (rows + kMdotG - 1) / kMdotG;
+    const int cols = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms / grows, ntiles));
+    k_mdot2<<<dim3(cols, grows), kTile, kStreamSmem, s>>>(n, ld, rows, V, u, wv, h->red,
+                                                          h->flag.p);
+    k_mdot_final<<<(2 * rows + 7) / 8, 256, 0, s>>>(h->red, cols, rows, 2, kMaxDots, coef.p);
+    h->launches += 2;
+  };
   int it = 0;
   double rel = 1.0;
   bool conv = false;
-  auto mdot = [&](int cnt, const double* vec, double* out) {
-    const int rows = (cnt + kMdotG - 1) / kMdotG;
-    const int cols = (int)std::max<int64_t>(
-        1, std::min<int64_t>(kReduceBlocks / rows, (n + 255) / 256));
-    k_mdot<<<dim3(cols, rows), 256, 0, s>>>(n, cnt, V, ld, vec, h->red);
-    k_mdot_final<<<(cnt + 7) / 8, 256, 0, s>>>(h->red, cols, cnt, out);
-    h->launches += 2;
+  auto col = [&](int j) { return Hc.data() + (size_t)j * (m + 1); };
+  // rotations 0..j-1 on column c[0..j+1], then the one that zeroes c[j+1]
+  auto rotate = [&](double* cj, int j, double& ck, double& sk) {
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * cj[i] + sn[i] * cj[i + 1];
+      cj[i + 1] = -sn[i] * cj[i] + cs[i] * cj[i + 1];
+      cj[i] = t;
+    }
+    const double den = std::hypot(cj[j], cj[j + 1]);
+    ck = cj[j] / den;
+    sk = cj[j + 1] / den;
+    cj[j] = den;
+    cj[j + 1] = 0.0;
+  };
+  auto commit = [&](int j) {
+    rotate(col(j), j, cs[j], sn[j]);
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+  };
+  auto read_coef = [&](int cnt) {
+    AMG_CUDA(cudaMemcpyAsync(hb.data(), coef.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+  };
+  // z_j = M u_j, the pressure projection of z_j and w = K z_j run on fixed vectors (u_j
+  // staged in kr, z_j in kz) as one graph launch per step, captured once per solve: the
+  // preconditioner's short coarse-level kernels then run back to back after the host's
+  // synchronisation of the step before
+  double* ur = h->kr;
+  double* zr = h->kz;
+  auto step = [&]() {
+    precond(h, ur, zr);
+    project_pressure(h, c, zr);
+    apply_K(h, zr, w);
+  };
+  cudaGraphExec_t exec = nullptr;
+  struct ExecGuard {
+    cudaGraphExec_t& e;
+    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+  } exec_guard{exec};
+  int64_t per_step = 0;
+  bool tried = !h->opt.use_graphs || h->iter_graph_failed;
+  auto run_step = [&]() {
+    if (!tried) {
+      tried = true;
+      const int64_t l0 = h->launches;
+      cudaGraph_t gr = nullptr;
+      bool capturing = false;
+      try {
+        AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        step();
+        capturing = false;
+        AMG_CUDA(cudaStreamEndCapture(s, &gr));
+        AMG_CUDA(cudaGraphInstantiate(&exec, gr, 0));
+        per_step = h->launches - l0;
+      } catch (const Error&) {
+        if (capturing) {
+          cudaGraph_t junk = nullptr;
+          cudaStreamEndCapture(s, &junk);
+          if (junk) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        exec = nullptr;
+        h->iter_graph_failed = true;   // plain launches from here on
+      }
+      if (gr) cudaGraphDestroy(gr);
+      h->launches = l0;
+    }
+    if (exec) {
+      AMG_CUDA(cudaGraphLaunch(exec, s));
+      h->launches += per_step;
+    } else {
+      step();
+    }
   };
   while (it < h->opt.max_iterations && !conv) {
-    // r = b - K x, v_0 = r / ||r||
+    // r = b - K x, u_0 = r / ||r|| (its own sweep makes it exactly unit)
     apply_K(h, x, w);
     k_sub<<<gridr(n), 256, 0, s>>>(n, b, w, w);
     h->launches++;
     c.dots(w, w, S_T0);
     const double beta = std::sqrt(read_scalar(h, S_T0));
     if (beta == 0.0) { conv = true; rel = 0.0; break; }
-    k_scale<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / beta, V);
+    k_pair_scaled<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / beta, V, ur);
     h->launches++;
-    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(Hc.begin(), Hc.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
+    double rho = beta;   // the norm that scaled the pending vector u_j
     int jused = 0;
     for (int j = 0; j < m; ++j) {
+      float2* uj = V + (int64_t)j * ld;
       double* zj = Z + (int64_t)j * ld;
-      precond(h, V + (int64_t)j * ld, zj);
-      project_pressure(h, c, zj);
-      apply_K(h, zj, w);
-      // classical Gram-Schmidt, applied twice (CGS2)
-      for (int pass = 0; pass < 2; ++pass) {
-        double* coef = hcol.p + pass * kMaxDots;
-        mdot(j + 1, w, coef);
-        k_basis_sub<<<gridr(n), 256, 0, s>>>(n, j + 1, V, ld, coef, w);
-        h->launches++;
+      run_step();
+      launch_copy(zr, zj, n, s, h);
+      k_to_pair<<<gridr(n), 256, 0, s>>>(n, w, wp);
+      h->launches++;
+      // one sweep: dots of rows 0..j with u_j and w, then the update of u_j to v_j and of
+      // w to the next pending vector u_{j+1} (row j + 1), normalised on the device
+      {
+        mdot2(j + 1, uj, wp);
+        k_dcgs2_coef<<<1, 32, 0, s>>>(j, coef.p);
+        float2* un = V + (int64_t)(j + 1) * ld;
+        k_dcgs2_update<<<ublocks, kTile, kStreamSmem, s>>>(n, ld, j, V, uj, wp, un, coef.p,
+                                                           h->red, h->flag.p);
+        k_final<<<1, 256, 0, s>>>(h->red, ublocks, 1, coef.p + kS + 3);
+        k_scale_norm<<<gridr(n), 256, 0, s>>>(n, un, ur, coef.p + kS + 3);
+        h->launches += 4;
       }
-      c.dots(w, w, S_T0);
-      // both passes' coefficients come back with the norm: one synchronisation
-      AMG_CUDA(cudaMemcpyAsync(hc.data(), hcol.p, (kMaxDots + j + 1) * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
-      const double hn = std::sqrt(read_scalar(h, S_T0));
-      for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i <= j; ++i) H[i * m + j] += hc[pass * kMaxDots + i];
-      H[(j + 1) * m + j] = hn;
-      if (hn != 0.0) {
-        k_scale<<<gridr(n), 256, 0, s>>>(n, w, 1.0 / hn, V + (int64_t)(j + 1) * ld);
-        h->launches++;
+      read_coef(kS + 8);
+      // u_j = s v_j + sum_{i<j} p_i v_i, and w'_{j-1} = rho u_j: column j - 1 is final
+      const double sj = hb[kS], hjj = hb[kS + 1];
+      if (j == 0) {
+        g[0] = rho * sj;
+      } else {
+        double* cp = col(j - 1);
+        for (int i = 0; i < j; ++i) cp[i] += rho * hb[i];
+        cp[j] = rho * sj;
+        commit(j - 1);
+        rel = std::fabs(g[j]) / bnorm;
       }
-      for (int i = 0; i < j; ++i) {
-        double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-        H[i * m + j] = t;
-      }
-      double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-      cs[j] = H[j * m + j] / den;
-      sn[j] = H[(j + 1) * m + j] / den;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      // column j before the reorthogonalisation of u_{j+1}: H(j+1, j) = ||w'||
+      rho = std::sqrt(std::max(hb[kS + 3], 0.0));
+      double* cj = col(j);
+      for (int i = 0; i < j; ++i) cj[i] = hb[kMaxDots + i];
+      cj[j] = hjj;
+      cj[j + 1] = rho;
       ++it;
       jused = j + 1;
+      std::copy(cj, cj + j + 2, tmp.begin());
+      double ck, sk;
+      rotate(tmp.data(), j, ck, sk);
+      const double est = std::fabs(sk * g[j]) / bnorm;
+      if (est > tol && j + 1 < m && it < h->opt.max_iterations) continue;
+      // stopping: reorthogonalise u_{j+1} against rows 0..j now, making column j final
+      {
+        const float2* un = V + (int64_t)(j + 1) * ld;
+        mdot2(j + 2, un, un);
+      }
+      read_coef(j + 2);
+      std::copy(cj, cj + j + 2, tmp.begin());
+      const double gj = g[j];
+      double pp = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        cj[i] += rho * hb[i];
+        pp += hb[i] * hb[i];
+      }
+      const double hnext = rho * std::sqrt(std::max(hb[j + 1] - pp, 0.0));
+      cj[j + 1] = hnext;
+      commit(j);
       rel = std::fabs(g[j + 1]) / bnorm;
       if (!std::isfinite(rel)) fail(AMG_ERR_BREAKDOWN, "non-finite residual in FGMRES");
-      if (rel <= tol || it >= h->opt.max_iterations || hn == 0.0) {
+      if (rel <= tol || j + 1 >= m || it >= h->opt.max_iterations || hnext == 0.0) {
         conv = rel <= tol;
         break;
       }
+      // the estimate before the reorthogonalisation was too optimistic: go on, and let
+      // the next sweep finalise column j as usual
+      std::copy(tmp.begin(), tmp.begin() + j + 2, cj);
+      g[j] = gj;
+      g[j + 1] = 0.0;
     }
-    // y = H^{-1} g (upper triangular), x += Z y
+    // y = R^{-1} g (R: the rotated H, upper triangular), x += Z y
     std::vector<double> y(jused);
     for (int i = jused - 1; i >= 0; --i) {
       double t = g[i];
-      for (int k = i + 1; k < jused; ++k) t -= H[i * m + k] * y[k];
-      y[i] = t / H[i * m + i];
+      for (int k = i + 1; k < jused; ++k) t -= col(k)[i] * y[k];
+      y[i] = t / col(i)[i];
     }
     AMG_CUDA(cudaMemcpyAsync(ydev.p, y.data(), jused * sizeof(double), cudaMemcpyHostToDevice, s));
     k_basis_add<<<gridr(n), 256, 0, s>>>(n, jused, Z, ld, ydev.p, x);
@@ -641,6 +1013,7 @@ int solve_device(amg_handle* h, const double* b_user, double* x_user, double tol
       const int64_t ld = (n + 7) / 8 * 8;
       ensure(h->gm_V, (int64_t)(m + 1) * ld);
       ensure(h->gm_Z, (int64_t)m * ld);
+      ensure(h->gm_wp, ld);
       rc = solve_fgmres(h, c, b, x, tol, st);
       break;
     }
