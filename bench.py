@@ -27,6 +27,10 @@ import time
 
 import numpy as np
 
+# the batched workload runs one stream per problem; more hardware work queues than
+# the default 8 let them overlap (read when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

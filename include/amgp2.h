@@ -90,9 +90,10 @@ enum amg_precision {
                                kernels); level 0, D^{-1}, P and the pressure
                                parts stay FP32                                  */
   AMG_FP32_PAIR = 3         /* not a cycle precision: amg_level_apply and
-                               amg_time_level_op on level 0 of an FP32 SPD
-                               handle with outer_pair run the Krylov operator's
-                               FP32-pair kernel (see amg_options.outer_pair)    */
+                               amg_time_level_op on level 0 of an FP32 handle
+                               with outer_pair run the Krylov operator's
+                               FP32-pair kernel (see amg_options.outer_pair;
+                               amg_level_apply adds the saddle blocks in FP64) */
 };
 
 enum amg_krylov {
@@ -172,7 +173,9 @@ typedef struct amg_options {
                                chosen per level by timing at setup (default),
                                0 one launch per colour, k = 1, 2, 4, 8 or 16:
                                the whole sweep in one cluster of k CTAs         */
-  int32_t outer_pair;       /* FP32-cycle CG solves of SPD kinds: 1 (default)
+  int32_t outer_pair;       /* FP32-cycle Krylov solves (CG for SPD kinds, the
+                               velocity block of FGMRES for saddle kinds, whose
+                               B and C parts stay FP64): 1 (default)
                                the Krylov operator products K p in FP32-pair
                                arithmetic -- every FP64 value and direction entry
                                held as two floats hi + lo, each product formed
@@ -341,19 +344,24 @@ int amg_set_pressure_weights(amg_handle* h, const double* w, int32_t device_ptrs
  * sides, solved together: the multi-right-hand-side form of amg_solve.  The
  * cycle kernels work on all right-hand sides of a problem at once (block-row
  * times 16-column block: SpMM), each right-hand side runs its own flexible CG
- * with the stopping rule of amg_solve, and all problems run as parallel
- * branches of ONE CUDA graph launch (each branch an initial block and a
- * device-side loop with its own stopping test).
- *   handles     n_problems handles (their precision and options apply).
+ * with the stopping rule of amg_solve, and every problem runs as one CUDA
+ * graph launch on its own handle's stream (an initial block and a device-side
+ * loop with its own stopping test), all of them side by side.  How many of the
+ * streams run concurrently is bounded by the process's hardware work queues:
+ * set CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32) before the CUDA context exists.
+ *   handles     n_problems distinct handles (their precision and options apply);
+ *               a handle listed twice is rejected with AMG_ERR_INVALID.
  *   n_rhs       1..16 right-hand sides per problem.
  *   B, X        per problem: device pointers to n_rhs vectors of 3*n_nodes
  *               doubles, vector r at offset r*3*n_nodes; X receives the
  *               solutions (x0 = 0).
- *   stats       NULL or an array of n_problems; solve_ms is the graph's device
- *               time, iterations the loop count (the slowest right-hand side),
+ *   stats       NULL or an array of n_problems; solve_ms is the device time of
+ *               the whole batch (from before the first launch to after the last
+ *               problem, on the first handle's stream), iterations the loop count
+ *               (the slowest right-hand side),
  *               true_rel_residual the worst right-hand side.
  * Returns AMG_OK when every right-hand side converged, AMG_NOT_CONVERGED when
- * some stopped at max_iterations.  Synchronises the first handle's stream.
+ * some stopped at max_iterations.  Synchronises every handle's stream.
  */
 int amg_solve_batched(amg_handle* const* handles, int32_t n_problems, int32_t n_rhs,
                       const double* const* B, double* const* X, double rel_tol,

@@ -284,6 +284,7 @@ void precondition_device(amg_handle* h, const double* r, double* z);
 // y = K_0 x with the FP32-pair operator (level 0 values split into hi/lo float
 // planes, x as 8 floats a node: hi x,y,z,0 then lo x,y,z,0); y padded FP64
 void apply_pair(amg_handle* h, const float* xp, double* y);
+void apply_K_pair(amg_handle* h, const double* x, float* xp, double* y);
 // the 8-floats-a-node pair form of a padded FP64 vector of n4 = 4 n entries
 void launch_split_pair(const double* x, float* xp, int64_t n4, cudaStream_t s, amg_handle* h);
 // restriction (restrict = true) or prolongation between level and level+1 on

@@ -497,12 +497,11 @@ int amg_level_apply(amg_handle* h, int32_t level, int32_t precision, const doubl
       launch_to_double(lv.r32, lv.r64, n4, h->stream, h);
     } else if (precision == AMG_FP32_PAIR) {
       if (level != 0 || !lv.val2.p)
-        fail(AMG_ERR_INVALID, "the FP32-pair operator exists on level 0 of FP32 SPD handles "
+        fail(AMG_ERR_INVALID, "the FP32-pair operator exists on level 0 of FP32 handles "
                               "with outer_pair");
       DBuf<float> xp;
       xp.alloc(8 * (size_t)lv.n);
-      launch_split_pair(lv.t64, xp, 4 * (int64_t)lv.n, h->stream, h);
-      apply_pair(h, xp, lv.r64);
+      apply_K_pair(h, lv.t64, xp, lv.r64);
       AMG_CUDA(cudaStreamSynchronize(h->stream));
     } else {
       fail(AMG_ERR_INVALID, "unknown precision");
@@ -568,7 +567,7 @@ int amg_time_level_op(amg_handle* h, int32_t op, int32_t level, int32_t precisio
     const bool pair = precision == AMG_FP32_PAIR;
     if (f32 && !h->L[0]->val32.p) fail(AMG_ERR_INVALID, "FP32 operators exist only with FP32");
     if (pair && (op != AMG_OP_APPLY || level != 0 || !h->L[0]->val2.p))
-      fail(AMG_ERR_INVALID, "the FP32-pair operator is AMG_OP_APPLY on level 0 of FP32 SPD "
+      fail(AMG_ERR_INVALID, "the FP32-pair operator is AMG_OP_APPLY on level 0 of FP32 "
                             "handles with outer_pair");
     Level& lv = *h->L[op == AMG_OP_PRECOND ? 0 : level];
     DBuf<float> xp;

@@ -2196,7 +2196,7 @@ void precondition_device<float>(amg_handle* h, const double* r, double* z) {
 void apply_pair(amg_handle* h, const float* xp, double* y) {
   const Level& lv = *h->L[0];
   if (!lv.val2.p)
-    fail(AMG_ERR_INVALID, "the FP32-pair operator needs an FP32 SPD handle with outer_pair");
+    fail(AMG_ERR_INVALID, "the FP32-pair operator needs an FP32 handle with outer_pair");
   switch (lv.group_pair) {
     case 4: launch_apply_pair<4>(lv, xp, y, h->stream); break;
     case 8: launch_apply_pair<8>(lv, xp, y, h->stream); break;
@@ -2204,6 +2204,20 @@ void apply_pair(amg_handle* h, const float* xp, double* y) {
     default: launch_apply_pair<16>(lv, xp, y, h->stream); break;
   }
   h->launches++;
+}
+
+// y = K_0 x with the velocity block in FP32-pair arithmetic (x split into xp, 8 floats a
+// node, first) and, on saddle levels, B^T p and B u - C p added in FP64
+void apply_K_pair(amg_handle* h, const double* x, float* xp, double* y) {
+  Level& lv = *h->L[0];
+  launch_split_pair(x, xp, 4 * (int64_t)lv.n, h->stream, h);
+  apply_pair(h, xp, y);
+  if (h->saddle && lv.np > 0) {
+    Emit<double> e{h};
+    const double* p = x + 4 * lv.n;
+    e.bt_add(lv, p, 1.0, y);
+    e.prows(0, lv, x, p, nullptr, y + 4 * lv.n, 0.0);
+  }
 }
 
 void level_transfer(amg_handle* h, int l, bool restrict_, bool f32) {

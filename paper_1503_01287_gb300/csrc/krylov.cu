@@ -814,10 +814,14 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   // synchronisation of the step before
   double* ur = h->kr;
   double* zr = h->kz;
+  // the FP32 cycle's operator products in FP32 pairs for the velocity block (the
+  // residual at each restart and at exit stays FP64)
+  float* pf = h->L[0]->val2.p ? h->kpf.p : nullptr;
   auto step = [&]() {
     precond(h, ur, zr);
     project_pressure(h, c, zr);
-    apply_K(h, zr, w);
+    if (pf) apply_K_pair(h, zr, pf, w);
+    else apply_K(h, zr, w);
   };
   cudaGraphExec_t exec = nullptr;
   struct ExecGuard {

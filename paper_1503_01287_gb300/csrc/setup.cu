@@ -1164,7 +1164,7 @@ void finish_level(amg_handle* h, Level& lv, bool coarsest) {
       AMG_LAUNCH_CHECK();
       h->launches++;
     }
-    if (&lv == h->L[0].get() && !h->saddle && h->opt.outer_pair && lv.nnzb > 0) {
+    if (&lv == h->L[0].get() && h->opt.outer_pair && lv.nnzb > 0) {
       lv.val2.alloc(9 * (size_t)lv.nnzb);
       k_split_pair<<<grid_for(9 * lv.nnzb), 256, 0, s>>>(lv.k_val(), lv.val2, 9 * lv.nnzb);
       AMG_LAUNCH_CHECK();

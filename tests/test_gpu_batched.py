@@ -162,3 +162,19 @@ def test_batched_workload_sample_matches_oracle():
             assert e_gpu <= 2 * e_or + 1e-12 * np.linalg.norm(conv.x), (picks[k], j, e_gpu, e_or)
     for h in handles:
         h.free()
+
+
+def test_batched_rejects_a_repeated_handle():
+    """Each problem runs on its own handle's stream and work vectors: a handle listed
+    twice would race with itself, so the call refuses it before any launch."""
+    p = fp.elasticity_problem(4, seed=1, nu=0.3)
+    h = B().setup_problem(p, B().default_options(precision=1))
+    b = torch.from_numpy(np.ascontiguousarray(p.f.reshape(-1))).cuda()
+    xs = [torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda") for _ in range(2)]
+    with pytest.raises(B().AmgError) as ei:
+        B().solve_batched([h, h], [b, b], xs, 1, 1e-8)
+    assert ei.value.code == -1                # AMG_ERR_INVALID
+    # the handle still works
+    rc, st = B().solve_batched([h], [b], xs[:1], 1, 1e-8)
+    assert rc == 0 and st[0].converged
+    h.free()

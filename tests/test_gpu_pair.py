@@ -62,6 +62,56 @@ def test_pair_operator_matches_oracle(kind, n):
     h.free()
 
 
+@pytest.mark.parametrize("kind", ["mixed", "stokes"])
+def test_pair_saddle_operator_matches_oracle(kind):
+    """Saddle kinds: the velocity block in pairs, B^T p and B u - C p in FP64; per
+    entry within 1e-12 of sum_j |k_ij x_j| against the oracle's K."""
+    from oracle import saddle
+    prob = (fp.mixed_elasticity_problem(5, nu=0.499, seed=5) if kind == "mixed"
+            else fp.stokes_lid_problem(5))
+    h = B().setup_problem(prob, B().default_options(precision=B().AMG_FP32))
+    oh = amg.build_hierarchy(prob, amg.Options(smoother="sgs"))
+    lv0 = oh.levels[0]
+    import scipy.sparse as sp
+    K = sp.bmat([[lv0.A, lv0.B.T], [lv0.B, -lv0.C]]).tocsr()
+    rng = np.random.default_rng(3)
+    for scale in (1.0, 1e-12, 1e9):
+        x = scale * rng.standard_normal(prob.n_dof)
+        want = saddle.apply_K(lv0, x)
+        bound = abs(K) @ np.abs(x)
+        y = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+        h.level_apply(0, cuda(x), y, B().AMG_FP32_PAIR)
+        err = np.abs(y.cpu().numpy() - want)
+        assert np.all(err <= 1e-12 * bound), (err / np.maximum(bound, 1e-300)).max()
+    h.free()
+
+
+@pytest.mark.parametrize("kind", ["mixed", "stokes"])
+def test_pair_saddle_solve_matches_fp64_operator_solve(kind):
+    """FGMRES with the FP32 cycle: the pair operator and the FP64 operator reach the
+    same tolerance in the same number of iterations (+-1), the FP64 residual checked
+    on the host from the oracle's K."""
+    from oracle import saddle
+    prob = (fp.mixed_elasticity_problem(6, nu=0.49, seed=5) if kind == "mixed"
+            else fp.stokes_lid_problem(6))
+    b = cuda(prob.rhs())
+    out = {}
+    for pair in (0, 1):
+        h = B().setup_problem(prob, B().default_options(precision=B().AMG_FP32,
+                                                        outer_pair=pair))
+        x = torch.zeros_like(b)
+        st = h.solve(b, x, 1e-10, device_ptrs=True)
+        assert st.converged and st.true_rel_residual <= 1.5e-10
+        out[pair] = (st.iterations, x.cpu().numpy())
+        h.free()
+    assert abs(out[0][0] - out[1][0]) <= 1, (out[0][0], out[1][0])
+    lv0 = amg.build_hierarchy(prob, amg.Options(smoother="sgs")).levels[0]
+    bh = prob.rhs()
+    for pair in (0, 1):
+        rel = np.linalg.norm(bh - saddle.apply_K(lv0, out[pair][1])) / np.linalg.norm(bh)
+        assert rel <= 1.5e-10, (pair, rel)
+
+
 @pytest.mark.parametrize("kind", ["elasticity", "laplace"])
 def test_pair_solve_matches_fp64_operator_solve(kind):
     prob = (fp.elasticity_problem(12, seed=1) if kind == "elasticity"
