@@ -489,15 +489,30 @@ def run_gpu(args, rank, world):
 
 
 def run_profile(args):
-    """One chosen and one plain solve, nothing else timed (a case for ncu)."""
+    """One chosen and one plain solve, nothing else timed (a case for ncu).  With
+    --workload mixed: one FP32-cycle FGMRES(300) solve of the nu = 0.499 member of the
+    mixed elasticity family on --n-mixed cubes, default options."""
     import torch
 
     from fem_inputs import elasticity_problem
     import __graft_entry__ as ge
     ge.build()
     from paper_1503_01287_gb300 import binding as B
-    prob = elasticity_problem(args.n, seed=1)
     stream = torch.cuda.Stream()
+    if args.workload == "mixed":
+        from fem_inputs.configs import make_config
+        prob = make_config("mixed_elast_n40", n=args.n_mixed)[1]
+        b = torch.from_numpy(prob.rhs()).cuda()
+        x = torch.zeros_like(b)
+        h = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32, gmres_restart=300,
+                                                    max_iterations=1000),
+                            stream=stream.cuda_stream)
+        st = h.solve(b, x, TOL, device_ptrs=True)
+        print(json.dumps({"precision": B.AMG_FP32, "workload": f"mixed_elast_n{args.n_mixed}",
+                          "nu": prob.params.get("nu"), **st.as_dict()}), flush=True)
+        h.free()
+        return
+    prob = elasticity_problem(args.n, seed=1)
     b = torch.from_numpy(prob.rhs()).cuda()
     x = torch.zeros_like(b)
     for prec in (B.AMG_FP32, B.AMG_FP64):
