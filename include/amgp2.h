@@ -208,6 +208,15 @@ typedef struct amg_options {
                                (default; 0 where one group of lanes per row is
                                faster), 0 never, k = 1..8 forced (lanes per
                                row as tuned for the chain)                     */
+  int32_t gs_tma;           /* FP32 one-launch-per-colour Gauss-Seidel kernel
+                               with the block values and columns of a CTA's rows
+                               staged in shared memory by bulk (TMA) copies
+                               issued before the wait on the previous colour:
+                               -1 with its lanes per row where it beats the
+                               register-prefetch kernel, chosen per level by
+                               timing at setup (default), 0 never, 1 on every
+                               coloured FP32 level with the chain's lanes per
+                               row (bitwise its results)                       */
 } amg_options;
 
 #define AMG_MAX_LEVELS 8
@@ -236,6 +245,8 @@ typedef struct amg_stats {
                                dataflow sweep (0: not used on the level)        */
   int32_t level_gs_stream[AMG_MAX_LEVELS];   /* CTAs per SM of the grid-stride
                                colour kernel (0: one group of lanes per row)    */
+  int32_t level_gs_tma[AMG_MAX_LEVELS];      /* 1: the level's colour kernel is
+                               the TMA-staged one                               */
 } amg_stats;
 
 typedef struct amg_level_info {

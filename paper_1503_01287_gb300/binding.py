@@ -75,7 +75,7 @@ class AmgOptions(C.Structure):
                 ("omega", C.c_double), ("omega_p", C.c_double),
                 ("batch_tile", C.c_int32), ("gs_cluster", C.c_int32),
                 ("outer_pair", C.c_int32), ("post_order", C.c_int32),
-                ("gs_flow", C.c_int32), ("gs_stream", C.c_int32)]
+                ("gs_flow", C.c_int32), ("gs_stream", C.c_int32), ("gs_tma", C.c_int32)]
 
 
 class AmgStats(C.Structure):
@@ -91,7 +91,8 @@ class AmgStats(C.Structure):
                 ("cluster_from", C.c_int32), ("cycle_kernel", C.c_int32),
                 ("level_gs_cluster", C.c_int32 * AMG_MAX_LEVELS),
                 ("level_gs_flow", C.c_int32 * AMG_MAX_LEVELS),
-                ("level_gs_stream", C.c_int32 * AMG_MAX_LEVELS)]
+                ("level_gs_stream", C.c_int32 * AMG_MAX_LEVELS),
+                ("level_gs_tma", C.c_int32 * AMG_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         nl = self.n_levels
@@ -107,7 +108,8 @@ class AmgStats(C.Structure):
                 "cluster_from": self.cluster_from, "cycle_kernel": self.cycle_kernel,
                 "level_gs_cluster": list(self.level_gs_cluster[:nl]),
                 "level_gs_flow": list(self.level_gs_flow[:nl]),
-                "level_gs_stream": list(self.level_gs_stream[:nl])}
+                "level_gs_stream": list(self.level_gs_stream[:nl]),
+                "level_gs_tma": list(self.level_gs_tma[:nl])}
 
 
 class AmgLearned(C.Structure):

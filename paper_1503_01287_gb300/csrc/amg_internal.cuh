@@ -105,6 +105,7 @@ struct Level {
   int group = 0;        // lanes per block row in the row kernels (autotuned at setup)
   int group_gs = 0;     // the same for the colour-subset Gauss-Seidel kernel
   int gs_stream = 0;    // CTAs per SM of the grid-stride colour kernel (0: k_gs_pdl)
+  int gs_tma = 0;       // 1: the FP32 colour kernel stages its rows' blocks by TMA (k_gs_tma)
   int gs_xnc = 0;       // k_gs_pdl gathers x through L1 (1) or L2 only (0), by timing
   int group64 = 0;      // the FP64 operator kernel when the cycle runs in FP32
   // level 0 of an FP32 SPD handle with outer_pair: the kernel-layout values as

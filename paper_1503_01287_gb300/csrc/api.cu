@@ -99,6 +99,7 @@ void amg_default_options(amg_options* o) {
   o->post_order = -1;     // resolved from the Krylov method in amg_setup
   o->gs_flow = -1;
   o->gs_stream = -1;
+  o->gs_tma = -1;
 }
 
 int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const amg_options* opt,
@@ -147,7 +148,8 @@ int amg_setup(const amg_matrix* m, const int32_t* node_tags, int32_t kind, const
     if (h->opt.m_pre < 0 || h->opt.m_post < 0 || h->opt.nu < 1 || h->opt.nu > 2 ||
         h->opt.cycles < 1 || h->opt.max_levels < 1 || h->opt.gmres_restart < 1 ||
         h->opt.post_order < -1 || h->opt.post_order > 1 || h->opt.gs_flow < -1 ||
-        h->opt.gs_flow > 1 || h->opt.gs_stream < -1 || h->opt.gs_stream > 8)
+        h->opt.gs_flow > 1 || h->opt.gs_stream < -1 || h->opt.gs_stream > 8 ||
+        h->opt.gs_tma < -1 || h->opt.gs_tma > 1)
       fail(AMG_ERR_INVALID, "option out of range");
     // post-smoothing colour order: the stand-alone iteration sweeps the colours in the
     // pre-smoothing order, a Krylov method gets the symmetric (reversed) order
@@ -234,10 +236,16 @@ static void fill_stats(amg_handle* h, amg_stats* st) {
                                 (int)l >= (h->sub_from > 0 ? h->sub_from : AMG_MAX_LEVELS))
                                    ? 0
                                    : h->L[l]->gs_stream;
+      st->level_gs_tma[l] = st->level_gs_stream[l] > 0 ? 0
+                            : (h->use_full || h->L[l]->gs_cl > 0 || st->level_gs_flow[l] > 0 ||
+                               (int)l >= (h->sub_from > 0 ? h->sub_from : AMG_MAX_LEVELS))
+                                  ? 0
+                                  : h->L[l]->gs_tma;
     } else {
       st->level_gs_cluster[l] = 0;
       st->level_gs_flow[l] = 0;
       st->level_gs_stream[l] = 0;
+      st->level_gs_tma[l] = 0;
       st->level_nodes[l] = st->level_pres[l] = st->level_colours[l] = 0;
       st->level_group[l] = 0;
       st->level_nnzb[l] = 0;

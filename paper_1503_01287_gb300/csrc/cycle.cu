@@ -483,6 +483,8 @@ struct Phase {
   int sctas;              // PH_ROWS, Gauss-Seidel: CTAs per SM of the streaming colour
                           // kernel (0: one group of lanes per row, k_gs_pdl)
   int xnc;                // PH_ROWS, Gauss-Seidel (k_gs_pdl): x through the L1 path
+  int tma;                // PH_ROWS, Gauss-Seidel, FP32: the TMA-staged colour kernel
+  int* err;               // the handle's error word (bounded waits that gave up)
   const long long* off;   // PH_VANKA: offsets of the patch inverses
 };
 
@@ -1460,6 +1462,206 @@ void launch_gs_stream(const Phase& P, cudaStream_t s) {
                               (const T*)P.dinv, P.wt));
 }
 
+// ------------------------------------------------- TMA-staged colour kernel (FP32)
+
+// The colour kernel with the block values and columns of a CTA's rows staged in shared
+// memory by 1-D bulk copies (cp.async.bulk, the TMA's linear mode), issued before
+// griddepcontrol.wait since they are setup constants.  A colour's rows are consecutive
+// in the kernel layout, so the blocks of a CTA's R = 256 / G rows are one range [A, E)
+// of each of the 9 value planes and of the column array.  The copies hold no registers:
+// more rows are in flight per SM than with k_gs_pdl's register prefetch, whose
+// registers cap its occupancy.  Up to kTmaBlocksPerRow * R blocks are staged; blocks
+// beyond that (rows far longer than a level's average) are read from global memory.
+// A plane's copy starts at the 16-byte boundary at or below its first element and
+// ends at the boundary at or below its last; the up to 3 elements after that are
+// loaded by threads.  A row's sums run in k_gs_pdl's order for the same G (lane gl
+// takes blocks a + gl, a + gl + G, ...), so both kernels give the same bits.  The
+// one mbarrier wait is bounded: a CTA that gives up sets *err, waits (bounded) once
+// more for its copies and returns.
+constexpr int kTmaBlocksPerRow = 36;
+constexpr unsigned kTmaSpins = 1u << 20;
+template <int G>
+constexpr int tma_cap() { return (256 / G) * kTmaBlocksPerRow; }   // a multiple of 4
+template <int G>
+constexpr int tma_smem() { return 10 * (tma_cap<G>() + 4) * (int)sizeof(float); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool tma_wait(uint32_t bar) {
+  for (unsigned i = 0; i < kTmaSpins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int G, bool XNC>
+__global__ void __launch_bounds__(256) k_gs_tma(int nrows, const int* __restrict__ rows,
+                                                const int* __restrict__ rowptr,
+                                                const int* __restrict__ col,
+                                                const float* __restrict__ val, int64_t nnzb,
+                                                float* x, const float* __restrict__ b,
+                                                const float* __restrict__ dinv,
+                                                const double* __restrict__ wt,
+                                                int* __restrict__ err) {
+  extern __shared__ __align__(128) float tma_sm[];
+  __shared__ __align__(8) uint64_t tbar;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int R = 256 / G;
+  constexpr int CAP = tma_cap<G>();
+  constexpr int PL = CAP + 4;                  // plane stride in shared memory
+  const int g0 = blockIdx.x * R;
+  const int g1 = min(g0 + R, nrows);
+  const int A = __ldg(rowptr + g0), E = __ldg(rowptr + g1);
+  const int Es = min(E, A + CAP);              // staged blocks [A, Es)
+  const uint32_t bar = smem_addr(&tbar);
+  const uint32_t sm0 = smem_addr(tma_sm);
+  // plane p: values p < 9 (element base p * nnzb of val), the columns p = 9 (base 0 of
+  // col); global elements [fs, fe) by bulk copy, fs = floor4(base + A),
+  // fe = floor4(base + Es); block k sits at position k - A + (base + A - fs)
+  if (threadIdx.x == 0) {
+    mbar_init(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();   // the barrier is initialised before any thread polls it
+  if (threadIdx.x == 0) {
+    uint32_t total = 0;
+    for (int p = 0; p < 10; ++p) {
+      const int64_t base = p < 9 ? (int64_t)p * nnzb : 0;
+      const int64_t fs = (base + A) & ~int64_t(3), fe = (base + Es) & ~int64_t(3);
+      if (fe > fs) total += (uint32_t)(fe - fs) * 4u;
+    }
+    mbar_expect(bar, total);
+    for (int p = 0; p < 10; ++p) {
+      const int64_t base = p < 9 ? (int64_t)p * nnzb : 0;
+      const int64_t fs = (base + A) & ~int64_t(3), fe = (base + Es) & ~int64_t(3);
+      const float* src = p < 9 ? val + fs : reinterpret_cast<const float*>(col) + fs;
+      if (fe > fs) bulk_g2s(sm0 + (uint32_t)(p * PL) * 4u, src, (uint32_t)(fe - fs) * 4u, bar);
+    }
+  }
+  // the tails: at most 3 elements a plane past the last 16-byte boundary
+  if (threadIdx.x < 40) {
+    const int p = threadIdx.x >> 2, t = threadIdx.x & 3;
+    const int64_t base = p < 9 ? (int64_t)p * nnzb : 0;
+    const int64_t gs = base + A, ge = base + Es;
+    const int64_t fs = gs & ~int64_t(3), fe = ge & ~int64_t(3);
+    const int64_t idx = (fe > gs ? fe : gs) + t;
+    if (idx < ge) {
+      const float* src = p < 9 ? val : reinterpret_cast<const float*>(col);
+      tma_sm[p * PL + (int)(idx - fs)] = __ldg(src + idx);
+    }
+  }
+  const int g = g0 + (int)(threadIdx.x / G);
+  const int gl = threadIdx.x & (G - 1);
+  const bool active = g < g1;
+  int i = 0, a = 0, e = 0;
+  float d[9];
+  if (active) {
+    i = __ldg(rows + g);
+    a = __ldg(rowptr + g);
+    e = __ldg(rowptr + g + 1);
+    if (gl == 0) {
+      const float* dp = dinv + 12 * (int64_t)i;
+      ld3(dp, 0, d[0], d[1], d[2]);
+      ld3(dp, 1, d[3], d[4], d[5]);
+      ld3(dp, 2, d[6], d[7], d[8]);
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const bool ok = tma_wait(bar);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      tma_wait(bar);
+    }
+    return;
+  }
+  const float om = wt ? (float)wt[0] : 1.f;   // learned relaxation multiplier (1: plain)
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f, xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
+  if (active) {
+    if (gl == 0) {
+      ld3(b, i, b0, b1, b2);
+      VL<!XNC>::node(x, i, xi0, xi1, xi2);
+    }
+    int off[10];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      const int64_t base = p < 9 ? (int64_t)p * nnzb : 0;
+      off[p] = p * PL + (int)((base + A) & 3) - A;   // position of block k: k + off[p]
+    }
+    for (int k = a + gl; k < e; k += G) {
+      int jj;
+      float v[9];
+      if (k < Es) {
+        jj = __float_as_int(tma_sm[k + off[9]]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] = tma_sm[k + off[q]];
+      } else {
+        jj = __ldg(col + k);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] = __ldg(val + q * nnzb + k);
+      }
+      float x0, x1, x2;
+      VL<!XNC>::node(x, jj, x0, x1, x2);
+      s0 = fmaf(v[0], x0, s0); s0 = fmaf(v[1], x1, s0); s0 = fmaf(v[2], x2, s0);
+      s1 = fmaf(v[3], x0, s1); s1 = fmaf(v[4], x1, s1); s1 = fmaf(v[5], x2, s1);
+      s2 = fmaf(v[6], x0, s2); s2 = fmaf(v[7], x1, s2); s2 = fmaf(v[8], x2, s2);
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (!active || gl != 0) return;
+  const float r0 = b0 - s0, r1 = b1 - s1, r2 = b2 - s2;
+  st3(x, i, xi0 + om * (d[0] * r0 + d[1] * r1 + d[2] * r2),
+      xi1 + om * (d[3] * r0 + d[4] * r1 + d[5] * r2), xi2 + om * (d[6] * r0 + d[7] * r1 + d[8] * r2));
+}
+
+template <int G, bool XNC>
+void launch_gs_tma_x(const Phase& P, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    AMG_CUDA(cudaFuncSetAttribute(k_gs_tma<G, XNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tma_smem<G>()));
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(((int64_t)P.n * G + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = tma_smem<G>();
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_gs_tma<G, XNC>, P.n, P.rows, P.rowptr, P.col,
+                              (const float*)P.val, P.nnz, (float*)P.y, (const float*)P.b,
+                              (const float*)P.dinv, P.wt, P.err));
+}
+
+template <int G>
+void launch_gs_tma(const Phase& P, cudaStream_t s) {
+  if (P.xnc) launch_gs_tma_x<G, true>(P, s);
+  else launch_gs_tma_x<G, false>(P, s);
+}
+
 template <typename T, typename V>
 void launch_rows_v(const Phase& P, cudaStream_t s, bool pdl) {
   if constexpr (std::is_same<T, V>::value) {
@@ -1469,6 +1671,16 @@ void launch_rows_v(const Phase& P, cudaStream_t s, bool pdl) {
         case 8: launch_gs_stream<T, 8>(P, s); return;
         case 16: launch_gs_stream<T, 16>(P, s); return;
         default: launch_gs_stream<T, 32>(P, s); return;
+      }
+    }
+  }
+  if constexpr (std::is_same<T, float>::value && std::is_same<V, float>::value) {
+    if (pdl && P.mode == kGS && P.rows && P.tma && P.n > 0) {
+      switch (P.G) {
+        case 4: launch_gs_tma<4>(P, s); return;
+        case 8: launch_gs_tma<8>(P, s); return;
+        case 16: launch_gs_tma<16>(P, s); return;
+        default: launch_gs_tma<32>(P, s); return;
       }
     }
   }
@@ -1685,6 +1897,8 @@ struct Emit {
     P.val = val; P.nnz = lv.nnzb; P.x = x; P.b = b; P.y = y; P.dinv = dinv; P.omega = omega;
     P.sctas = mode == kGS ? lv.gs_stream : 0;
     P.xnc = mode == kGS ? lv.gs_xnc : 0;
+    P.tma = mode == kGS ? lv.gs_tma : 0;
+    P.err = h->flag.p;
     if (sizeof(T) == 4 && lv.val16.p && (const void*)val == (const void*)lv.val32.p) {
       P.val = lv.val16.p;   // BF16 storage of this level's values
       P.vbf = 1;
@@ -2364,6 +2578,26 @@ void autotune_levels(amg_handle* h) {
       }
       lv.gs_stream = c_best;
       lv.group_gs = c_best ? g_best : g_keep;
+    }
+    // the TMA-staged colour kernel (FP32 values): forced with the chain's lanes per row
+    // (gs_tma = 1), else kept with the fastest lanes per row if it beats the chain
+    lv.gs_tma = 0;
+    if (f32 && !lv.val16.p && lv.gs_stream == 0 && h->opt.gs_tma != 0) {
+      if (h->opt.gs_tma > 0) {
+        lv.gs_tma = 1;
+      } else {
+        float t_best = sweep_ms();
+        int g_best = 0;
+        const int g_keep = lv.group_gs;
+        for (int G : {4, 8, 16, 32}) {
+          lv.group_gs = G;
+          lv.gs_tma = 1;
+          const float t = sweep_ms();
+          if (t < t_best) { t_best = t; g_best = G; }
+        }
+        lv.gs_tma = g_best ? 1 : 0;
+        lv.group_gs = g_best ? g_best : g_keep;
+      }
     }
     // the sweep as one dataflow launch: forced on with the chain's lanes per row
     // (gs_flow = 1), or the fastest lanes per row if it beats the colour chain
