@@ -78,14 +78,19 @@ __global__ void k_mdot_final(const double* __restrict__ partial, int nblk, int m
 // four FP64 FMAs per basis entry and step the sweep was bound by them, far below
 // the memory bandwidth.  Only each warp's final sums are converted to FP64.
 //
-// The basis streams through shared memory: one thread of a CTA issues 1-D bulk
-// copies (cp.async.bulk, the TMA's linear mode) of kTile-entry pieces of the rows
-// into a ring of kStages stages, each completing on its own mbarrier; all threads
-// wait for a stage's phase, use it, and pass a __syncthreads before it is refilled.
-// The copies run ahead of the arithmetic by up to kStages stages, so the memory
-// latency is hidden without holding loads in registers.  Every wait is bounded: a
-// CTA that gives up waits (bounded) for its copies in flight, sets *err and returns.
-constexpr int kTile = 256;                 // entries of a row piece (2 KB of pairs) = CTA size
+// The basis streams through shared memory in a ring of kStages stages, filled by a
+// producer warp with 1-D bulk copies (cp.async.bulk, the TMA's linear mode) of
+// kTile-entry pieces of the rows.  Each stage has two mbarriers: "full" completes when
+// the stage's bytes have landed; "empty" completes when each of the kConsumers
+// consumer warps has arrived on it after using the stage.  The producer refills a
+// stage once it is empty, so the copies run ahead of the arithmetic by up to kStages
+// stages and a consumer warp waits only for its own next stage, never for the other
+// warps.  Every wait is bounded: a warp that gives up raises the CTA's abort flag
+// and *err, the others stop at their next wait, and the producer waits (bounded) for
+// its copies in flight before the CTA returns.
+constexpr int kTile = 256;                 // entries of a row piece (2 KB of pairs)
+constexpr int kConsumers = kTile / 32;     // consumer warps: one entry a thread
+constexpr int kThreads = kTile + 32;       // and one producer warp
 constexpr int kPieces = 10;                // pieces a stage: up to 8 basis rows, u and w
 constexpr int kStages = 4;
 constexpr unsigned kBulkSpins = 1u << 20;
@@ -94,8 +99,12 @@ constexpr int kStreamSmem = kStages * kPieces * kTile * (int)sizeof(float2);   /
 __device__ __forceinline__ uint32_t sm_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void bar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(b)) : "memory");
+__device__ __forceinline__ void bar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(b)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(b)) : "memory");
 }
 __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(b)),
@@ -126,12 +135,60 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t par) {
   }
   return false;
 }
-// after a wait gave up at load q: wait (bounded) for loads q .. q + kStages - 1 of nq
-// that may still be in flight, then flag the error
-__device__ void ring_drain(uint64_t* bar, int64_t q, int64_t nq, int* err) {
-  for (int64_t d = q; d < q + kStages && d < nq; ++d)
-    bar_wait(&bar[d % kStages], (uint32_t)((d / kStages) & 1));
-  atomicExch(err, 1);
+// The ring of one CTA: full and empty mbarriers a stage and the abort flag.
+struct Ring {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  int abort;
+};
+__device__ __forceinline__ void ring_init(Ring& r) {
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      bar_init(&r.full[st], 1);
+      bar_init(&r.empty[st], kConsumers);
+    }
+    r.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+// The producer loop (lane 0 of the last warp): load q goes to stage q % kStages once
+// the consumers have emptied that stage's previous load; issue(st, q) posts the
+// expected bytes on full[st] and starts the copies.  At the end it waits (bounded) for
+// the last loads' copies, which are all that can still be in flight.
+template <typename Issue>
+__device__ void ring_produce(Ring& r, int64_t nq, int* err, Issue issue) {
+  int64_t q = 0;
+  for (; q < nq; ++q) {
+    const int st = (int)(q % kStages);
+    if (q >= kStages &&
+        !bar_wait(&r.empty[st], (uint32_t)(((q / kStages) - 1) & 1))) {
+      atomicExch(&r.abort, 1);
+      atomicExch(err, 1);
+      break;
+    }
+    if (*(volatile int*)&r.abort) break;
+    issue(st, q);
+  }
+  for (int64_t d = q > kStages ? q - kStages : 0; d < q; ++d)
+    bar_wait(&r.full[d % kStages], (uint32_t)((d / kStages) & 1));
+}
+// A consumer warp's wait for load q, called by all its lanes; false in every lane
+// (abort raised) if a lane gave up or another warp did.
+__device__ __forceinline__ bool ring_wait(Ring& r, int64_t q, int* err) {
+  bool ok = *(volatile int*)&r.abort == 0;
+  if (ok) ok = bar_wait(&r.full[q % kStages], (uint32_t)((q / kStages) & 1));
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok && (threadIdx.x & 31) == 0) {
+    atomicExch(&r.abort, 1);
+    atomicExch(err, 1);
+  }
+  return ok;
+}
+// A consumer warp is done with load q's stage.
+__device__ __forceinline__ void ring_release(Ring& r, int64_t q) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) bar_arrive(&r.empty[q % kStages]);
 }
 __device__ __forceinline__ uint32_t piece_bytes(int64_t ld, int64_t k0) {
   return (uint32_t)(min((int64_t)kTile, ld - k0) * (int64_t)sizeof(float2));
@@ -140,80 +197,76 @@ __device__ __forceinline__ uint32_t piece_bytes(int64_t ld, int64_t k0) {
 // partial[(blockIdx.x * rows + i) * 2 + {0, 1}] = sum over the tiles of block column
 // blockIdx.x of V_i[k] u[k] and V_i[k] w[k], kMdotG rows per block row (blockIdx.y).
 // Rows are ld entries apart; the entries from n to ld are padding (copied, not used).
-__global__ void __launch_bounds__(kTile) k_mdot2(int64_t n, int64_t ld, int rows,
-                                                 const float2* __restrict__ V,
-                                                 const float2* __restrict__ u,
-                                                 const float2* __restrict__ w,
-                                                 double* __restrict__ partial,
-                                                 int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 2) k_mdot2(int64_t n, int64_t ld, int rows,
+                                                    const float2* __restrict__ V,
+                                                    const float2* __restrict__ u,
+                                                    const float2* __restrict__ w,
+                                                    double* __restrict__ partial,
+                                                    int* __restrict__ err) {
   extern __shared__ __align__(128) float2 ring[];
-  __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ double sh[2 * kMdotG][kTile / 32];
+  __shared__ Ring R;
+  __shared__ double sh[2 * kMdotG][kConsumers];
   const int i0 = blockIdx.y * kMdotG;
   const int gn = min(kMdotG, rows - i0);
   const int64_t ntiles = (n + kTile - 1) / kTile;
   const int64_t nq = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  auto issue = [&](int st, int64_t q) {
-    const int64_t k0 = (blockIdx.x + q * gridDim.x) * kTile;
-    const uint32_t bytes = piece_bytes(ld, k0);
-    bar_expect(&bar[st], bytes * (gn + 2));
-    float2* dst = ring + (size_t)st * kPieces * kTile;
-    for (int g = 0; g < gn; ++g)
-      bulk_load(dst + g * kTile, V + (int64_t)(i0 + g) * ld + k0, bytes, &bar[st]);
-    bulk_load(dst + 8 * kTile, u + k0, bytes, &bar[st]);
-    bulk_load(dst + 9 * kTile, w + k0, bytes, &bar[st]);
-  };
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) bar_init(&bar[st]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int st = 0; st < kStages && st < nq; ++st) issue(st, st);
+  ring_init(R);
   float Su[kMdotG], su[kMdotG], Sw[kMdotG], sw[kMdotG];
 #pragma unroll
   for (int g = 0; g < kMdotG; ++g) Su[g] = su[g] = Sw[g] = sw[g] = 0.f;
-  for (int64_t q = 0; q < nq; ++q) {
-    const int st = (int)(q % kStages);
-    const bool ok = bar_wait(&bar[st], (uint32_t)((q / kStages) & 1));
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) ring_drain(bar, q, nq, err);
-      return;
-    }
-    const float2* sg = ring + (size_t)st * kPieces * kTile;
-    const int64_t k = (blockIdx.x + q * gridDim.x) * kTile + threadIdx.x;
-    if (k < n) {
-      const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
+  if (threadIdx.x >= kTile) {
+    if (threadIdx.x == kTile)
+      ring_produce(R, nq, err, [&](int st, int64_t q) {
+        const int64_t k0 = (blockIdx.x + q * gridDim.x) * kTile;
+        const uint32_t bytes = piece_bytes(ld, k0);
+        bar_expect(&R.full[st], bytes * (gn + 2));
+        float2* dst = ring + (size_t)st * kPieces * kTile;
+        for (int g = 0; g < gn; ++g)
+          bulk_load(dst + g * kTile, V + (int64_t)(i0 + g) * ld + k0, bytes, &R.full[st]);
+        bulk_load(dst + 8 * kTile, u + k0, bytes, &R.full[st]);
+        bulk_load(dst + 9 * kTile, w + k0, bytes, &R.full[st]);
+      });
+  } else {
+    for (int64_t q = 0; q < nq; ++q) {
+      if (!ring_wait(R, q, err)) break;
+      const float2* sg = ring + (size_t)(q % kStages) * kPieces * kTile;
+      const int64_t k = (blockIdx.x + q * gridDim.x) * kTile + threadIdx.x;
+      if (k < n) {
+        const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
 #pragma unroll
-      for (int g = 0; g < kMdotG; ++g) {
-        if (g < gn) {
-          const float2 v = sg[g * kTile + threadIdx.x];
-          pair_fma(Su[g], su[g], v, uk.x, uk.y);
-          pair_fma(Sw[g], sw[g], v, wk.x, wk.y);
+        for (int g = 0; g < kMdotG; ++g) {
+          if (g < gn) {
+            const float2 v = sg[g * kTile + threadIdx.x];
+            pair_fma(Su[g], su[g], v, uk.x, uk.y);
+            pair_fma(Sw[g], sw[g], v, wk.x, wk.y);
+          }
         }
       }
+      ring_release(R, q);
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && q + kStages < nq) issue(st, q + kStages);
   }
-  // the sums of a warp in pair arithmetic, then in FP64 across the warps
+  __syncthreads();
+  // the sums of a warp in pair arithmetic, then in FP64 across the consumer warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < kConsumers) {
 #pragma unroll
-  for (int q = 0; q < 2 * kMdotG; ++q) {
-    float S = q < kMdotG ? Su[q] : Sw[q - kMdotG];
-    float e = q < kMdotG ? su[q] : sw[q - kMdotG];
+    for (int q = 0; q < 2 * kMdotG; ++q) {
+      float S = q < kMdotG ? Su[q] : Sw[q - kMdotG];
+      float e = q < kMdotG ? su[q] : sw[q - kMdotG];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float T = __shfl_xor_sync(0xffffffffu, S, o), t = __shfl_xor_sync(0xffffffffu, e, o);
-      pair_add(S, e, T, t);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float T = __shfl_xor_sync(0xffffffffu, S, o);
+        const float t = __shfl_xor_sync(0xffffffffu, e, o);
+        pair_add(S, e, T, t);
+      }
+      if (lane == 0) sh[q][wid] = (double)S + (double)e;
     }
-    if (lane == 0) sh[q][wid] = (double)S + (double)e;
   }
   __syncthreads();
   const int g = threadIdx.x >> 1, d = threadIdx.x & 1;
-  if (g < gn) {
+  if (threadIdx.x < 2 * kMdotG && g < gn) {
     double t = 0.0;
-    for (int q = 0; q < kTile / 32; ++q) t += sh[d * kMdotG + g][q];
+    for (int q = 0; q < kConsumers; ++q) t += sh[d * kMdotG + g][q];
     partial[(blockIdx.x * (int64_t)rows + i0 + g) * 2 + d] = t;
   }
 }
@@ -262,16 +315,18 @@ __global__ void k_dcgs2_coef(int m, double* __restrict__ coef) {
 // vector before its normalisation; partial[blockIdx.x] = the block's sum of w'^2.
 // A CTA takes tiles of kTile entries (one a thread); a tile's rows stream through
 // the ring eight at a time, u and w with the first eight.
-__global__ void __launch_bounds__(kTile) k_dcgs2_update(int64_t n, int64_t ld, int m,
-                                                        const float2* __restrict__ V, float2* u,
-                                                        const float2* __restrict__ w, float2* wn,
-                                                        const double* __restrict__ coef,
-                                                        double* __restrict__ partial,
-                                                        int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 2) k_dcgs2_update(int64_t n, int64_t ld, int m,
+                                                           const float2* __restrict__ V,
+                                                           float2* u,
+                                                           const float2* __restrict__ w,
+                                                           float2* wn,
+                                                           const double* __restrict__ coef,
+                                                           double* __restrict__ partial,
+                                                           int* __restrict__ err) {
   extern __shared__ __align__(128) float2 ring[];
-  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ Ring R;
   __shared__ float2 cp[kMaxDots], cq[kMaxDots];   // -p_i and -q_i as pairs
-  __shared__ double sh[32];
+  __shared__ double sh[kConsumers];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     cp[i] = to_pair(-coef[i]);
     cq[i] = to_pair(-coef[kMaxDots + i]);
@@ -282,67 +337,79 @@ __global__ void __launch_bounds__(kTile) k_dcgs2_update(int64_t n, int64_t ld, i
   const int64_t ntiles = (n + kTile - 1) / kTile;
   const int64_t my = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t nq = my * nch;
-  auto issue = [&](int st, int64_t q) {
-    const int64_t k0 = (blockIdx.x + (q / nch) * gridDim.x) * kTile;
-    const int c = (int)(q % nch);
-    const int r0 = 8 * c, rn = max(0, min(8, m - r0));
-    const uint32_t bytes = piece_bytes(ld, k0);
-    bar_expect(&bar[st], bytes * (rn + (c == 0 ? 2 : 0)));
-    float2* dst = ring + (size_t)st * kPieces * kTile;
-    for (int r = 0; r < rn; ++r)
-      bulk_load(dst + r * kTile, V + (int64_t)(r0 + r) * ld + k0, bytes, &bar[st]);
-    if (c == 0) {
-      bulk_load(dst + 8 * kTile, u + k0, bytes, &bar[st]);
-      bulk_load(dst + 9 * kTile, w + k0, bytes, &bar[st]);
-    }
-  };
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) bar_init(&bar[st]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int st = 0; st < kStages && st < nq; ++st) issue(st, st);
-  float Sv = 0.f, sv = 0.f, Sw = 0.f, sw = 0.f, Sn = 0.f, sn = 0.f;
-  for (int64_t q = 0; q < nq; ++q) {
-    const int st = (int)(q % kStages);
-    const bool ok = bar_wait(&bar[st], (uint32_t)((q / kStages) & 1));
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) ring_drain(bar, q, nq, err);
-      return;
-    }
-    const float2* sg = ring + (size_t)st * kPieces * kTile;
-    const int c = (int)(q % nch);
-    if (c == 0) {
-      const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
-      Sv = uk.x; sv = uk.y; Sw = wk.x; sw = wk.y;
-    }
-    const int r0 = 8 * c, rn = min(8, m - r0);
+  ring_init(R);   // also orders the coefficient stores before their use
+  float Sn = 0.f, sn = 0.f;
+  if (threadIdx.x >= kTile) {
+    if (threadIdx.x == kTile)
+      ring_produce(R, nq, err, [&](int st, int64_t q) {
+        const int64_t k0 = (blockIdx.x + (q / nch) * gridDim.x) * kTile;
+        const int c = (int)(q % nch);
+        const int r0 = 8 * c, rn = max(0, min(8, m - r0));
+        const uint32_t bytes = piece_bytes(ld, k0);
+        bar_expect(&R.full[st], bytes * (rn + (c == 0 ? 2 : 0)));
+        float2* dst = ring + (size_t)st * kPieces * kTile;
+        for (int r = 0; r < rn; ++r)
+          bulk_load(dst + r * kTile, V + (int64_t)(r0 + r) * ld + k0, bytes, &R.full[st]);
+        if (c == 0) {
+          bulk_load(dst + 8 * kTile, u + k0, bytes, &R.full[st]);
+          bulk_load(dst + 9 * kTile, w + k0, bytes, &R.full[st]);
+        }
+      });
+  } else {
+    // even and odd rows of a chunk in separate sums: two independent chains each
+    float Sv = 0.f, sv = 0.f, Sw = 0.f, sw = 0.f, Tv = 0.f, tv = 0.f, Tw = 0.f, tw = 0.f;
+    for (int64_t q = 0; q < nq; ++q) {
+      if (!ring_wait(R, q, err)) break;
+      const float2* sg = ring + (size_t)(q % kStages) * kPieces * kTile;
+      const int c = (int)(q % nch);
+      if (c == 0) {
+        const float2 uk = sg[8 * kTile + threadIdx.x], wk = sg[9 * kTile + threadIdx.x];
+        Sv = uk.x; sv = uk.y; Sw = wk.x; sw = wk.y;
+        Tv = tv = Tw = tw = 0.f;
+      }
+      const int r0 = 8 * c, rn = min(8, m - r0);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      if (r < rn) {
-        const float2 v = sg[r * kTile + threadIdx.x];
-        pair_fma(Sv, sv, cp[r0 + r], v.x, v.y);
-        pair_fma(Sw, sw, cq[r0 + r], v.x, v.y);
+      for (int r = 0; r < 8; r += 2) {
+        if (r < rn) {
+          const float2 v = sg[r * kTile + threadIdx.x];
+          pair_fma(Sv, sv, cp[r0 + r], v.x, v.y);
+          pair_fma(Sw, sw, cq[r0 + r], v.x, v.y);
+        }
+        if (r + 1 < rn) {
+          const float2 v = sg[(r + 1) * kTile + threadIdx.x];
+          pair_fma(Tv, tv, cp[r0 + r + 1], v.x, v.y);
+          pair_fma(Tw, tw, cq[r0 + r + 1], v.x, v.y);
+        }
+      }
+      ring_release(R, q);
+      const int64_t k = (blockIdx.x + (q / nch) * gridDim.x) * kTile + threadIdx.x;
+      if (c == nch - 1 && k < n) {
+        pair_add(Sv, sv, Tv, tv);
+        pair_add(Sw, sw, Tw, tw);
+        const float2 a = norm_pair(Sv, sv);
+        float P = 0.f, pl = 0.f;
+        pair_fma(P, pl, inv_s, a.x, a.y);
+        const float2 vk = norm_pair(P, pl);
+        u[k] = vk;
+        pair_fma(Sw, sw, hneg, vk.x, vk.y);
+        const float2 wk2 = norm_pair(Sw, sw);
+        wn[k] = wk2;
+        pair_fma(Sn, sn, wk2, wk2.x, wk2.y);
       }
     }
-    const int64_t k = (blockIdx.x + (q / nch) * gridDim.x) * kTile + threadIdx.x;
-    if (c == nch - 1 && k < n) {
-      const float2 a = norm_pair(Sv, sv);
-      float P = 0.f, pl = 0.f;
-      pair_fma(P, pl, inv_s, a.x, a.y);
-      const float2 vk = norm_pair(P, pl);
-      u[k] = vk;
-      pair_fma(Sw, sw, hneg, vk.x, vk.y);
-      const float2 wk2 = norm_pair(Sw, sw);
-      wn[k] = wk2;
-      pair_fma(Sn, sn, wk2, wk2.x, wk2.y);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && q + kStages < nq) issue(st, q + kStages);
   }
-  const double t = block_sum((double)Sn + (double)sn, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  __syncthreads();
+  double t = (double)Sn + (double)sn;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0 && wid < kConsumers) sh[wid] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < kConsumers; ++q) sum += sh[q];
+    partial[blockIdx.x] = sum;
+  }
 }
 
 // v *= 1 / sqrt(nrm2[0]) (0 if the norm is 0) in pair arithmetic, also written to v2 as
@@ -777,7 +844,7 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   auto mdot2 = [&](int rows, const float2* u, const float2* wv) {
     const int grows = (rows + kMdotG - 1) / kMdotG;
     const int cols = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms / grows, ntiles));
-    k_mdot2<<<dim3(cols, grows), kTile, kStreamSmem, s>>>(n, ld, rows, V, u, wv, h->red,
+    k_mdot2<<<dim3(cols, grows), kThreads, kStreamSmem, s>>>(n, ld, rows, V, u, wv, h->red,
                                                           h->flag.p);
     k_mdot_final<<<(2 * rows + 7) / 8, 256, 0, s>>>(h->red, cols, rows, 2, kMaxDots, coef.p);
     h->launches += 2;
@@ -891,7 +958,7 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
         mdot2(j + 1, uj, wp);
         k_dcgs2_coef<<<1, 32, 0, s>>>(j, coef.p);
         float2* un = V + (int64_t)(j + 1) * ld;
-        k_dcgs2_update<<<ublocks, kTile, kStreamSmem, s>>>(n, ld, j, V, uj, wp, un, coef.p,
+        k_dcgs2_update<<<ublocks, kThreads, kStreamSmem, s>>>(n, ld, j, V, uj, wp, un, coef.p,
                                                            h->red, h->flag.p);
         k_final<<<1, 256, 0, s>>>(h->red, ublocks, 1, coef.p + kS + 3);
         k_scale_norm<<<gridr(n), 256, 0, s>>>(n, un, ur, coef.p + kS + 3);
