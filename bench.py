@@ -929,7 +929,7 @@ def run_batched(args):
                    "dof_total": summ["dof_total"], "rhs": args.rhs, "tol": TOL},
         "iterations": summ["iterations"], "true_rel_residual_max": summ["true_rel_residual_max"],
         "converged": summ["converged"], "setup_s": summ["setup_s"], "generate_s": gen_s,
-        "graph_launches_per_step": 1, "gpu_launches": summ["gpu_launches"],
+        "graph_launches_per_step": summ["problems"], "gpu_launches": summ["gpu_launches"],
         "plain_fp64_per_rhs": plain,
     }
     print(json.dumps(line), flush=True)

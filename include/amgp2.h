@@ -162,10 +162,14 @@ typedef struct amg_options {
                                launches (cluster_from 0, cycle_kernel 1)        */
   double omega;             /* block Jacobi damping (default 0.5)               */
   double omega_p;           /* sGS pressure step omega (default 0.125)          */
-  int32_t batch_tile;       /* amg_solve_batched: tile of the SpMM row kernels,
-                               -1 chosen per level by timing (default); 0..3 =
-                               (lane groups per row, blocks unrolled) of (1,2),
-                               (2,2), (1,4), (2,4)                              */
+  int32_t batch_tile;       /* amg_solve_batched: tile of the SpMM row kernels
+                               and of the colour kernels, -1 chosen per level by
+                               timing the SpMM (default; the colour kernels take
+                               the same tile); t =
+                               0..7 forces (lane groups per row, blocks
+                               unrolled) = (1,2), (2,2), (1,4), (2,4), (4,2),
+                               (8,2), (4,4), (8,4) on the colour kernels and
+                               tile t mod 4 on the SpMM row kernels             */
   int32_t gs_cluster;       /* multicolour Gauss-Seidel sweep of a level whose
                                iterate, right-hand side and row offsets fit in
                                shared memory (SPD kinds, up to about 5000 nodes

@@ -197,6 +197,7 @@ struct BatchLevel {
   int tile = 0;     // block-row tile of the cycle's SpMM kernels (chosen by timing)
   int tile64 = 0;   // the same for the FP64 operator (level 0)
   int tile_pair = 0;   // the same for the FP32-pair operator (level 0)
+  int tile_gs = 0;     // tile of the multi-right-hand-side colour kernel
 };
 
 }  // namespace amgp2

@@ -292,14 +292,18 @@ __global__ void k_dots_m(int64_t nel, int nd, const double* a0, const double* b0
   (void)rr;
 }
 
+// out[d * K + r] = sum over b < nblk of partial[(b * nd + d) * K + r]: one warp per
+// (d, r) (block d * K + r), lanes over b, then a fixed shuffle tree (deterministic)
 __global__ void k_final_m(const double* __restrict__ partial, int nblk, int nd,
                           double* __restrict__ out) {
-  const int t = threadIdx.x;   // nd * K threads
+  const int t = blockIdx.x;
   if (t >= nd * K) return;
   const int d = t / K, r = t % K;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(b * nd + d) * K + r];
-  out[d * K + r] = s;
+  for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(b * nd + d) * K + r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[d * K + r] = s;
 }
 
 // scalar slots, each K wide
@@ -426,6 +430,8 @@ template <> struct MV<float> {
 };
 
 constexpr int kTiles = 4;   // tile t: S = 1 + (t & 1), U = (t & 2) ? 4 : 2
+constexpr int kGsTiles = 8; // colour kernel: tiles 0..3 as above, 4..7: S = 4 << (t & 1),
+                            // U = (t & 2) ? 4 : 2
 
 // One colour of the multicolour Gauss-Seidel sweep for all right-hand sides,
 // launched with programmatic dependent launch: the row's ids, the column indices
@@ -433,7 +439,8 @@ constexpr int kTiles = 4;   // tile t: S = 1 + (t & 1), U = (t & 2) ? 4 : 2
 // no cycle kernel writes) are loaded before griddepcontrol.wait, so this prologue
 // runs under the previous kernel; b, the relaxation multiplier and the x gathers
 // come after the wait, which is where the previous kernel's writes become
-// visible.  Tile as in k_rows_m.
+// visible.  Tiles as in k_rows_m, and with S = 4 or 8 lane groups a row (2 or 4 warps,
+// their sums combined in shared memory) for rows whose dependent block chain is long.
 template <typename T, int S, int U>
 __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restrict__ rows,
                                                   const int* __restrict__ rowptr,
@@ -442,6 +449,8 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ dinv,
                                                   const double* __restrict__ wt) {
+  // S > 2: the S / 2 warps of a row combine their sums through shared memory
+  __shared__ T red[S > 2 ? 256 / 32 : 1][K][3];
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) / (K * S);
   const int q = (threadIdx.x / K) % S;
@@ -477,9 +486,9 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
   // the right-hand side and the multiplier may be written by the previous kernel
   // (the restriction before a sweep's first colour): read only after the wait
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (!active) return;
+  if (S <= 2 && !active) return;   // S > 2: every thread reaches the block barrier below
   const T om = wt ? (T)wt[0] : T(1);   // learned relaxation multiplier (1: plain)
-  if (q == 0) ld3(b, i * K + r, b0, b1, b2);
+  if (active && q == 0) ld3(b, i * K + r, b0, b1, b2);
   T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
     s1 = fma(v[u][3], x0, s1); s1 = fma(v[u][4], x1, s1); s1 = fma(v[u][5], x2, s1);
     s2 = fma(v[u][6], x0, s2); s2 = fma(v[u][7], x1, s2); s2 = fma(v[u][8], x2, s2);
   }
-  for (int k = a + q + U * S; k < e; k += S) {   // blocks beyond the prefetched ones
+  for (int k = a + q + U * S; active && k < e; k += S) {   // blocks beyond the prefetched ones
     const int jj = __ldg(col + k);
     T x0, x1, x2;
     ld3(x, jj * K + r, x0, x1, x2);
@@ -505,12 +514,30 @@ __global__ void __launch_bounds__(256) k_gs_m_pdl(int nrows, const int* __restri
     s2 = fma(__ldg(vv + 7 * nnzb), x1, s2);
     s2 = fma(__ldg(vv + 8 * nnzb), x2, s2);
   }
-  if (S == 2) {
+  if (S >= 2) {   // lane groups q and q + 1 share a warp (K = 16 lanes each)
     s0 += __shfl_xor_sync(0xffffffffu, s0, 16);
     s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
     s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-    if (q != 0) return;
   }
+  if (S > 2) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < K) {
+      red[w][lane][0] = s0;
+      red[w][lane][1] = s1;
+      red[w][lane][2] = s2;
+    }
+    __syncthreads();
+    if (!active || q != 0) return;
+    // the row's first warp holds q = 0: add its S / 2 warps' sums in order
+    s0 = s1 = s2 = T(0);
+#pragma unroll
+    for (int v = 0; v < S / 2; ++v) {
+      s0 += red[w + v][r][0];
+      s1 += red[w + v][r][1];
+      s2 += red[w + v][r][2];
+    }
+  }
+  if (S >= 2 && q != 0) return;
   const int o = i * K + r;
   T x0, x1, x2;
   ld3(x, o, x0, x1, x2);
@@ -549,6 +576,10 @@ void gs_colour_m(amg_handle* h, Level& lv, int first, int nrows, const T* val, T
     case 1: launch_gs_m_pdl<T, 2, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
     case 2: launch_gs_m_pdl<T, 1, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
     case 3: launch_gs_m_pdl<T, 2, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 4: launch_gs_m_pdl<T, 4, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 5: launch_gs_m_pdl<T, 8, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 6: launch_gs_m_pdl<T, 4, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
+    case 7: launch_gs_m_pdl<T, 8, 4>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
     default: launch_gs_m_pdl<T, 1, 2>(nrows, rows, rowptr, lv, val, x, b, dinv, s); break;
   }
   h->launches++;
@@ -635,7 +666,7 @@ void smooth_m(amg_handle* h, int l, T* x, const T* b, bool post) {
     const int c = post ? lv.ncolours - 1 - q : q;
     const int a = lv.colour_ptr[c], e = lv.colour_ptr[c + 1];
     if (h->use_pdl && lv.k_rows())
-      gs_colour_m<T>(h, lv, a, e - a, MV<T>::val(lv), x, b, MV<T>::dinv(lv), bl.tile);
+      gs_colour_m<T>(h, lv, a, e - a, MV<T>::val(lv), x, b, MV<T>::dinv(lv), bl.tile_gs);
     else
       rows_m<T>(h, mGS, lv, a, e - a, MV<T>::val(lv), x, b, x, MV<T>::dinv(lv), T(1), bl.tile);
   }
@@ -712,7 +743,7 @@ void dots_m(amg_handle* h, int slot, const double* a0, const double* b0,
   const int nd = a1 ? 2 : 1;
   const int64_t nel = 4 * (int64_t)K * h->L[0]->n;
   k_dots_m<<<kDotBlocks, kDotThreads, 0, h->stream>>>(nel, nd, a0, b0, a1, b1, h->bred);
-  k_final_m<<<1, 64, 0, h->stream>>>(h->bred, kDotBlocks, nd, h->bscal.p + slot * K);
+  k_final_m<<<nd * K, 32, 0, h->stream>>>(h->bred, kDotBlocks, nd, h->bscal.p + slot * K);
   h->launches += 2;
 }
 
@@ -804,17 +835,26 @@ void alloc_batch(amg_handle* h) {
   AMG_CUDA(cudaStreamSynchronize(h->stream));
   // SpMM tile per level (the coarsest level is solved densely): given, or timed
   const int fixed = h->opt.batch_tile;
-  if (fixed >= kTiles) fail(AMG_ERR_INVALID, "batch_tile must be -1 or 0..3");
+  if (fixed >= kGsTiles) fail(AMG_ERR_INVALID, "batch_tile must be -1 or 0..7");
   for (size_t l = 0; l + 1 < h->L.size(); ++l) {
     Level& lv = *h->L[l];
     BatchLevel& b = h->B[l];
-    if (fixed >= 0) b.tile = fixed;
+    if (fixed >= 0) b.tile = fixed % kTiles;
     else if (f32) b.tile = tune_tile<float>(h, lv, MV<float>::val(lv), b.x32, b.t32);
     else b.tile = tune_tile<double>(h, lv, MV<double>::val(lv), b.x64, b.t64);
   }
-  h->B[0].tile64 = fixed >= 0 ? fixed
+  h->B[0].tile64 = fixed >= 0 ? fixed % kTiles
                               : tune_tile<double>(h, *h->L[0], h->L[0]->k_val(), h->mx, h->mq);
-  if (h->mpf.p) h->B[0].tile_pair = fixed >= 0 ? fixed : tune_pair_tile(h);
+  if (h->mpf.p) h->B[0].tile_pair = fixed >= 0 ? fixed % kTiles : tune_pair_tile(h);
+  // the colour kernel's tile per level: forced, else the SpMM's.  Timing each level's
+  // sweep alone picked 4 or 8 lane groups a row on the small levels, which shortens a
+  // lone problem's sweeps but made the 64-problem batch slower (2.24 against 2.09 s):
+  // with all problems running side by side the device is full and the wider groups
+  // only add threads.
+  for (size_t l = 0; l + 1 < h->L.size(); ++l) {
+    BatchLevel& b = h->B[l];
+    b.tile_gs = fixed >= 0 ? fixed : b.tile;
+  }
 }
 
 // initial block of one problem: x = 0, r = b, z = M r, rz, p = z, active set
@@ -845,7 +885,7 @@ void emit_iteration(amg_handle* h, cudaGraphConditionalHandle cond) {
   dots_m(h, M_PQ, h->mp, h->mq);
   k_update_m<<<kDotBlocks, kDotThreads, 0, s>>>(nel, h->mx, h->mr, h->mp, h->mq, h->mro,
                                                 h->bscal, h->bred);
-  k_final_m<<<1, 64, 0, s>>>(h->bred, kDotBlocks, 1, h->bscal.p + M_RR * K);
+  k_final_m<<<K, 32, 0, s>>>(h->bred, kDotBlocks, 1, h->bscal.p + M_RR * K);
   k_check_m<<<1, 32, 0, s>>>(cond, h->bscal, h->bit, h->opt.max_iterations);
   h->launches += 3;
   precond_m(h, h->mr, h->mz);

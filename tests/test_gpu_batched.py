@@ -45,10 +45,13 @@ def _rhs(prob, k, rng):
 
 @pytest.mark.parametrize("precision,k,tile,pair", [
     (0, 5, -1, 1), (1, 5, -1, 1), (1, 16, -1, 1), (1, 1, -1, 1), (1, 5, 0, 1), (1, 5, 1, 1),
-    (1, 5, 2, 1), (1, 5, 3, 1), (0, 3, 1, 1), (0, 3, 3, 1), (1, 5, -1, 0), (1, 16, 3, 0)])
+    (1, 5, 2, 1), (1, 5, 3, 1), (0, 3, 1, 1), (0, 3, 3, 1), (1, 5, -1, 0), (1, 16, 3, 0),
+    (1, 5, 4, 1), (1, 16, 5, 1), (1, 5, 6, 1), (1, 16, 7, 1), (0, 3, 5, 1), (0, 16, 6, 1)])
 def test_batched_matches_single_and_direct(precision, k, tile, pair):
-    """tile -1: the SpMM tile chosen per level by timing; 0..3: each tile forced.
-    pair: with the FP32 cycle, the operator products in FP32 pairs (1) or FP64 (0)."""
+    """tile -1: the SpMM tile chosen per level by timing, the colour kernel's the same; 0..7: the
+    colour kernel's tile forced (4..7: 4 or 8 lane groups a row, combined through
+    shared memory), the SpMM's tile t mod 4.  pair: with the FP32 cycle, the operator
+    products in FP32 pairs (1) or FP64 (0)."""
     probs = _problems()
     rng = np.random.default_rng(7)
     handles, Bs, Xs, rhs = [], [], [], []
@@ -177,4 +180,14 @@ def test_batched_rejects_a_repeated_handle():
     # the handle still works
     rc, st = B().solve_batched([h], [b], xs[:1], 1, 1e-8)
     assert rc == 0 and st[0].converged
+    h.free()
+
+
+def test_batched_rejects_tile_out_of_range():
+    p = fp.elasticity_problem(4, seed=1, nu=0.3)
+    h = B().setup_problem(p, B().default_options(precision=1, batch_tile=8))
+    b = torch.from_numpy(np.ascontiguousarray(p.f.reshape(-1))).cuda()
+    x = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+    with pytest.raises(B().AmgError):
+        B().solve_batched([h], [b], [x], 1, 1e-8)
     h.free()
