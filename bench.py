@@ -491,7 +491,7 @@ def run_gpu(args, rank, world):
 def run_profile(args):
     """One chosen and one plain solve, nothing else timed (a case for ncu).  With
     --workload mixed: one FP32-cycle FGMRES(300) solve of the nu = 0.499 member of the
-    mixed elasticity family on --n-mixed cubes, default options."""
+    mixed elasticity family on --n-mixed cubes (default options but the cycle variant)."""
     import torch
 
     from fem_inputs import elasticity_problem
@@ -504,8 +504,12 @@ def run_profile(args):
         prob = make_config("mixed_elast_n40", n=args.n_mixed)[1]
         b = torch.from_numpy(prob.rhs()).cuda()
         x = torch.zeros_like(b)
+        # the cycle variant given explicitly (timing under a profiler would choose
+        # differently): per-operation launches by default, as the bench's runs select
         h = B.setup_problem(prob, B.default_options(precision=B.AMG_FP32, gmres_restart=300,
-                                                    max_iterations=1000),
+                                                    max_iterations=1000,
+                                                    cycle_kernel=args.cycle_kernel,
+                                                    cluster_from=args.cluster_from),
                             stream=stream.cuda_stream)
         st = h.solve(b, x, TOL, device_ptrs=True)
         print(json.dumps({"precision": B.AMG_FP32, "workload": f"mixed_elast_n{args.n_mixed}",

@@ -306,6 +306,10 @@ __device__ __forceinline__ void bt_add_body(int n, const int* __restrict__ row,
 // MODE 0: yp = B u - C p;  MODE 1: yp = g - B u + C p (residual);
 // MODE 2: yp = p + omega (B u - C p - g) / S_D (sGS pressure step);
 // MODE 3: yp = B u - g (Braess-Sarazin: g holds the pressure residual)
+// The pressure rows: kProwLanes consecutive lanes share a row (its B entries and then
+// its C entries taken in strides of kProwLanes, the lane sums combined by shuffles),
+// so a row's dependent gather chain is about 1/kProwLanes of its length.
+constexpr int kProwLanes = 8;
 template <typename T, int MODE, bool COH>
 __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
                                            const int* __restrict__ bcol,
@@ -316,9 +320,12 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
                                            const T* g, T* yp, const T* __restrict__ sd, T omega,
                                            const double* __restrict__ wt, int tid, int nthr) {
   if (MODE == 2 && wt) omega = (T)((double)omega * wt[2]);
-  for (int k = tid; k < np; k += nthr) {
+  constexpr int L = kProwLanes;
+  const int gl = tid & (L - 1);
+  const unsigned gmask = ((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1));
+  for (int k = tid / L; k < np; k += nthr / L) {
     T s = T(0);
-    for (int q = brow[k]; q < brow[k + 1]; ++q) {
+    for (int q = brow[k] + gl; q < brow[k + 1]; q += L) {
       const int j = bcol[q];
       T u0, u1, u2;
       VL<COH>::node(u, j, u0, u1, u2);
@@ -326,13 +333,19 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
       s = fma(bval[bnnz + q], u1, s);
       s = fma(bval[2 * bnnz + q], u2, s);
     }
+    T cp = T(0);
+    if (MODE != 3)
+      for (int q = crow[k] + gl; q < crow[k + 1]; q += L)
+        cp = fma(cval[q], VL<COH>::one(p + ccol[q]), cp);
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(gmask, s, o);
+      cp += __shfl_xor_sync(gmask, cp, o);
+    }
+    if (gl != 0) continue;
     if (MODE == 3) {               // Braess-Sarazin right-hand side B w - r_p
       yp[k] = s - VL<COH>::one(g + k);
-      continue;
-    }
-    T cp = T(0);
-    for (int q = crow[k]; q < crow[k + 1]; ++q) cp = fma(cval[q], VL<COH>::one(p + ccol[q]), cp);
-    if (MODE == 0) {
+    } else if (MODE == 0) {
       yp[k] = s - cp;
     } else if (MODE == 1) {
       yp[k] = VL<COH>::one(g + k) - s + cp;
@@ -1998,7 +2011,7 @@ struct Emit {
     P.cval = LvVec<T>::cval(lv); P.x = u; P.p = p; P.b = g; P.y = yp;
     P.sd = LvVec<T>::schur(lv); P.omega = (double)omega;
     P.wt = mode == 2 ? lv.wt : nullptr;
-    put(P, lv.np);
+    put(P, lv.np, kProwLanes);
   }
 };
 
