@@ -771,7 +771,9 @@ def run_configs(args, B, budget_s=300.0):
     small = sorted(range(len(specs)), key=lambda i: specs[i]["n"])[:2]
     out = {}
     ctx = mp.get_context("spawn")
-    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+    # two host cores stay free for the process that drives the GPU: the FGMRES loop
+    # synchronises with the host every iteration
+    with ctx.Pool(max(1, min(16, (os.cpu_count() or 3) - 2))) as pool:
         o_stokes = pool.apply_async(oracle_worker, (("stokes", 24, TOL),))
         o_batch = [pool.apply_async(oracle_worker, (("batched", specs[i], j, TOL),))
                    for i in small for j in (0, 15)]
