@@ -181,27 +181,15 @@ __device__ __forceinline__ void rows_body(int nrows, const int* __restrict__ row
   }
 }
 
-// Row kernels whose rows are long gather chains take kGatherLanes consecutive lanes a
-// row (entries in strides of kGatherLanes, lane sums combined by shuffles within the
-// aligned lane group): R = P^T (a coarse node gathers from every fine node that
-// interpolates from it), H^T, and B^T.
-constexpr int kGatherLanes = 4;
-__device__ __forceinline__ unsigned lane_group_mask(int L) {
-  return ((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
-}
-
 // R = P^T gather: bc_I = sum_t w_t r_{i_t} (3 components, same weight)
 template <typename T, bool COH>
 __device__ __forceinline__ void restrict_body(int nc, const int* __restrict__ rrow,
                                               const int* __restrict__ rcol,
                                               const T* __restrict__ rval, const T* r, T* bc,
                                               int tid, int nthr) {
-  constexpr int L = kGatherLanes;
-  const int gl = tid & (L - 1);
-  const unsigned gmask = lane_group_mask(L);
-  for (int I = tid / L; I < nc; I += nthr / L) {
+  for (int I = tid; I < nc; I += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    for (int t = rrow[I] + gl; t < rrow[I + 1]; t += L) {
+    for (int t = rrow[I]; t < rrow[I + 1]; ++t) {
       const int i = rcol[t];
       const T w = rval[t];
       T r0, r1, r2;
@@ -210,13 +198,7 @@ __device__ __forceinline__ void restrict_body(int nc, const int* __restrict__ rr
       s1 = fma(w, r1, s1);
       s2 = fma(w, r2, s2);
     }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(gmask, s0, o);
-      s1 += __shfl_xor_sync(gmask, s1, o);
-      s2 += __shfl_xor_sync(gmask, s2, o);
-    }
-    if (gl == 0) st3(bc, I, s0, s1, s2);
+    st3(bc, I, s0, s1, s2);
   }
 }
 
@@ -251,16 +233,10 @@ __device__ __forceinline__ void restrict1_body(int nc, const int* __restrict__ r
                                                const int* __restrict__ rcol,
                                                const T* __restrict__ rval, const T* r, T* bc,
                                                int tid, int nthr) {
-  constexpr int L = kGatherLanes;
-  const int gl = tid & (L - 1);
-  const unsigned gmask = lane_group_mask(L);
-  for (int I = tid / L; I < nc; I += nthr / L) {
+  for (int I = tid; I < nc; I += nthr) {
     T s = T(0);
-    for (int t = rrow[I] + gl; t < rrow[I + 1]; t += L)
-      s = fma(rval[t], VL<COH>::one(r + rcol[t]), s);
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
-    if (gl == 0) bc[I] = s;
+    for (int t = rrow[I]; t < rrow[I + 1]; ++t) s = fma(rval[t], VL<COH>::one(r + rcol[t]), s);
+    bc[I] = s;
   }
 }
 
@@ -313,24 +289,14 @@ __device__ __forceinline__ void bt_add_body(int n, const int* __restrict__ row,
                                             const int* __restrict__ col,
                                             const T* __restrict__ val, int64_t nnz, const T* p,
                                             T sign, T* y, int tid, int nthr) {
-  constexpr int L = kGatherLanes;
-  const int gl = tid & (L - 1);
-  const unsigned gmask = lane_group_mask(L);
-  for (int i = tid / L; i < n; i += nthr / L) {
+  for (int i = tid; i < n; i += nthr) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    for (int q = row[i] + gl; q < row[i + 1]; q += L) {
+    for (int q = row[i]; q < row[i + 1]; ++q) {
       const T pk = VL<COH>::one(p + col[q]);
       s0 = fma(val[q], pk, s0);
       s1 = fma(val[nnz + q], pk, s1);
       s2 = fma(val[2 * nnz + q], pk, s2);
     }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(gmask, s0, o);
-      s1 += __shfl_xor_sync(gmask, s1, o);
-      s2 += __shfl_xor_sync(gmask, s2, o);
-    }
-    if (gl != 0) continue;
     T y0, y1, y2;
     VL<COH>::node(y, i, y0, y1, y2);
     st3(y, i, y0 + sign * s0, y1 + sign * s1, y2 + sign * s2);
@@ -356,7 +322,7 @@ __device__ __forceinline__ void prows_body(int np, const int* __restrict__ brow,
   if (MODE == 2 && wt) omega = (T)((double)omega * wt[2]);
   constexpr int L = kProwLanes;
   const int gl = tid & (L - 1);
-  const unsigned gmask = lane_group_mask(L);
+  const unsigned gmask = ((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1));
   for (int k = tid / L; k < np; k += nthr / L) {
     T s = T(0);
     for (int q = brow[k] + gl; q < brow[k + 1]; q += L) {
@@ -1987,8 +1953,7 @@ struct Emit {
                 T* dst, const double* wt = nullptr) {
     Phase P = blank(type);
     P.n = n; P.rowptr = row; P.col = col; P.val = val; P.x = src; P.y = dst; P.wt = wt;
-    const bool gather = type == PH_RESTRICT || type == PH_RESTRICT1;
-    put(P, n, gather ? kGatherLanes : 1);
+    put(P, n);
   }
   void coarse(const T* b, T* x) {
     Phase P = blank(PH_COARSE);
@@ -1999,7 +1964,7 @@ struct Emit {
     Phase P = blank(PH_BT_ADD);
     P.n = lv.n; P.rowptr = lv.bt_rowptr; P.col = lv.bt_col; P.val = LvVec<T>::btval(lv);
     P.nnz = lv.b_nnz; P.x = p; P.omega = (double)sign; P.y = y;
-    put(P, lv.n, kGatherLanes);
+    put(P, lv.n);
   }
   void srows(int mode, SLevel& q, const T* x, const T* b, T* y, T omega) {
     Phase P = blank(PH_SROWS);
