@@ -92,9 +92,10 @@ constexpr int kTile = 256;                 // entries of a row piece (2 KB of pa
 constexpr int kConsumers = kTile / 32;     // consumer warps: one entry a thread
 constexpr int kThreads = kTile + 32;       // and one producer warp
 constexpr int kPieces = 10;                // pieces a stage: up to 8 basis rows, u and w
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr unsigned kBulkSpins = 1u << 20;
-constexpr int kStreamSmem = kStages * kPieces * kTile * (int)sizeof(float2);   // 80 KB
+constexpr int kStreamSmem = kStages * kPieces * kTile * (int)sizeof(float2);   // 60 KB
+constexpr int kCtasPerSm = 3;              // CTAs of a sweep kernel an SM (shared memory)
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -197,7 +198,7 @@ __device__ __forceinline__ uint32_t piece_bytes(int64_t ld, int64_t k0) {
 // partial[(blockIdx.x * rows + i) * 2 + {0, 1}] = sum over the tiles of block column
 // blockIdx.x of V_i[k] u[k] and V_i[k] w[k], kMdotG rows per block row (blockIdx.y).
 // Rows are ld entries apart; the entries from n to ld are padding (copied, not used).
-__global__ void __launch_bounds__(kThreads, 2) k_mdot2(int64_t n, int64_t ld, int rows,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_mdot2(int64_t n, int64_t ld, int rows,
                                                     const float2* __restrict__ V,
                                                     const float2* __restrict__ u,
                                                     const float2* __restrict__ w,
@@ -315,7 +316,7 @@ __global__ void k_dcgs2_coef(int m, double* __restrict__ coef) {
 // vector before its normalisation; partial[blockIdx.x] = the block's sum of w'^2.
 // A CTA takes tiles of kTile entries (one a thread); a tile's rows stream through
 // the ring eight at a time, u and w with the first eight.
-__global__ void __launch_bounds__(kThreads, 2) k_dcgs2_update(int64_t n, int64_t ld, int m,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_dcgs2_update(int64_t n, int64_t ld, int m,
                                                            const float2* __restrict__ V,
                                                            float2* u,
                                                            const float2* __restrict__ w,
@@ -830,8 +831,8 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   ydev.alloc(kMaxDots);
   // H by columns: Hc[j * (m + 1) + i] = H(i, j); rotated in place once a column is final
   std::vector<double> Hc((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hb(kS + 8), tmp(m + 1);
-  // the sweep's kernels: kTile threads a CTA, the ring in dynamic shared memory, two
-  // CTAs an SM
+  // the sweep's kernels: kThreads threads a CTA, the ring in dynamic shared memory,
+  // kCtasPerSm CTAs an SM
   int dev = 0, sms = 0;
   AMG_CUDA(cudaGetDevice(&dev));
   AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -840,10 +841,10 @@ int solve_fgmres(amg_handle* h, Ctx& c, const double* b, double* x, double tol, 
   AMG_CUDA(cudaFuncSetAttribute(k_dcgs2_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kStreamSmem));
   const int64_t ntiles = (n + kTile - 1) / kTile;
-  const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * sms));
+  const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)kCtasPerSm * sms));
   auto mdot2 = [&](int rows, const float2* u, const float2* wv) {
     const int grows = (rows + kMdotG - 1) / kMdotG;
-    const int cols = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms / grows, ntiles));
+    const int cols = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)kCtasPerSm * sms / grows, ntiles));
     k_mdot2<<<dim3(cols, grows), kThreads, kStreamSmem, s>>>(n, ld, rows, V, u, wv, h->red,
                                                           h->flag.p);
     k_mdot_final<<<(2 * rows + 7) / 8, 256, 0, s>>>(h->red, cols, rows, 2, kMaxDots, coef.p);
