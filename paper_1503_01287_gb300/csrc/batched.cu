@@ -10,9 +10,9 @@
 // Each problem runs flexible CG per right-hand side (Polak-Ribiere beta, the
 // FP64 outer iteration of the FP32 or FP64 cycle; with the FP32 cycle the
 // operator products K p are FP32-pair SpMM, see k_apply_pair_m); converged right-hand sides
-// are frozen (alpha = beta = 0).  The whole batch is ONE CUDA graph: one branch
-// per problem, each branch an initial block followed by a conditional WHILE
-// node whose body is one iteration and its device-side stopping test.
+// are frozen (alpha = beta = 0).  Each problem is one CUDA graph, launched on its own
+// handle's stream: an initial block followed by a conditional WHILE node whose body is
+// one iteration and its device-side stopping test.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -1,9 +1,10 @@
 // Krylov accelerators of the AMG preconditioner (Sec. 3.1 and Sec. 4):
 // preconditioned CG (SPD, FP64 cycle), flexible CG (SPD, FP32 cycle), right-
 // preconditioned flexible GMRES(m) (saddle systems), and the stand-alone AMG
-// iteration.  Residuals, inner products and orthogonalisation are FP64;
-// scalars stay on the device and the host reads one residual norm per
-// iteration for the stopping rule ||b - K x_k|| / ||b|| <= tol.
+// iteration.  The CG vectors, residuals and inner products are FP64; the FGMRES basis
+// and its Gram-Schmidt sweep are FP32 pairs (about 2^-48), its Hessenberg matrix FP64.
+// Scalars stay on the device and the host reads one residual estimate per iteration
+// for the stopping rule ||b - K x_k|| / ||b|| <= tol.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
